@@ -1,0 +1,295 @@
+"""CPU oracle for RLT2 dual ascent -- TEST INFRASTRUCTURE.
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library never does, and this
+package never imports the CUDA library: the two share nothing but the seeded
+input generator (``paper_1710_03732_gb300.instances``), which holds none of
+the method's arithmetic.
+
+The C source ``rlt2_oracle.c`` is compiled with gcc (``-O2 -ffp-contract=off``,
+OpenMP when available) into ``oracle/_build/liboracle.so`` on first use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rlt2_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_lp = ctypes.POINTER(ctypes.c_longlong)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc, -O2 -ffp-contract=off; OpenMP if it links)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        L = _lib
+        L.or_lap.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _ip, _ip, _lp]
+        L.or_lap_canonical.argtypes = [ctypes.c_int, _dp, _ip, _dp, _dp]
+        L.or_lap_brute.argtypes = [ctypes.c_int, _dp, _ip]
+        L.or_lap_brute.restype = ctypes.c_double
+        L.or_qap_cost.argtypes = [ctypes.c_int, _dp, _dp, _dp, _ip]
+        L.or_qap_cost.restype = ctypes.c_double
+        L.or_qap_brute.argtypes = [ctypes.c_int, _dp, _dp, _dp, _ip]
+        L.or_qap_brute.restype = ctypes.c_double
+        L.or_num_tiles.argtypes = [ctypes.c_int]
+        L.or_num_tiles.restype = ctypes.c_longlong
+        L.or_num_z.argtypes = [ctypes.c_int]
+        L.or_num_z.restype = ctypes.c_longlong
+        L.or_setup.argtypes = [ctypes.c_int, _dp, _dp, _dp, _ip, _ip, _dp, _dp, _dp, _dp]
+        L.or_stage_z.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _lp, _lp, ctypes.c_int]
+        L.or_stage_y.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _lp, _lp]
+        L.or_stage_x.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _ip, _lp, _lp]
+        L.or_reduced_xy.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.or_redistribute_z.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
+        L.or_redistribute_y.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp]
+        L.or_feasibility.argtypes = [ctypes.c_int, _ip, _dp, _dp, _dp, _dp, ctypes.c_double]
+        L.or_iterate.argtypes = ([ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                  _dp, _dp, _dp, _dp, _ip, _dp, _dp, _lp, ctypes.c_int])
+        L.or_have_openmp.restype = ctypes.c_int
+    return _lib
+
+
+def _d(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _i(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(_ip)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def max_threads() -> int:
+    return int(lib().or_have_openmp())
+
+
+# --------------------------------------------------------------------------
+# LAP
+# --------------------------------------------------------------------------
+@dataclass
+class LapResult:
+    value: float
+    u: np.ndarray
+    v: np.ndarray
+    row_to_col: np.ndarray
+    n_aug: int
+    n_relax: int
+
+
+def lap(cost: np.ndarray, u0: Optional[np.ndarray] = None, canonical: bool = False) -> LapResult:
+    c = _f64(cost)
+    m = c.shape[0]
+    u = np.zeros(m)
+    v = np.zeros(m)
+    r2c = np.zeros(m, dtype=np.int32)
+    val = ctypes.c_double()
+    aug = ctypes.c_int()
+    rel = ctypes.c_longlong()
+    u0c = None if u0 is None else _f64(u0)
+    lib().or_lap(m, _d(c), _d(u0c), ctypes.byref(val), _d(u), _d(v), _i(r2c), ctypes.byref(aug), ctypes.byref(rel))
+    if canonical:
+        u, v = lap_canonical(c, r2c)
+    return LapResult(val.value, u, v, r2c, aug.value, rel.value)
+
+
+def lap_canonical(cost: np.ndarray, row_to_col: np.ndarray):
+    c = _f64(cost)
+    m = c.shape[0]
+    r2c = np.ascontiguousarray(row_to_col, dtype=np.int32)
+    u = np.zeros(m)
+    v = np.zeros(m)
+    lib().or_lap_canonical(m, _d(c), _i(r2c), _d(u), _d(v))
+    return u, v
+
+
+def lap_brute(cost: np.ndarray):
+    c = _f64(cost)
+    m = c.shape[0]
+    perm = np.zeros(m, dtype=np.int32)
+    val = lib().or_lap_brute(m, _d(c), _i(perm))
+    return val, perm
+
+
+def qap_cost(F, D, B, perm) -> float:
+    F, D = _f64(F), _f64(D)
+    B = None if B is None else _f64(B)
+    p = np.ascontiguousarray(perm, dtype=np.int32)
+    return lib().or_qap_cost(F.shape[0], _d(F), _d(D), _d(B), _i(p))
+
+
+def qap_brute(F, D, B=None):
+    F, D = _f64(F), _f64(D)
+    B = None if B is None else _f64(B)
+    n = F.shape[0]
+    perm = np.zeros(n, dtype=np.int32)
+    val = lib().or_qap_brute(n, _d(F), _d(D), _d(B), _i(perm))
+    return val, perm
+
+
+# --------------------------------------------------------------------------
+# RLT2 state and one iteration
+# --------------------------------------------------------------------------
+def num_tiles(n: int) -> int:
+    return n * n * (n - 1) * (n - 1)
+
+
+def num_z(n: int) -> int:
+    return num_tiles(n) * (n - 2) * (n - 2)
+
+
+def params_array(kz=1.0, ky=0.5, kx=1.0, phi_y=0.5, phi_z: Sequence[float] = (0.2,) * 5) -> np.ndarray:
+    return np.array([kz, ky, kx, phi_y] + list(phi_z), dtype=np.float64)
+
+
+@dataclass
+class State:
+    n: int           # residual size
+    const: float     # constant from the fixed facilities
+    bprime: np.ndarray
+    Chat: np.ndarray
+    Dhat: np.ndarray
+
+
+def setup(F, D, B=None, partial=None) -> State:
+    F, D = _f64(F), _f64(D)
+    n = F.shape[0]
+    B = None if B is None else _f64(B)
+    part = None if partial is None else np.ascontiguousarray(partial, dtype=np.int32)
+    nr = n if part is None else int((part < 0).sum())
+    bprime = np.zeros(nr * nr)
+    Chat = np.zeros(max(num_tiles(nr), 1))
+    Dhat = np.zeros(max(num_z(nr), 1)) if nr >= 3 else np.zeros(1)
+    nres = ctypes.c_int()
+    cst = ctypes.c_double()
+    rc = lib().or_setup(n, _d(F), _d(D), _d(B), _i(part), ctypes.byref(nres), ctypes.byref(cst), _d(bprime),
+                        _d(Chat), _d(Dhat))
+    if rc != 0:
+        raise ValueError("or_setup rejected the input")
+    return State(nr, cst.value, bprime, Chat, Dhat)
+
+
+@dataclass
+class IterOut:
+    lb: float
+    Theta: np.ndarray
+    xi: np.ndarray
+    psi: np.ndarray
+    Delta: np.ndarray
+    gamma: np.ndarray
+    delta: np.ndarray
+    alpha: np.ndarray
+    beta: np.ndarray
+    xperm: np.ndarray
+    pix: np.ndarray
+    piy: np.ndarray
+    stats: np.ndarray  # [aug_z, relax_z, aug_y, relax_y, aug_x, relax_x]
+
+
+def iterate(st: State, prm: np.ndarray, dual_mode: int = 1, u0z: Optional[np.ndarray] = None,
+            threads: int = 1) -> IterOut:
+    """One S1 iteration in place on st.Chat / st.Dhat; returns the bound and all duals
+    (the bound is of the multipliers before this iteration's ascent step)."""
+    n = st.n
+    T = num_tiles(n)
+    mz, my = n - 2, n - 1
+    o = IterOut(0.0, np.zeros(T), np.zeros(T * mz), np.zeros(T * mz), np.zeros(n * n), np.zeros(n * n * my),
+                np.zeros(n * n * my), np.zeros(n), np.zeros(n), np.zeros(n, dtype=np.int32), np.zeros(n * n),
+                np.zeros(T), np.zeros(6, dtype=np.int64))
+    lb = ctypes.c_double()
+    prm = _f64(prm)
+    u0c = None if u0z is None else _f64(u0z)
+    rc = lib().or_iterate(n, _d(prm), dual_mode, _d(st.bprime), _d(st.Chat), _d(st.Dhat), _d(u0c),
+                          ctypes.byref(lb), _d(o.Theta), _d(o.xi), _d(o.psi), _d(o.Delta), _d(o.gamma),
+                          _d(o.delta), _d(o.alpha), _d(o.beta), _i(o.xperm), _d(o.pix), _d(o.piy),
+                          o.stats.ctypes.data_as(_lp), threads)
+    if rc != 0:
+        raise ValueError("or_iterate rejected the input")
+    o.lb = lb.value
+    return o
+
+
+def stage_z(n, Dhat, dual_mode=1, u0=None, threads=1):
+    T = num_tiles(n)
+    m = n - 2
+    Theta, xi, psi = np.zeros(T), np.zeros(T * m), np.zeros(T * m)
+    aug, rel = ctypes.c_longlong(), ctypes.c_longlong()
+    lib().or_stage_z(n, dual_mode, _d(_f64(Dhat)), _d(None if u0 is None else _f64(u0)), _d(Theta), _d(xi),
+                     _d(psi), ctypes.byref(aug), ctypes.byref(rel), threads)
+    return Theta, xi, psi, aug.value, rel.value
+
+
+def redistribute_z(n, prm, Dhat, xi, psi, piy, pix, threads=1):
+    """Returns a new D^ after the z move (input left untouched)."""
+    out = _f64(Dhat).copy()
+    lib().or_redistribute_z(n, _d(_f64(prm)), _d(out), _d(_f64(xi)), _d(_f64(psi)), _d(_f64(piy)), _d(_f64(pix)),
+                            threads)
+    return out
+
+
+def redistribute_y(n, phi_y, Chat, piy):
+    out = _f64(Chat).copy()
+    lib().or_redistribute_y(n, float(phi_y), _d(out), _d(_f64(piy)))
+    return out
+
+
+def feasibility(n, xperm, piy, Dhat, xi, psi, tol=1e-9) -> bool:
+    return bool(lib().or_feasibility(n, _i(np.ascontiguousarray(xperm, dtype=np.int32)), _d(_f64(piy)),
+                                     _d(_f64(Dhat)), _d(_f64(xi)), _d(_f64(psi)), float(tol)))
+
+
+def run(F, D, B=None, iters=10, prm=None, dual_mode=1, partial=None, threads=1, warm=False):
+    """Run the dual ascent; returns (state, list of per-iteration bounds incl. const, last IterOut)."""
+    st = setup(F, D, B, partial)
+    prm = params_array() if prm is None else prm
+    lbs = []
+    out = None
+    u0 = None
+    for _ in range(iters):
+        out = iterate(st, prm, dual_mode, u0z=u0 if warm else None, threads=threads)
+        lbs.append(st.const + out.lb)
+        u0 = out.xi.copy()
+    return st, lbs, out
+
+
+# index helpers used by tests
+def tile_index(n, i, p, j, q):
+    jj = j - (j > i)
+    qq = q - (q > p)
+    return ((i * n + p) * (n - 1) + jj) * (n - 1) + qq
+
+
+def z_index(n, i, j, k, p, q, r):
+    m = n - 2
+    kk = k - (k > i) - (k > j)
+    rr = r - (r > p) - (r > q)
+    return tile_index(n, i, p, j, q) * m * m + kk * m + rr

@@ -1,0 +1,602 @@
+/*
+ * CPU oracle for RLT2 Lagrangian dual ascent on the QAP (Date & Nagi,
+ * "RLT2-based Parallel Algorithms for Solving Large Quadratic Assignment
+ * Problems on Graphics Processing Unit Clusters").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, deliberately obvious
+ * restatement of the method in FP64.  It is used by the test-suite, by the
+ * package smoke check and by the benchmark's CPU-baseline leg; nothing on the
+ * product path links, loads or calls it.  It shares no code with the CUDA
+ * library.  Build flags: -O2 -ffp-contract=off (no fused multiply-add, so
+ * every + and * below is one IEEE round-to-nearest operation).
+ *
+ * Notation follows the paper (Section 2.3):
+ *   n facilities/locations, b (n x n), C_ijpq = f_ij d_pq (RLT1, Eq. 2.1),
+ *   D_ijkpqr (RLT2, Eq. 2.6) = 0 for the QAP, multiplier-adjusted costs
+ *   b', C^ = C - u, D^ = D - v (Section 3.3: the multipliers live inside the
+ *   costs, there is no separate multiplier array).
+ *   Z-LAP(i,j,p,q): rows k != i,j, cols r != p,q, cost D^_ijkpqr -> Theta, xi, psi
+ *   Y-LAP(i,p):     rows j != i,   cols q != p,   cost C^_ijpq + Theta_ijpq -> Delta, gamma, delta
+ *   X-LAP:          rows i,        cols p,        cost b'_ip + Delta_ip -> LB, alpha, beta
+ *
+ * Array layouts (shared by contract with the CUDA library, not by code):
+ *   compressed index: j' = j - (j > i); k' = k - (k > i) - (k > j) (same for
+ *   locations).  Tile t(i,p,j',q') = ((i*n + p)*(n-1) + j')*(n-1) + q'.
+ *   C^[t], Theta[t], pi_y[t]; D^[t*m*m + k'*m + r'] with m = n-2;
+ *   xi[t*m + k'], psi[t*m + r']; gamma/delta[(i*n+p)*(n-1) + j'/q'];
+ *   Delta[i*n+p], pi_x[i*n+p], alpha[i], beta[p].
+ *
+ * Readings of points the paper leaves open (all listed in the design doc):
+ *   - state is (b', C^, D^); Theta and Delta are rebuilt every iteration
+ *     (Algorithm 1's "C' <- C' + Theta" is read as a temporary, S1 variant);
+ *   - all reduced costs come from one snapshot before any cost moves (Jacobi);
+ *   - LAP duals: raw (this Hungarian's own) or canonical (pointwise-maximal
+ *     row duals with u_0 = 0 among all optimal duals; unique);
+ *   - per z entry a=(i,j,k,p,q,r), s(a) = kz*pi_z(a) + (cy*pi_y(ijpq) + cx*pi_x(ip)),
+ *     cy = ky/(n-2), cx = kx/((n-1)(n-2))  (Eq. 2.20, 2.22, 2.23 combined as
+ *     in the proof of Theorem 1), and
+ *     D^'(a) = (D^(a) - s(a)) + sum over the five partners b of phi(b->a)*s(b);
+ *   - y move (Eq. 2.21): C^'_ijpq = (C^_ijpq - phi_y*pi_y(ijpq)) + phi_y*pi_y(jiqp).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_OK 0
+#define OR_EINVAL 1
+
+/* ------------------------------------------------------------------------ */
+/* Linear assignment: shortest-augmenting-path Hungarian (primal-dual).      */
+/* The paper solves every LAP with a Hungarian method (Section 3.2); this is  */
+/* the textbook Dijkstra-based form with Jonker-Volgenant dual updates.       */
+/* Reduced cost pi(r,c) = (c_rc - u_r) - v_c >= 0; matched edges have 0.      */
+/* Ties always go to the lowest index; relaxations use strict '<'.            */
+/* ------------------------------------------------------------------------ */
+int or_lap(int m, const double* c, const double* u0, double* value, double* u, double* v,
+           int* row_to_col, int* n_aug, long long* n_relax) {
+  if (m <= 0) {
+    if (value) *value = 0.0;
+    if (n_aug) *n_aug = 0;
+    if (n_relax) *n_relax = 0;
+    return OR_OK;
+  }
+  int* col_to_row = (int*)malloc(sizeof(int) * m);
+  int* argrow = (int*)malloc(sizeof(int) * m);
+  int* pred = (int*)malloc(sizeof(int) * m);
+  char* scanned = (char*)malloc(m);
+  double* d = (double*)malloc(sizeof(double) * m);
+  int aug = 0;
+  long long relax = 0;
+
+  /* start duals: u = u0 (or 0), v_c = min_r (c_rc - u_r) */
+  for (int r = 0; r < m; r++) {
+    u[r] = u0 ? u0[r] : 0.0;
+    row_to_col[r] = -1;
+  }
+  for (int col = 0; col < m; col++) {
+    double best = 0.0;
+    int arg = -1;
+    for (int r = 0; r < m; r++) {
+      double x = c[r * m + col] - u[r];
+      if (arg < 0 || x < best) {
+        best = x;
+        arg = r;
+      }
+    }
+    v[col] = best;
+    argrow[col] = arg;
+    col_to_row[col] = -1;
+  }
+  /* greedy pass: column col takes its argmin row if that row is still free */
+  for (int col = 0; col < m; col++) {
+    int r = argrow[col];
+    if (row_to_col[r] < 0) {
+      row_to_col[r] = col;
+      col_to_row[col] = r;
+    }
+  }
+  /* one Dijkstra search per free row, rows in increasing order */
+  for (int i = 0; i < m; i++) {
+    if (row_to_col[i] >= 0) continue;
+    aug++;
+    for (int col = 0; col < m; col++) {
+      d[col] = (c[i * m + col] - u[i]) - v[col];
+      pred[col] = i;
+      scanned[col] = 0;
+    }
+    relax += m;
+    int sink = -1;
+    double dlast = 0.0;
+    for (;;) {
+      int cs = -1;
+      double dm = 0.0;
+      for (int col = 0; col < m; col++) {
+        if (scanned[col]) continue;
+        if (cs < 0 || d[col] < dm) {
+          cs = col;
+          dm = d[col];
+        }
+      }
+      scanned[cs] = 1;
+      if (col_to_row[cs] < 0) {
+        sink = cs;
+        dlast = dm;
+        break;
+      }
+      int r = col_to_row[cs];
+      for (int col = 0; col < m; col++) {
+        if (scanned[col]) continue;
+        double nd = dm + ((c[r * m + col] - u[r]) - v[col]);
+        relax++;
+        if (nd < d[col]) {
+          d[col] = nd;
+          pred[col] = r;
+        }
+      }
+    }
+    /* dual update on the scanned columns */
+    for (int col = 0; col < m; col++)
+      if (scanned[col]) v[col] = v[col] + (d[col] - dlast);
+    /* augment along the predecessor chain back to row i */
+    int col = sink;
+    for (;;) {
+      int r = pred[col];
+      int nxt = row_to_col[r];
+      col_to_row[col] = r;
+      row_to_col[r] = col;
+      if (r == i) break;
+      col = nxt;
+    }
+    /* row duals of matched rows from the tight matched edges */
+    for (int r = 0; r < m; r++)
+      if (row_to_col[r] >= 0) u[r] = c[r * m + row_to_col[r]] - v[row_to_col[r]];
+  }
+  double val = 0.0;
+  for (int r = 0; r < m; r++) val = val + c[r * m + row_to_col[r]];
+  if (value) *value = val;
+  if (n_aug) *n_aug = aug;
+  if (n_relax) *n_relax = relax;
+  free(col_to_row);
+  free(argrow);
+  free(pred);
+  free(scanned);
+  free(d);
+  return OR_OK;
+}
+
+/* Canonical optimal dual of an LAP, given an optimal assignment sigma.
+ * All optimal duals satisfy u_r - u_r' <= c[r][sigma(r')] - c[r'][sigma(r')]
+ * (eliminate v through the tight matched edges).  With u_0 = 0 the pointwise
+ * largest solution is the shortest-path distance from row 0 in the graph with
+ * arcs r' -> r of that weight; computed here by plain Bellman-Ford.  The set of
+ * optimal duals does not depend on which optimal sigma was found, so neither
+ * does this dual.  v_c = c[sigma^-1(c)][c] - u[sigma^-1(c)]. */
+void or_lap_canonical(int m, const double* c, const int* row_to_col, double* u_out, double* v_out) {
+  if (m <= 0) return;
+  char* reached = (char*)calloc(m, 1);
+  u_out[0] = 0.0;
+  reached[0] = 1;
+  for (int r = 1; r < m; r++) u_out[r] = 0.0;
+  for (int round = 0; round < m - 1; round++) {
+    int changed = 0;
+    for (int rp = 0; rp < m; rp++) {
+      if (!reached[rp]) continue;
+      int sp = row_to_col[rp];
+      for (int r = 1; r < m; r++) {
+        if (r == rp) continue;
+        double w = c[r * m + sp] - c[rp * m + sp];
+        double nd = u_out[rp] + w;
+        if (!reached[r] || nd < u_out[r]) {
+          u_out[r] = nd;
+          reached[r] = 1;
+          changed = 1;
+        }
+      }
+    }
+    if (!changed) break;
+  }
+  for (int r = 0; r < m; r++) v_out[row_to_col[r]] = c[r * m + row_to_col[r]] - u_out[r];
+  free(reached);
+}
+
+/* Brute-force LAP over all m! permutations (m <= 9): pins or_lap. */
+static void lap_brute_rec(int m, const double* c, int r, int* perm, char* used, double acc, double* best,
+                          int* bestp) {
+  if (r == m) {
+    if (acc < *best) {
+      *best = acc;
+      memcpy(bestp, perm, sizeof(int) * m);
+    }
+    return;
+  }
+  for (int col = 0; col < m; col++) {
+    if (used[col]) continue;
+    used[col] = 1;
+    perm[r] = col;
+    lap_brute_rec(m, c, r + 1, perm, used, acc + c[r * m + col], best, bestp);
+    used[col] = 0;
+  }
+}
+double or_lap_brute(int m, const double* c, int* best_perm) {
+  int perm[16];
+  char used[16] = {0};
+  int bp[16];
+  double best = INFINITY;
+  if (m <= 0 || m > 10) return NAN;
+  lap_brute_rec(m, c, 0, perm, used, 0.0, &best, bp);
+  if (best_perm) memcpy(best_perm, bp, sizeof(int) * m);
+  return best;
+}
+
+/* QAP objective of a permutation (Eq. 1.1): sum b_i,perm(i) + sum f_ij d_perm(i)perm(j). */
+double or_qap_cost(int n, const double* F, const double* D, const double* B, const int* perm) {
+  double s = 0.0;
+  for (int i = 0; i < n; i++) {
+    if (B) s += B[i * n + perm[i]];
+    for (int j = 0; j < n; j++) s += F[i * n + j] * D[perm[i] * n + perm[j]];
+  }
+  return s;
+}
+
+/* Brute-force QAP optimum over all n! permutations (Heap's algorithm), n <= 11. */
+double or_qap_brute(int n, const double* F, const double* D, const double* B, int* best_perm) {
+  int perm[16], cnt[16];
+  if (n <= 0 || n > 11) return NAN;
+  for (int i = 0; i < n; i++) {
+    perm[i] = i;
+    cnt[i] = 0;
+  }
+  double best = or_qap_cost(n, F, D, B, perm);
+  if (best_perm) memcpy(best_perm, perm, sizeof(int) * n);
+  int i = 1;
+  while (i < n) {
+    if (cnt[i] < i) {
+      int k = (i % 2 == 0) ? 0 : cnt[i];
+      int tmp = perm[k];
+      perm[k] = perm[i];
+      perm[i] = tmp;
+      double s = or_qap_cost(n, F, D, B, perm);
+      if (s < best) {
+        best = s;
+        if (best_perm) memcpy(best_perm, perm, sizeof(int) * n);
+      }
+      cnt[i]++;
+      i = 1;
+    } else {
+      cnt[i] = 0;
+      i++;
+    }
+  }
+  return best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Index helpers                                                              */
+/* ------------------------------------------------------------------------ */
+static inline int cmp1(int j, int i) { return j - (j > i); }              /* j' of j != i */
+static inline int cmp2(int k, int i, int j) { return k - (k > i) - (k > j); } /* k' of k != i,j */
+static inline long long tile_of(int n, int i, int p, int j, int q) {
+  return (((long long)i * n + p) * (n - 1) + cmp1(j, i)) * (n - 1) + cmp1(q, p);
+}
+long long or_num_tiles(int n) { return (long long)n * n * (n - 1) * (n - 1); }
+long long or_num_z(int n) { return or_num_tiles(n) * (n - 2) * (n - 2); }
+
+/* ------------------------------------------------------------------------ */
+/* Setup (Eq. 1.1, 2.1, 2.6; partial assignment = fixed facilities of a       */
+/* branch-and-bound node, Section 4).  Free facilities and free locations are */
+/* renumbered in increasing order.  With a partial assignment phi on A:       */
+/*   b'_ip = b_ip + f_ii d_pp + sum_{a in A} (f_ia d_{p,phi a} + f_ai d_{phi a,p})  */
+/*   const = sum_{a in A} b_{a,phi a} + sum_{a,a' in A} f_aa' d_{phi a,phi a'} */
+/*   C^_ijpq = f_ij d_pq (i != j, p != q), D^ = 0.                           */
+/* ------------------------------------------------------------------------ */
+int or_setup(int n, const double* F, const double* D, const double* B, const int* partial, int* n_res_out,
+             double* cst_out, double* bprime, double* Chat, double* Dhat) {
+  int fac[64], loc[64];
+  int nf = 0, nl = 0;
+  char locused[64] = {0};
+  if (n < 1 || n > 64) return OR_EINVAL;
+  for (int i = 0; i < n; i++) {
+    if (partial && partial[i] >= 0) {
+      if (partial[i] >= n || locused[partial[i]]) return OR_EINVAL;
+      locused[partial[i]] = 1;
+    }
+  }
+  for (int i = 0; i < n; i++)
+    if (!partial || partial[i] < 0) fac[nf++] = i;
+  for (int p = 0; p < n; p++)
+    if (!locused[p]) loc[nl++] = p;
+  if (nf != nl) return OR_EINVAL;
+  int nr = nf;
+  if (n_res_out) *n_res_out = nr;
+  double cst = 0.0;
+  if (partial) {
+    for (int a = 0; a < n; a++) {
+      if (partial[a] < 0) continue;
+      if (B) cst += B[a * n + partial[a]];
+      for (int a2 = 0; a2 < n; a2++) {
+        if (partial[a2] < 0) continue;
+        cst += F[a * n + a2] * D[partial[a] * n + partial[a2]];
+      }
+    }
+  }
+  if (cst_out) *cst_out = cst;
+  for (int ii = 0; ii < nr; ii++) {
+    for (int pp = 0; pp < nr; pp++) {
+      int i = fac[ii], p = loc[pp];
+      double s = (B ? B[i * n + p] : 0.0) + F[i * n + i] * D[p * n + p];
+      if (partial) {
+        for (int a = 0; a < n; a++) {
+          if (partial[a] < 0) continue;
+          s += F[i * n + a] * D[p * n + partial[a]] + F[a * n + i] * D[partial[a] * n + p];
+        }
+      }
+      bprime[ii * nr + pp] = s;
+    }
+  }
+  if (nr >= 2 && Chat) {
+    for (int ii = 0; ii < nr; ii++)
+      for (int jj = 0; jj < nr; jj++) {
+        if (jj == ii) continue;
+        for (int pp = 0; pp < nr; pp++)
+          for (int qq = 0; qq < nr; qq++) {
+            if (qq == pp) continue;
+            Chat[tile_of(nr, ii, pp, jj, qq)] = F[fac[ii] * n + fac[jj]] * D[loc[pp] * n + loc[qq]];
+          }
+      }
+  }
+  if (nr >= 3 && Dhat) memset(Dhat, 0, sizeof(double) * (size_t)or_num_z(nr));
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Stages of one iteration (Algorithm 1, steps 3-5; Figure 1)                 */
+/* ------------------------------------------------------------------------ */
+static void solve_one(int m, const double* cost, const double* u0, int dual_mode, double* value, double* u,
+                      double* v, int* perm, int* aug, long long* relax) {
+  or_lap(m, cost, u0, value, u, v, perm, aug, relax);
+  if (dual_mode == 1) {
+    double* uc = (double*)malloc(sizeof(double) * m);
+    double* vc = (double*)malloc(sizeof(double) * m);
+    or_lap_canonical(m, cost, perm, uc, vc);
+    memcpy(u, uc, sizeof(double) * m);
+    memcpy(v, vc, sizeof(double) * m);
+    free(uc);
+    free(vc);
+  }
+}
+
+/* Z stage: n^2 (n-1)^2 LAPs of size n-2 over the tiles of D^.  u0 (nullable)
+ * holds starting row duals per tile (warm start). */
+void or_stage_z(int n, int dual_mode, const double* Dhat, const double* u0, double* Theta, double* xi, double* psi,
+                long long* naug, long long* nrelax, int nthreads) {
+  long long T = or_num_tiles(n);
+  int m = n - 2;
+  long long aug_tot = 0, relax_tot = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1) reduction(+ : aug_tot, relax_tot)
+#endif
+  for (long long t = 0; t < T; t++) {
+    int perm[64];
+    int aug;
+    long long relax;
+    solve_one(m, Dhat + t * m * m, u0 ? u0 + t * m : NULL, dual_mode, &Theta[t], xi + t * m, psi + t * m, perm,
+              &aug, &relax);
+    aug_tot += aug;
+    relax_tot += relax;
+  }
+  if (naug) *naug = aug_tot;
+  if (nrelax) *nrelax = relax_tot;
+  (void)nthreads;
+}
+
+/* Y stage: n^2 LAPs of size n-1 with cost C^ + Theta (Figure 1, second stage). */
+void or_stage_y(int n, int dual_mode, const double* Chat, const double* Theta, double* Delta, double* gamma,
+                double* delta, long long* naug, long long* nrelax) {
+  int m = n - 1;
+  double* cost = (double*)malloc(sizeof(double) * m * m);
+  long long aug_tot = 0, relax_tot = 0;
+  for (int i = 0; i < n; i++)
+    for (int p = 0; p < n; p++) {
+      long long base = ((long long)i * n + p) * m * m;
+      for (int e = 0; e < m * m; e++) cost[e] = Chat[base + e] + Theta[base + e];
+      int perm[64];
+      int aug;
+      long long relax;
+      solve_one(m, cost, NULL, dual_mode, &Delta[i * n + p], gamma + (i * n + p) * m, delta + (i * n + p) * m,
+                perm, &aug, &relax);
+      aug_tot += aug;
+      relax_tot += relax;
+    }
+  free(cost);
+  if (naug) *naug = aug_tot;
+  if (nrelax) *nrelax = relax_tot;
+}
+
+/* X stage: one LAP of size n with cost b' + Delta; its value is the bound. */
+void or_stage_x(int n, int dual_mode, const double* bprime, const double* Delta, double* lb, double* alpha,
+                double* beta, int* xperm, long long* naug, long long* nrelax) {
+  double* cost = (double*)malloc(sizeof(double) * n * n);
+  for (int e = 0; e < n * n; e++) cost[e] = bprime[e] + Delta[e];
+  int aug;
+  long long relax;
+  solve_one(n, cost, NULL, dual_mode, lb, alpha, beta, xperm, &aug, &relax);
+  free(cost);
+  if (naug) *naug = aug;
+  if (nrelax) *nrelax = relax;
+}
+
+/* Reduced costs (Eq. 2.19 and the constraints of DLRLT2, Eq. 2.13-2.15):
+ * pi_x(ip) = ((b'_ip + Delta_ip) - alpha_i) - beta_p
+ * pi_y(t)  = ((C^_t + Theta_t) - gamma_ip[j']) - delta_ip[q']      */
+void or_reduced_xy(int n, const double* bprime, const double* Delta, const double* alpha, const double* beta,
+                   const double* Chat, const double* Theta, const double* gamma, const double* delta, double* pix,
+                   double* piy) {
+  int m = n - 1;
+  for (int i = 0; i < n; i++)
+    for (int p = 0; p < n; p++) pix[i * n + p] = ((bprime[i * n + p] + Delta[i * n + p]) - alpha[i]) - beta[p];
+  for (int i = 0; i < n; i++)
+    for (int p = 0; p < n; p++)
+      for (int jp = 0; jp < m; jp++)
+        for (int qp = 0; qp < m; qp++) {
+          long long t = (((long long)i * n + p) * m + jp) * m + qp;
+          piy[t] = ((Chat[t] + Theta[t]) - gamma[(i * n + p) * m + jp]) - delta[(i * n + p) * m + qp];
+        }
+}
+
+/* pi_z of one entry: (D^ - xi_k') - psi_r'. */
+static inline double piz_at(int n, const double* Dhat, const double* xi, const double* psi, int i, int j, int k, int p,
+                            int q, int r) {
+  int m = n - 2;
+  long long t = tile_of(n, i, p, j, q);
+  int kk = cmp2(k, i, j), rr = cmp2(r, p, q);
+  return (Dhat[t * m * m + kk * m + rr] - xi[t * m + kk]) - psi[t * m + rr];
+}
+static inline long long zidx(int n, int i, int j, int k, int p, int q, int r) {
+  int m = n - 2;
+  return tile_of(n, i, p, j, q) * m * m + cmp2(k, i, j) * m + cmp2(r, p, q);
+}
+
+/* z redistribution (Types 1-3 combined, Eq. 2.20, 2.22, 2.23 and Eq. 2.25 in
+ * the proof of Theorem 1), applied to D^ in place (Section 3.3).
+ * prm = {kz, ky, kx, phi_y, phi_1..phi_5}.  The member a=(i,j,k,p,q,r) gives
+ * phi_l * s(a) to its l-th partner, partners listed as in Eq. 2.20:
+ *   1:(i,k,j,p,r,q) 2:(j,i,k,q,p,r) 3:(j,k,i,q,r,p) 4:(k,i,j,r,p,q) 5:(k,j,i,r,q,p).
+ * Seen from the receiver a, the partners b1..b5 (same list) give it
+ * phi_1, phi_2, phi_4, phi_3, phi_5 respectively (the two 3-cycles are each
+ * other's inverse; the swaps are their own inverse). */
+void or_redistribute_z(int n, const double* prm, double* Dhat, const double* xi, const double* psi, const double* piy,
+                       const double* pix, int nthreads) {
+  double kz = prm[0], cy = prm[1] / (double)(n - 2), cx = prm[2] / ((double)(n - 1) * (double)(n - 2));
+  const double* phi = prm + 4;
+  /* members of a class as position orders of the triple (i,j,k)/(p,q,r):
+   * member 0 = a itself, members 1..5 = the partners b1..b5 of Eq. 2.20 */
+  static const int M[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  /* pmap[a][l] = which member is the l-th partner of member a (apply M[l+1] to a's order) */
+  int pmap[6][5];
+  for (int a = 0; a < 6; a++)
+    for (int l = 0; l < 5; l++) {
+      int comp[3] = {M[a][M[l + 1][0]], M[a][M[l + 1][1]], M[a][M[l + 1][2]]};
+      for (int b = 0; b < 6; b++)
+        if (M[b][0] == comp[0] && M[b][1] == comp[1] && M[b][2] == comp[2]) pmap[a][l] = b;
+    }
+  /* gives[a][b] = weight member a gives to member b */
+  double gives[6][6];
+  for (int a = 0; a < 6; a++) {
+    for (int b = 0; b < 6; b++) gives[a][b] = 0.0;
+    for (int l = 0; l < 5; l++) gives[a][pmap[a][l]] = phi[l];
+  }
+  int ntrip = 0;
+  int(*trip)[3] = (int(*)[3])malloc(sizeof(int[3]) * (size_t)(n * n * n / 6 + 1));
+  for (int i = 0; i < n; i++)
+    for (int j = i + 1; j < n; j++)
+      for (int k = j + 1; k < n; k++) {
+        trip[ntrip][0] = i;
+        trip[ntrip][1] = j;
+        trip[ntrip][2] = k;
+        ntrip++;
+      }
+  /* one canonical class {(i,p),(j,q),(k,r)} with i<j<k at a time: all six s
+   * values come from the unmodified snapshot, then the six entries are written */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (int tr = 0; tr < ntrip; tr++) {
+    int f[3] = {trip[tr][0], trip[tr][1], trip[tr][2]};
+    for (int p = 0; p < n; p++)
+      for (int q = 0; q < n; q++) {
+        if (q == p) continue;
+        for (int r = 0; r < n; r++) {
+          if (r == p || r == q) continue;
+          int l3[3] = {p, q, r};
+          double s[6];
+          long long idx[6];
+          for (int a = 0; a < 6; a++) {
+            int fi = f[M[a][0]], fj = f[M[a][1]], fk = f[M[a][2]];
+            int li = l3[M[a][0]], lj = l3[M[a][1]], lk = l3[M[a][2]];
+            double pz = piz_at(n, Dhat, xi, psi, fi, fj, fk, li, lj, lk);
+            double ty = cy * piy[tile_of(n, fi, li, fj, lj)] + cx * pix[fi * n + li];
+            s[a] = kz * pz + ty;
+            idx[a] = zidx(n, fi, fj, fk, li, lj, lk);
+          }
+          double newv[6];
+          for (int a = 0; a < 6; a++) {
+            /* inflow from a's partners b1..b5, summed in that order */
+            double inflow = 0.0;
+            for (int l = 0; l < 5; l++) {
+              int b = pmap[a][l];
+              double term = gives[b][a] * s[b];
+              inflow = (l == 0) ? term : inflow + term;
+            }
+            newv[a] = (Dhat[idx[a]] - s[a]) + inflow;
+          }
+          for (int a = 0; a < 6; a++) Dhat[idx[a]] = newv[a];
+        }
+      }
+  }
+  free(trip);
+}
+
+/* y redistribution (Type 1 rule for y, Eq. 2.21) in place on C^:
+ * C^'_ijpq = (C^_ijpq - phi_y pi_y(ijpq)) + phi_y pi_y(jiqp). */
+void or_redistribute_y(int n, double phi_y, double* Chat, const double* piy) {
+  long long T = or_num_tiles(n);
+  double* out = (double*)malloc(sizeof(double) * T);
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < n; j++) {
+      if (j == i) continue;
+      for (int p = 0; p < n; p++)
+        for (int q = 0; q < n; q++) {
+          if (q == p) continue;
+          long long t = tile_of(n, i, p, j, q), tp = tile_of(n, j, q, i, p);
+          out[t] = (Chat[t] - phi_y * piy[t]) + phi_y * piy[tp];
+        }
+    }
+  memcpy(Chat, out, sizeof(double) * T);
+  free(out);
+}
+
+/* Feasibility check (Section 2.3, after Algorithm 1): build y and z from the
+ * X-LAP primal and test complementary slackness (Eq. 2.19) for them. */
+int or_feasibility(int n, const int* xperm, const double* piy, const double* Dhat, const double* xi, const double* psi,
+                   double tol) {
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < n; j++) {
+      if (j == i) continue;
+      if (fabs(piy[tile_of(n, i, xperm[i], j, xperm[j])]) > tol) return 0;
+      for (int k = 0; k < n; k++) {
+        if (k == i || k == j) continue;
+        if (fabs(piz_at(n, Dhat, xi, psi, i, j, k, xperm[i], xperm[j], xperm[k])) > tol) return 0;
+      }
+    }
+  return 1;
+}
+
+/* One S1 iteration (Algorithm 1 steps 3-5, then the ascent step).
+ * prm = {kz, ky, kx, phi_y, phi_1..phi_5}; stats[6] = {aug,relax} for Z, Y, X. */
+int or_iterate(int n, const double* prm, int dual_mode, const double* bprime, double* Chat, double* Dhat,
+               const double* u0z, double* lb, double* Theta, double* xi, double* psi, double* Delta, double* gamma,
+               double* delta, double* alpha, double* beta, int* xperm, double* pix, double* piy, long long* stats,
+               int nthreads) {
+  if (n < 3) return OR_EINVAL;
+  long long st[6] = {0, 0, 0, 0, 0, 0};
+  or_stage_z(n, dual_mode, Dhat, u0z, Theta, xi, psi, &st[0], &st[1], nthreads);
+  or_stage_y(n, dual_mode, Chat, Theta, Delta, gamma, delta, &st[2], &st[3]);
+  or_stage_x(n, dual_mode, bprime, Delta, lb, alpha, beta, xperm, &st[4], &st[5]);
+  or_reduced_xy(n, bprime, Delta, alpha, beta, Chat, Theta, gamma, delta, pix, piy);
+  or_redistribute_z(n, prm, Dhat, xi, psi, piy, pix, nthreads);
+  or_redistribute_y(n, prm[3], Chat, piy);
+  if (stats) memcpy(stats, st, sizeof st);
+  return OR_OK;
+}
+
+int or_have_openmp(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 0;
+#endif
+}
