@@ -1,0 +1,181 @@
+/*
+ * rlt2.h -- C ABI of the GB300 (sm_103a) RLT2 dual-ascent library.
+ *
+ * Lower bounds for the Quadratic Assignment Problem by Lagrangian dual ascent
+ * on the level-2 RLT formulation (Date & Nagi, arXiv:1710.03732).  Problem
+ * statement: Section 1, Eq. 1.1-1.4 (flow F, distance D, fixed cost B);
+ * RLT2 and its Lagrangian dual: Section 2.3, Eq. 2.6-2.16; the three-stage
+ * LAP decomposition: Figure 1 and the Theta/Delta definitions after it; the
+ * ascent rules: Eq. 2.20-2.23 and their combination in the proof of
+ * Theorem 1; the iteration: Algorithm 1 / Algorithm 2 (S1 variant).
+ *
+ * General conventions
+ *  - Every function returns an rlt2_status; nothing throws or aborts.
+ *  - All floating point is IEEE FP64.  Matrices are row-major, n x n.
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    global memory of the current device.  Inputs are borrowed for the
+ *    duration of the call only (copied where kept); outputs are written into
+ *    caller-owned buffers of the documented length.
+ *  - The library owns every buffer it allocates inside a context and frees it
+ *    in rlt2_destroy.  All GPU work of a context runs on the stream given at
+ *    creation (a cudaStream_t passed as void*; NULL = legacy default stream).
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *  - Sizes: 3 <= n (after removing fixed facilities) and n <= 32.
+ *
+ * Array layouts (residual size n, m = n-2; compressed index of j != i is
+ * j' = j - (j > i), of k != i,j is k' = k - (k > i) - (k > j); same for
+ * locations):
+ *   tile t(i,p,j',q') = ((i*n + p)*(n-1) + j')*(n-1) + q',  T = n^2 (n-1)^2 tiles
+ *   C^[t] (y costs, Section 3.3), pi_y[t]
+ *   D^[t*m*m + k'*m + r'] (z costs, E = T*m*m entries)
+ *   xi[t*m + k'], psi[t*m + r']              (Z-LAP duals, Eq. 2.15)
+ *   gamma[(i*n+p)*(n-1) + j'], delta[(i*n+p)*(n-1) + q']  (Y-LAP duals)
+ *   alpha[i], beta[p] (X-LAP duals), pi_x[i*n + p]
+ */
+#ifndef RLT2_H
+#define RLT2_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RLT2_OK = 0,
+  RLT2_EINVAL = 1,   /* bad argument: NULL, size out of range, non-finite input, bad parameters */
+  RLT2_ENOMEM = 2,   /* device allocation failed or the memory budget is too small */
+  RLT2_ECUDA = 3,    /* a CUDA call failed; rlt2_last_error() has the message */
+  RLT2_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+  RLT2_EADMIT = 5    /* a node does not fit the memory budget even alone */
+} rlt2_status;
+
+/* Dual-ascent parameters.
+ *  kz, ky, kx : kappa^z, kappa^y, kappa^x of Eq. 2.20, 2.22, 2.23, each in [0,1]
+ *  phi_y      : varphi of Eq. 2.21 (y_ijpq <-> y_jiqp), in [0,1], phi_y + ky <= 1
+ *  phi_z[5]   : phi_1..phi_5 of Eq. 2.20 (used by rules 1-3), each in [0,1],
+ *               summing to 1 within 1e-12
+ *  dual_mode  : 0 = the Hungarian's own duals, 1 = canonical duals (the
+ *               pointwise-largest optimal row duals with u_0 = 0; unique for a
+ *               given cost matrix, so warm and cold solves agree)
+ *  warm       : 0 = cold Z-LAPs, 1 = start each Z-LAP from its previous
+ *               iteration's row duals (column-min repair keeps them feasible)
+ *  min_gap    : stop once (UB - LB)/UB < min_gap (needs ub > 0 or a found UB)
+ *  ub         : known upper bound on the node's QAP value (<= 0: unknown)
+ *  feas_tol   : tolerance of the feasibility check after Algorithm 1
+ *               (relative to max(1, |LB|)); the check stops the ascent when
+ *               every y and z of the X-LAP primal has |reduced cost| <= tol */
+typedef struct rlt2_params {
+  double kz, ky, kx, phi_y;
+  double phi_z[5];
+  int dual_mode;
+  int warm;
+  double min_gap;
+  double ub;
+  double feas_tol;
+} rlt2_params;
+
+typedef struct rlt2_ctx rlt2_ctx;
+
+/* Default parameters: kz = kx = 1, ky = 1/2, phi_y = 1/2, phi_z = 1/5 each,
+ * canonical duals, cold start, min_gap = 0, ub unknown, feas_tol = 1e-9. */
+void rlt2_params_default(rlt2_params* p);
+
+/* Create a dual-ascent context for one QAP node (Eq. 1.1; a branch-and-bound
+ * node fixes some facilities, Section 4).
+ *  n        : problem size, 3 <= n - (#fixed) and n <= 64 (residual <= 32)
+ *  F, D     : host, n*n flow and distance matrices (finite)
+ *  B        : host, n*n fixed costs, or NULL for B = 0
+ *  partial  : host, n ints, partial[i] = location of facility i or -1 (free);
+ *             NULL = root node.  Must be injective.
+ *  p        : host parameters (NULL = defaults); copied
+ *  stream   : cudaStream_t used for all work of this context
+ *  out      : receives the context (NULL on failure)
+ * Multipliers start at 0 (Algorithm 1 step 1), so the first iteration's bound
+ * is the Gilmore-Lawler bound.  Errors: EINVAL, ENOMEM, ECUDA. */
+rlt2_status rlt2_create(int n, const double* F, const double* D, const double* B, const int* partial,
+                        const rlt2_params* p, void* stream, rlt2_ctx** out);
+
+/* Run up to `iters` iterations of S1 RLT2-DA (Algorithm 1 / 2): the ascent
+ * step from the previous iteration's reduced costs (if any), then the Z, Y and
+ * X LAP stages.  After return, the bound, duals, reduced costs and state all
+ * belong to the same multipliers (the last solved ones).
+ *  lb_hist : host, iters doubles (nullable): bound of each iteration
+ *            (including the fixed facilities' constant); entries after an
+ *            early stop are set to NaN
+ *  done    : host (nullable): receives the number of iterations performed
+ * Stops early (returns OK) once the feasibility check or min_gap fires.
+ * Synchronises the context's stream before returning. */
+rlt2_status rlt2_iterate(rlt2_ctx* ctx, int iters, double* lb_hist, int* done);
+
+/* Enqueue `iters` iterations without synchronising or reading anything back
+ * (for timing and for callers that overlap work).  The bounds can be read
+ * later with rlt2_bound. */
+rlt2_status rlt2_iterate_async(rlt2_ctx* ctx, int iters);
+
+/* Bounds of the last solve (host outputs, each nullable):
+ *  lb      : bound of the last iteration;  best_lb : best bound so far
+ *  ub      : best upper bound seen (QAP value of an X-LAP primal), or +inf
+ *  perm    : n ints (full problem), location of every facility in the last
+ *            X-LAP primal (fixed facilities keep their location)
+ *  ub_perm : n ints, the permutation whose value is ub (same convention)
+ *  iters   : iterations performed so far. Synchronises the stream. */
+rlt2_status rlt2_bound(rlt2_ctx* ctx, double* lb, double* best_lb, double* ub, int* perm, int* ub_perm,
+                       int* iters);
+
+/* Duals of the last solve (Section 2.3: alpha, beta of Eq. 1.2-1.3; gamma,
+ * delta of Eq. 2.2-2.3; xi, psi of Eq. 2.7-2.8).  Lengths: alpha, beta: n;
+ * gamma, delta: n*n*(n-1); xi, psi: T*(n-2).  Any pointer may be NULL.
+ * on_device != 0: the pointers are device memory (copied on the stream). */
+rlt2_status rlt2_duals(rlt2_ctx* ctx, double* alpha, double* beta, double* gamma, double* delta, double* xi,
+                       double* psi, int on_device);
+
+/* Reduced costs of the last solve (Eq. 2.19 and the DLRLT2 constraints):
+ *  pi_x: n*n, pi_y: T, pi_z: E = T*(n-2)^2; each nullable. */
+rlt2_status rlt2_reduced_costs(rlt2_ctx* ctx, double* pi_x, double* pi_y, double* pi_z, int on_device);
+
+/* Checkpoint / restore of the multiplier-adjusted costs (Section 3.3: the
+ * multipliers live inside D^ and C^).  Dhat: E doubles, Chat: T doubles.
+ * Import discards the pending ascent step, so the next iteration solves the
+ * imported costs directly. */
+rlt2_status rlt2_export_state(rlt2_ctx* ctx, double* Dhat, double* Chat, int on_device);
+rlt2_status rlt2_import_state(rlt2_ctx* ctx, const double* Dhat, const double* Chat, int on_device);
+
+/* Counters since creation, out[8] = {iterations, Z augmentations, Z relaxations,
+ * Y augmentations, Y relaxations, X augmentations, X relaxations, stopped}. */
+rlt2_status rlt2_stats(rlt2_ctx* ctx, long long* out);
+
+/* Sizes: *T = n^2 (n-1)^2, *E = T (n-2)^2, *n_res = residual n, *cst = constant
+ * of the fixed facilities (each nullable). */
+rlt2_status rlt2_sizes(rlt2_ctx* ctx, int* n_res, long long* T, long long* E, double* cst);
+
+/* Per-kernel timing with CUDA events on the context's stream (disables CUDA
+ * graph replay while on).  rlt2_kernel_times fills ms[k] (total milliseconds)
+ * and count[k] (launches) for k = 0..nk-1 in the order
+ * {move_y, move_z, lap_z, lap_y, lap_x, finalize}; synchronises. */
+rlt2_status rlt2_set_timing(rlt2_ctx* ctx, int on);
+rlt2_status rlt2_kernel_times(rlt2_ctx* ctx, double* ms, long long* count, int nk);
+
+rlt2_status rlt2_destroy(rlt2_ctx* ctx);
+
+/* Batched LAPs, one warp per LAP (the tiled-LAP idea of Section 3.2: many
+ * small LAPs solved in one launch).
+ *  batch, m : number of LAPs and their size, 1 <= m <= 32
+ *  cost     : device, batch*m*m, LAP b at cost + b*m*m, row-major
+ *  u0       : device, batch*m starting row duals, or NULL (cold start)
+ *  value    : device, batch optimal values (sum of the assigned costs)
+ *  u, v     : device, batch*m row / column duals (nullable)
+ *  row_to_col: device, batch*m assignment (nullable)
+ *  n_aug    : device, batch augmenting searches per LAP (nullable)
+ *  dual_mode: 0 raw, 1 canonical.  Asynchronous on `stream`. */
+rlt2_status rlt2_lap_batched(int batch, int m, const double* cost, const double* u0, double* value, double* u,
+                             double* v, int* row_to_col, int* n_aug, int dual_mode, void* stream);
+
+/* Human-readable name of a status, and the last error message of this thread. */
+const char* rlt2_strerror(rlt2_status s);
+const char* rlt2_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RLT2_H */

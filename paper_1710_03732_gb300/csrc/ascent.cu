@@ -1,0 +1,928 @@
+// RLT2 dual ascent on one GPU: context, setup, ascent moves, stage driver and C ABI.
+//
+// One iteration (Algorithm 2, S1 variant, one GPU, no MPI) is six kernels on the
+// context's stream, captured once into a CUDA graph and replayed:
+//   k_move_y   per tile: pending y move (Eq. 2.21) and the tile term
+//              cy*pi_y + cx*pi_x that rules 2 and 3 (Eq. 2.22, 2.23) add to every z
+//   k_move_z   class-owned z move (Eq. 2.20 + 2.22 + 2.23, combined as in the
+//              proof of Theorem 1), in place on D^ (Section 3.3)
+//   k_lap(Z)   n^2 (n-1)^2 LAPs of size n-2 on the tiles of D^
+//   k_lap(Y)   n^2 LAPs of size n-1 on C^ + Theta (fold fused into the tile load),
+//              writes pi_y
+//   k_lap(X)   one LAP of size n on b' + Delta, writes pi_x
+//   k_finalize bound, best bound, upper bound of the X primal, the feasibility
+//              check that follows Algorithm 1, stop flags, bound history
+// The ascent step of iteration m runs at the start of iteration m+1, so after
+// every call the state, duals and reduced costs describe the same multipliers.
+// Device-side flags (done / have_snapshot) make every kernel a no-op after a
+// stop, so whole batches of iterations can be enqueued without host round trips.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rlt2_internal.h"
+
+namespace rlt2 {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+rlt2_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return RLT2_ECUDA;
+}
+
+constexpr int kRing = 1 << 16;
+constexpr int kKinds = 6;
+
+struct DevScalars {
+  double lb, best_lb, ub, gap;
+  int iter, done, have_snap, reason;
+  unsigned long long stats[6];  // Z aug, Z relax, Y aug, Y relax, X aug, X relax
+};
+
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+
+// ------------------------------------------------------------------ setup ----
+// b'_ip = b_ip + f_ii d_pp + sum_{a fixed} (f_ia d_{p,phi a} + f_ai d_{phi a,p})
+// (Eq. 1.1 with the fixed facilities of a branch-and-bound node moved into b),
+// plus the residual F and D used for the upper bound.
+__global__ void k_setup_b(int n, int nr, const double* F, const double* D, const double* B, const int* fac,
+                          const int* loc, const int* fixf, const int* fixl, int nfix, double* bprime, double* Fr,
+                          double* Dr) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nr * nr) return;
+  const int ii = e / nr, pp = e - ii * nr;
+  const int i = fac[ii], p = loc[pp];
+  double s = dadd(B ? B[i * n + p] : 0.0, dmul(F[i * n + i], D[p * n + p]));
+  for (int x = 0; x < nfix; ++x) {
+    const int a = fixf[x], pa = fixl[x];
+    s = dadd(s, dadd(dmul(F[i * n + a], D[p * n + pa]), dmul(F[a * n + i], D[pa * n + p])));
+  }
+  bprime[e] = s;
+  Fr[e] = F[fac[ii] * n + fac[pp]];
+  Dr[e] = D[loc[ii] * n + loc[pp]];
+}
+
+// const = sum_a b_{a,phi a} + sum_{a,a'} f_aa' d_{phi a, phi a'} over fixed facilities.
+__global__ void k_setup_const(int n, const double* F, const double* D, const double* B, const int* fixf,
+                              const int* fixl, int nfix, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double c = 0.0;
+  for (int x = 0; x < nfix; ++x) {
+    const int a = fixf[x], pa = fixl[x];
+    if (B) c = dadd(c, B[a * n + pa]);
+    for (int y = 0; y < nfix; ++y) c = dadd(c, dmul(F[a * n + fixf[y]], D[pa * n + fixl[y]]));
+  }
+  *out = c;
+}
+
+// C^_ijpq = f_ij d_pq on the tile layout (RLT1 cost, Eq. 2.1).
+__global__ void k_setup_c(int nr, long long T, const double* Fr, const double* Dr, double* Chat) {
+  const int n1 = nr - 1;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < T; t += (long long)gridDim.x * blockDim.x) {
+    const int ip = (int)(t / (n1 * n1));
+    const int rem = (int)(t - (long long)ip * n1 * n1);
+    const int jj = rem / n1, qq = rem - jj * n1;
+    const int i = ip / nr, p = ip - i * nr;
+    const int j = jj + (jj >= i), q = qq + (qq >= p);
+    Chat[t] = dmul(Fr[i * nr + j], Dr[p * nr + q]);
+  }
+}
+
+// ------------------------------------------------------------------ moves ----
+// Per tile (i,p,j,q): the pending y move of Eq. 2.21 on C^ and the term
+// cy*pi_y(ijpq) + cx*pi_x(ip) that rules 2 and 3 add to each z of the tile.
+__global__ void k_move_y(int n, long long T, double cy, double cx, double phi_y, const double* __restrict__ piy,
+                         const double* __restrict__ pix, double* __restrict__ Chat, double* __restrict__ tterm,
+                         const DevScalars* sc) {
+  if (!sc->have_snap || sc->done) return;
+  const int n1 = n - 1;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < T; t += (long long)gridDim.x * blockDim.x) {
+    const int ip = (int)(t / (n1 * n1));
+    const int rem = (int)(t - (long long)ip * n1 * n1);
+    const int jj = rem / n1, qq = rem - jj * n1;
+    const int i = ip / n, p = ip - i * n;
+    const int j = jj + (jj >= i), q = qq + (qq >= p);
+    const long long tp = ((long long)(j * n + q) * n1 + (i - (i > j))) * n1 + (p - (p > q));
+    const double py = piy[t];
+    tterm[t] = dadd(dmul(cy, py), dmul(cx, pix[ip]));
+    Chat[t] = dadd(dsub(Chat[t], dmul(phi_y, py)), dmul(phi_y, piy[tp]));
+  }
+}
+
+// The six members of a class {(i,p),(j,q),(k,r)} are the position orders of the
+// triples, member 0 = (i,j,k | p,q,r) and members 1..5 = its partners 1..5 in
+// the order of Eq. 2.20: (i,k,j|p,r,q), (j,i,k|q,p,r), (j,k,i|q,r,p),
+// (k,i,j|r,p,q), (k,j,i|r,q,p).
+// kOrd[b] is member b's order; kPart[a][l] is the member that is the l-th
+// partner of member a (apply order l+1 to member a's order).  The weight that
+// partner gives back to member a is phi_{h_widx[l]}: the swaps are their own
+// inverse and the two 3-cycles are each other's inverse.
+#define RLT2_CLASS_TABLES                                                                              \
+  constexpr int kOrd[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};      \
+  constexpr int kPart[6][5] = {{1, 2, 3, 4, 5}, {0, 4, 5, 2, 3}, {3, 0, 1, 5, 4},                    \
+                               {2, 5, 4, 0, 1}, {5, 1, 0, 3, 2}, {4, 3, 2, 1, 0}};
+static const int h_widx[5] = {0, 1, 3, 2, 4};
+
+struct MoveZArgs {
+  int n, m;
+  double kz;
+  double w[5];  // weight received from partner l (phi permuted by h_widx)
+  int kz_one;   // kz == 1: kz*x == x exactly, skip the product
+  int uniform;  // all phi equal: each s_b is scaled once
+  double* Dhat;
+  const double* xi;
+  const double* psi;
+  const double* tterm;
+  const int* trips;  // i | j<<8 | k<<16 with i<j<k
+  const DevScalars* sc;
+};
+
+// One thread per class; a block covers one facility triple and one location p
+// of its first facility (all (q, r)).  Consecutive threads take consecutive r,
+// so members (i,j,k|p,q,r) and (j,i,k|q,p,r) are read and written as contiguous
+// rows; the other four members' rows are shared by the block or by the n blocks
+// of the same triple, which run back to back.
+__global__ void __launch_bounds__(128) k_move_z(MoveZArgs a) {
+  if (!a.sc->have_snap || a.sc->done) return;
+  RLT2_CLASS_TABLES
+  const int n = a.n, m = a.m, n1 = n - 1;
+  const int tr = blockIdx.x / n, p = blockIdx.x - tr * n;
+  const int packed = a.trips[tr];
+  const int F3[3] = {packed & 255, (packed >> 8) & 255, packed >> 16};
+  const int npairs = n1 * m;
+  const long long mm = (long long)m * m;
+  for (int c = threadIdx.x; c < npairs; c += blockDim.x) {
+    const int qq = c / m, rr = c - qq * m;
+    const int q = qq + (qq >= p);
+    const int lo = p < q ? p : q, hi = p < q ? q : p;
+    int r = rr;
+    r += (r >= lo);
+    r += (r >= hi);
+    const int L3[3] = {p, q, r};
+    double s[6], Dv[6];
+    long long idx[6];
+#pragma unroll
+    for (int b = 0; b < 6; ++b) {
+      const int f0 = F3[kOrd[b][0]], f1 = F3[kOrd[b][1]], f2 = F3[kOrd[b][2]];
+      const int l0 = L3[kOrd[b][0]], l1 = L3[kOrd[b][1]], l2 = L3[kOrd[b][2]];
+      const long long t = ((long long)(f0 * n + l0) * n1 + (f1 - (f1 > f0))) * n1 + (l1 - (l1 > l0));
+      const int kr = f2 - (f2 > f0) - (f2 > f1), cc = l2 - (l2 > l0) - (l2 > l1);
+      idx[b] = t * mm + kr * m + cc;
+      Dv[b] = a.Dhat[idx[b]];
+      const double pz = dsub(dsub(Dv[b], __ldg(a.xi + t * m + kr)), __ldg(a.psi + t * m + cc));
+      s[b] = dadd(a.kz_one ? pz : dmul(a.kz, pz), __ldg(a.tterm + t));
+    }
+    if (a.uniform) {
+      double ws[6];
+#pragma unroll
+      for (int b = 0; b < 6; ++b) ws[b] = dmul(a.w[0], s[b]);
+#pragma unroll
+      for (int b = 0; b < 6; ++b) {
+        double in = ws[kPart[b][0]];
+#pragma unroll
+        for (int l = 1; l < 5; ++l) in = dadd(in, ws[kPart[b][l]]);
+        a.Dhat[idx[b]] = dadd(dsub(Dv[b], s[b]), in);
+      }
+    } else {
+#pragma unroll
+      for (int b = 0; b < 6; ++b) {
+        double in = dmul(a.w[0], s[kPart[b][0]]);
+#pragma unroll
+        for (int l = 1; l < 5; ++l) in = dadd(in, dmul(a.w[l], s[kPart[b][l]]));
+        a.Dhat[idx[b]] = dadd(dsub(Dv[b], s[b]), in);
+      }
+    }
+  }
+}
+
+// pi_z = (D^ - xi_k') - psi_r' for every z entry (reduced costs on demand).
+__global__ void k_pi_z(long long E, int m, const double* Dhat, const double* xi, const double* psi, double* out) {
+  const long long mm = (long long)m * m;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < E; e += (long long)gridDim.x * blockDim.x) {
+    const long long t = e / mm;
+    const int w = (int)(e - t * mm);
+    const int k = w / m, r = w - k * m;
+    out[e] = dsub(dsub(Dhat[e], xi[t * m + k]), psi[t * m + r]);
+  }
+}
+
+// ---------------------------------------------------------------- finalize ----
+struct FinArgs {
+  int n, m;
+  const double* cst;
+  const double* xval;
+  const int* xperm;
+  int* ubperm;
+  const double* piy;
+  const double* Dhat;
+  const double* xi;
+  const double* psi;
+  const double* Fr;
+  const double* Dr;
+  const double* bprime;
+  double* ring;
+  double min_gap, ub_known, feas_tol;
+  DevScalars* sc;
+};
+
+__global__ void k_finalize(FinArgs a) {
+  if (a.sc->done) return;
+  __shared__ double red[256];
+  __shared__ int bad, improve;
+  const int n = a.n, m = a.m, n1 = n - 1, tid = threadIdx.x;
+  const double lb = dadd(*a.cst, a.xval[0]);
+  if (tid == 0) bad = (a.feas_tol > 0.0) ? 0 : 1;
+  // residual QAP value of the X-LAP primal (an upper bound)
+  double part = 0.0;
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    const int si = a.xperm[i], sj = a.xperm[j];
+    part += (i == j) ? a.bprime[i * n + si] : a.Fr[i * n + j] * a.Dr[si * n + sj];
+  }
+  red[tid] = part;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (tid < s) red[tid] += red[tid + s];
+    __syncthreads();
+  }
+  const double ub = *a.cst + red[0];
+  // feasibility check: every y and z built from the X primal has zero slack (Eq. 2.19)
+  if (a.feas_tol > 0.0) {
+    const double tol = a.feas_tol * fmax(1.0, fabs(lb));
+    for (int e = tid; e < n * n1; e += blockDim.x) {
+      const int i = e / n1, jj = e - i * n1, j = jj + (jj >= i);
+      const int si = a.xperm[i], sj = a.xperm[j];
+      const long long t = ((long long)(i * n + si) * n1 + jj) * n1 + (sj - (sj > si));
+      if (fabs(a.piy[t]) > tol) bad = 1;
+    }
+    const int per = n1 * m;
+    for (int e = tid; e < n * per; e += blockDim.x) {
+      if (bad) break;
+      const int i = e / per, w = e - i * per, jj = w / m, kk = w - jj * m;
+      const int j = jj + (jj >= i);
+      const int lo = i < j ? i : j, hi = i < j ? j : i;
+      int k = kk;
+      k += (k >= lo);
+      k += (k >= hi);
+      const int si = a.xperm[i], sj = a.xperm[j], sk = a.xperm[k];
+      const long long t = ((long long)(i * n + si) * n1 + jj) * n1 + (sj - (sj > si));
+      const int rc = sk - (sk > si) - (sk > sj);
+      const double pz = dsub(dsub(a.Dhat[t * m * m + (long long)kk * m + rc], a.xi[t * m + kk]), a.psi[t * m + rc]);
+      if (fabs(pz) > tol) bad = 1;
+    }
+  }
+  if (tid == 0) improve = ub < a.sc->ub;
+  __syncthreads();
+  if (improve)
+    for (int i = tid; i < n; i += blockDim.x) a.ubperm[i] = a.xperm[i];
+  if (tid == 0) {
+    DevScalars* sc = a.sc;
+    sc->lb = lb;
+    if (sc->iter == 0 || lb > sc->best_lb) sc->best_lb = lb;
+    if (improve) sc->ub = ub;
+    const int it = sc->iter;
+    a.ring[it & (kRing - 1)] = lb;
+    sc->iter = it + 1;
+    sc->have_snap = 1;
+    double ubk = sc->ub;
+    if (a.ub_known > 0.0 && a.ub_known < ubk) ubk = a.ub_known;
+    sc->gap = (ubk - sc->best_lb) / fabs(ubk);
+    if (!bad) {
+      sc->done = 1;
+      sc->reason = 1;
+    } else if (a.min_gap > 0.0 && sc->gap < a.min_gap) {
+      sc->done = 1;
+      sc->reason = 2;
+    }
+  }
+}
+
+}  // namespace rlt2
+
+using namespace rlt2;
+
+// ------------------------------------------------------------------ context ---
+struct rlt2_ctx {
+  int n_full = 0, n = 0, m = 0;
+  long long T = 0, E = 0;
+  rlt2_params prm{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::vector<int> fac, loc;  // free facilities / locations (host)
+  std::vector<int> fixf, fixl;
+  double* d_cst = nullptr;
+  double *Fr = nullptr, *Dr = nullptr, *bprime = nullptr, *Chat = nullptr, *Dhat = nullptr;
+  double *Theta = nullptr, *xi = nullptr, *psi = nullptr, *Delta = nullptr, *gamma = nullptr, *delta = nullptr;
+  double *alpha = nullptr, *beta = nullptr, *pix = nullptr, *piy = nullptr, *tterm = nullptr, *xval = nullptr;
+  double* ring = nullptr;
+  int *xperm = nullptr, *ubperm = nullptr, *trips = nullptr;
+  int ntrip = 0;
+  DevScalars* sc = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;  // timing mode: 2 events per kernel launch
+  double kms[kKinds] = {0, 0, 0, 0, 0, 0};
+  long long kcount[kKinds] = {0, 0, 0, 0, 0, 0};
+  int iter_host = 0;
+  double cst_host = 0.0;
+};
+
+static void ctx_free(rlt2_ctx* c) {
+  if (!c) return;
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (auto e : c->ev) cudaEventDestroy(e);
+  void* ptrs[] = {c->d_cst, c->Fr,    c->Dr,   c->bprime, c->Chat, c->Dhat,  c->Theta, c->xi,
+                  c->psi,   c->Delta, c->gamma, c->delta, c->alpha, c->beta, c->pix,   c->piy,
+                  c->tterm, c->xval,  c->ring, c->xperm,  c->ubperm, c->trips, c->sc};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}
+
+static bool finite_all(const double* x, size_t k) {
+  for (size_t i = 0; i < k; ++i)
+    if (!std::isfinite(x[i])) return false;
+  return true;
+}
+
+extern "C" void rlt2_params_default(rlt2_params* p) {
+  if (!p) return;
+  p->kz = 1.0;
+  p->ky = 0.5;
+  p->kx = 1.0;
+  p->phi_y = 0.5;
+  for (int l = 0; l < 5; ++l) p->phi_z[l] = 0.2;
+  p->dual_mode = 1;
+  p->warm = 0;
+  p->min_gap = 0.0;
+  p->ub = 0.0;
+  p->feas_tol = 1e-9;
+}
+
+static bool params_ok(const rlt2_params& p) {
+  auto in01 = [](double x) { return std::isfinite(x) && x >= 0.0 && x <= 1.0; };
+  if (!in01(p.kz) || !in01(p.ky) || !in01(p.kx) || !in01(p.phi_y)) return false;
+  if (p.phi_y + p.ky > 1.0) return false;
+  double s = 0.0;
+  for (int l = 0; l < 5; ++l) {
+    if (!in01(p.phi_z[l])) return false;
+    s += p.phi_z[l];
+  }
+  if (std::fabs(s - 1.0) > 1e-12) return false;
+  if (p.dual_mode != 0 && p.dual_mode != 1) return false;
+  if (p.warm != 0 && p.warm != 1) return false;
+  if (!std::isfinite(p.min_gap) || !std::isfinite(p.ub) || !std::isfinite(p.feas_tol)) return false;
+  return true;
+}
+
+#define CK(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+template <class T>
+static cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
+}
+
+extern "C" rlt2_status rlt2_create(int n, const double* F, const double* D, const double* B, const int* partial,
+                                   const rlt2_params* p, void* stream, rlt2_ctx** out) {
+  if (!out) {
+    set_error("rlt2_create: out is NULL");
+    return RLT2_EINVAL;
+  }
+  *out = nullptr;
+  if (n < 3 || n > 64 || !F || !D) {
+    set_error("rlt2_create: need 3 <= n <= 64 and non-NULL F, D");
+    return RLT2_EINVAL;
+  }
+  const size_t nn = (size_t)n * n;
+  if (!finite_all(F, nn) || !finite_all(D, nn) || (B && !finite_all(B, nn))) {
+    set_error("rlt2_create: non-finite input");
+    return RLT2_EINVAL;
+  }
+  rlt2_params prm;
+  rlt2_params_default(&prm);
+  if (p) prm = *p;
+  if (!params_ok(prm)) {
+    set_error("rlt2_create: parameters out of range (kappa, phi in [0,1], phi_y+ky<=1, sum phi_z = 1)");
+    return RLT2_EINVAL;
+  }
+  rlt2_ctx* c = new rlt2_ctx();
+  c->n_full = n;
+  c->prm = prm;
+  c->stream = (cudaStream_t)stream;
+  std::vector<char> used(n, 0);
+  for (int i = 0; i < n; ++i) {
+    if (partial && partial[i] >= 0) {
+      if (partial[i] >= n || used[partial[i]]) {
+        delete c;
+        set_error("rlt2_create: partial assignment is not injective / out of range");
+        return RLT2_EINVAL;
+      }
+      used[partial[i]] = 1;
+      c->fixf.push_back(i);
+      c->fixl.push_back(partial[i]);
+    } else if (partial && partial[i] < -1) {
+      delete c;
+      set_error("rlt2_create: partial entries must be -1 or a location");
+      return RLT2_EINVAL;
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    if (!partial || partial[i] < 0) c->fac.push_back(i);
+  for (int q = 0; q < n; ++q)
+    if (!used[q]) c->loc.push_back(q);
+  const int nr = (int)c->fac.size();
+  if (nr < 3 || nr > 32) {
+    delete c;
+    set_error("rlt2_create: residual size must be in [3, 32]");
+    return RLT2_EINVAL;
+  }
+  c->n = nr;
+  c->m = nr - 2;
+  c->T = (long long)nr * nr * (nr - 1) * (nr - 1);
+  c->E = c->T * c->m * c->m;
+  c->ntrip = nr * (nr - 1) * (nr - 2) / 6;
+  // memory admission
+  size_t need = sizeof(double) * ((size_t)c->E + 6 * (size_t)c->T + 2 * (size_t)c->T * c->m + 8 * (size_t)nr * nr +
+                                  2 * (size_t)nr * nr * nr + kRing) +
+                sizeof(int) * (size_t)(c->ntrip + nr) + (64u << 20);
+  size_t fr = 0, tot = 0;
+  cudaError_t e = cudaMemGetInfo(&fr, &tot);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaMemGetInfo");
+  }
+  if (need > fr) {
+    delete c;
+    set_error("rlt2_create: not enough free device memory");
+    return RLT2_ENOMEM;
+  }
+  rlt2_status st = RLT2_OK;
+  auto fail = [&](cudaError_t err, const char* what) {
+    st = (err == cudaErrorMemoryAllocation) ? RLT2_ENOMEM : RLT2_ECUDA;
+    cuda_fail(err, what);
+    ctx_free(c);
+    return st;
+  };
+#define AL(ptr, cnt)                                   \
+  do {                                                 \
+    cudaError_t e2 = dalloc(&(ptr), (cnt));            \
+    if (e2 != cudaSuccess) return fail(e2, "cudaMalloc"); \
+  } while (0)
+  const size_t T = c->T, m = c->m, n2 = (size_t)nr * nr;
+  AL(c->d_cst, 1);
+  AL(c->Fr, n2);
+  AL(c->Dr, n2);
+  AL(c->bprime, n2);
+  AL(c->Chat, T);
+  AL(c->Dhat, (size_t)c->E);
+  AL(c->Theta, T);
+  AL(c->xi, T * m);
+  AL(c->psi, T * m);
+  AL(c->Delta, n2);
+  AL(c->gamma, n2 * (nr - 1));
+  AL(c->delta, n2 * (nr - 1));
+  AL(c->alpha, nr);
+  AL(c->beta, nr);
+  AL(c->pix, n2);
+  AL(c->piy, T);
+  AL(c->tterm, T);
+  AL(c->xval, 1);
+  AL(c->ring, kRing);
+  AL(c->xperm, nr);
+  AL(c->ubperm, nr);
+  AL(c->trips, c->ntrip);
+  AL(c->sc, 1);
+#undef AL
+  if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return fail(e, "cudaStreamCreate");
+
+  // inputs to the device, then the setup kernels (step A0) on the stream
+  std::vector<int> trips;
+  trips.reserve(c->ntrip);
+  for (int i = 0; i < nr; ++i)
+    for (int j = i + 1; j < nr; ++j)
+      for (int k = j + 1; k < nr; ++k) trips.push_back(i | (j << 8) | (k << 16));
+  double *dF = nullptr, *dD = nullptr, *dB = nullptr;
+  int* dint = nullptr;
+  const int nfix = (int)c->fixf.size();
+  std::vector<int> ints;
+  ints.insert(ints.end(), c->fac.begin(), c->fac.end());
+  ints.insert(ints.end(), c->loc.begin(), c->loc.end());
+  ints.insert(ints.end(), c->fixf.begin(), c->fixf.end());
+  ints.insert(ints.end(), c->fixl.begin(), c->fixl.end());
+  cudaStream_t s = c->stream;
+  auto cleanup_tmp = [&]() {
+    if (dF) cudaFree(dF);
+    if (dD) cudaFree(dD);
+    if (dB) cudaFree(dB);
+    if (dint) cudaFree(dint);
+  };
+  if ((e = dalloc(&dF, nn)) != cudaSuccess || (e = dalloc(&dD, nn)) != cudaSuccess ||
+      (B && (e = dalloc(&dB, nn)) != cudaSuccess) || (e = dalloc(&dint, ints.size())) != cudaSuccess) {
+    cleanup_tmp();
+    return fail(e, "cudaMalloc");
+  }
+  DevScalars init{};
+  init.ub = INFINITY;
+  init.best_lb = -INFINITY;
+  init.lb = -INFINITY;
+  if ((e = cudaMemcpyAsync(dF, F, nn * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(dD, D, nn * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (B && (e = cudaMemcpyAsync(dB, B, nn * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) ||
+      (e = cudaMemcpyAsync(dint, ints.data(), ints.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(c->trips, trips.data(), trips.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(c->sc, &init, sizeof init, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->Dhat, 0, sizeof(double) * (size_t)c->E, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->xi, 0, sizeof(double) * T * m, s)) != cudaSuccess) {
+    cudaStreamSynchronize(s);
+    cleanup_tmp();
+    return fail(e, "upload");
+  }
+  const int* dfac = dint;
+  const int* dloc = dint + nr;
+  const int* dfixf = dint + 2 * nr;
+  const int* dfixl = dint + 2 * nr + nfix;
+  k_setup_b<<<(int)((n2 + 127) / 128), 128, 0, s>>>(n, nr, dF, dD, dB, dfac, dloc, dfixf, dfixl, nfix, c->bprime,
+                                                     c->Fr, c->Dr);
+  k_setup_const<<<1, 32, 0, s>>>(n, dF, dD, dB, dfixf, dfixl, nfix, c->d_cst);
+  k_setup_c<<<(int)((T + 255) / 256 < 4096 ? (T + 255) / 256 : 4096), 256, 0, s>>>(nr, c->T, c->Fr, c->Dr, c->Chat);
+  e = cudaGetLastError();
+  cudaError_t e3 = cudaStreamSynchronize(s);
+  cleanup_tmp();
+  if (e != cudaSuccess) return fail(e, "setup kernels");
+  if (e3 != cudaSuccess) return fail(e3, "setup sync");
+  if ((e = cudaMemcpy(&c->cst_host, c->d_cst, 8, cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e, "cst");
+  for (int mm2 : {nr - 2, nr - 1, nr})
+    if ((e = prepare_lap(mm2)) != cudaSuccess) return fail(e, "prepare_lap");
+  *out = c;
+  return RLT2_OK;
+}
+
+// Enqueue one iteration (six kernels) on stream s.  With timing, events bracket
+// every kernel (ev_base indexes the event pool).
+static cudaError_t enqueue_iteration(rlt2_ctx* c, cudaStream_t s, int ev_base) {
+  const int n = c->n, m = c->m;
+  const long long T = c->T;
+  const rlt2_params& p = c->prm;
+  const int* done = &c->sc->done;
+  cudaError_t e;
+  auto rec = [&](int k, int which) -> cudaError_t {
+    if (ev_base < 0) return cudaSuccess;
+    return cudaEventRecord(c->ev[ev_base + 2 * k + which], s);
+  };
+  // 1) y move + tile terms
+  const double cy = p.ky / (double)(n - 2);
+  const double cx = p.kx / ((double)(n - 1) * (double)(n - 2));
+  if ((e = rec(0, 0)) != cudaSuccess) return e;
+  {
+    const long long blocks = (T + 255) / 256;
+    k_move_y<<<(int)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(n, T, cy, cx, p.phi_y, c->piy, c->pix, c->Chat,
+                                                                    c->tterm, c->sc);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess || (e = rec(0, 1)) != cudaSuccess) return e;
+  // 2) z move
+  MoveZArgs mz{};
+  mz.n = n;
+  mz.m = m;
+  mz.kz = p.kz;
+  for (int l = 0; l < 5; ++l) mz.w[l] = p.phi_z[h_widx[l]];
+  mz.kz_one = (p.kz == 1.0);
+  mz.uniform = (p.phi_z[0] == p.phi_z[1] && p.phi_z[0] == p.phi_z[2] && p.phi_z[0] == p.phi_z[3] &&
+                p.phi_z[0] == p.phi_z[4]);
+  mz.Dhat = c->Dhat;
+  mz.xi = c->xi;
+  mz.psi = c->psi;
+  mz.tterm = c->tterm;
+  mz.trips = c->trips;
+  mz.sc = c->sc;
+  if ((e = rec(1, 0)) != cudaSuccess) return e;
+  k_move_z<<<c->ntrip * n, 128, 0, s>>>(mz);
+  if ((e = cudaGetLastError()) != cudaSuccess || (e = rec(1, 1)) != cudaSuccess) return e;
+  // 3) Z stage
+  LapArgs z{};
+  z.batch = T;
+  z.m = m;
+  z.A = c->Dhat;
+  z.u0 = p.warm ? c->xi : nullptr;
+  z.warm_gate = &c->sc->have_snap;
+  z.value = c->Theta;
+  z.u = c->xi;
+  z.v = c->psi;
+  z.dual_mode = p.dual_mode;
+  z.stats = c->sc->stats + 0;
+  z.skip = done;
+  if ((e = rec(2, 0)) != cudaSuccess) return e;
+  if ((e = launch_lap(z, s)) != cudaSuccess) return e;
+  if ((e = rec(2, 1)) != cudaSuccess) return e;
+  // 4) Y stage on C^ + Theta, writes pi_y
+  LapArgs y{};
+  y.batch = (long long)n * n;
+  y.m = n - 1;
+  y.A = c->Chat;
+  y.Badd = c->Theta;
+  y.value = c->Delta;
+  y.u = c->gamma;
+  y.v = c->delta;
+  y.pi = c->piy;
+  y.dual_mode = p.dual_mode;
+  y.stats = c->sc->stats + 2;
+  y.skip = done;
+  if ((e = rec(3, 0)) != cudaSuccess) return e;
+  if ((e = launch_lap(y, s)) != cudaSuccess) return e;
+  if ((e = rec(3, 1)) != cudaSuccess) return e;
+  // 5) X stage on b' + Delta, writes pi_x
+  LapArgs x{};
+  x.batch = 1;
+  x.m = n;
+  x.A = c->bprime;
+  x.Badd = c->Delta;
+  x.value = c->xval;
+  x.u = c->alpha;
+  x.v = c->beta;
+  x.r2c = c->xperm;
+  x.pi = c->pix;
+  x.dual_mode = p.dual_mode;
+  x.stats = c->sc->stats + 4;
+  x.skip = done;
+  if ((e = rec(4, 0)) != cudaSuccess) return e;
+  if ((e = launch_lap(x, s)) != cudaSuccess) return e;
+  if ((e = rec(4, 1)) != cudaSuccess) return e;
+  // 6) finalize
+  FinArgs f{};
+  f.n = n;
+  f.m = m;
+  f.cst = c->d_cst;
+  f.xval = c->xval;
+  f.xperm = c->xperm;
+  f.ubperm = c->ubperm;
+  f.piy = c->piy;
+  f.Dhat = c->Dhat;
+  f.xi = c->xi;
+  f.psi = c->psi;
+  f.Fr = c->Fr;
+  f.Dr = c->Dr;
+  f.bprime = c->bprime;
+  f.ring = c->ring;
+  f.min_gap = p.min_gap;
+  f.ub_known = p.ub;
+  f.feas_tol = p.feas_tol;
+  f.sc = c->sc;
+  if ((e = rec(5, 0)) != cudaSuccess) return e;
+  k_finalize<<<1, 256, 0, s>>>(f);
+  if ((e = cudaGetLastError()) != cudaSuccess || (e = rec(5, 1)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+static rlt2_status build_graph(rlt2_ctx* c) {
+  if (c->graph) return RLT2_OK;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = enqueue_iteration(c, c->cap_stream, -1);
+  cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(e, "capture");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->graph = nullptr;
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  return RLT2_OK;
+}
+
+static rlt2_status enqueue_many(rlt2_ctx* c, int iters) {
+  if (c->timing) {
+    const size_t need = (size_t)iters * kKinds * 2;
+    while (c->ev.size() < need) {
+      cudaEvent_t ev;
+      CK(cudaEventCreate(&ev));
+      c->ev.push_back(ev);
+    }
+    for (int it = 0; it < iters; ++it) {
+      cudaError_t e = enqueue_iteration(c, c->stream, it * kKinds * 2);
+      if (e != cudaSuccess) return cuda_fail(e, "enqueue_iteration");
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    for (int it = 0; it < iters; ++it)
+      for (int k = 0; k < kKinds; ++k) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev[it * kKinds * 2 + 2 * k], c->ev[it * kKinds * 2 + 2 * k + 1]));
+        c->kms[k] += ms;
+        c->kcount[k] += 1;
+      }
+    return RLT2_OK;
+  }
+  rlt2_status st = build_graph(c);
+  if (st != RLT2_OK) return st;
+  for (int it = 0; it < iters; ++it) CK(cudaGraphLaunch(c->graph, c->stream));
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_iterate_async(rlt2_ctx* c, int iters) {
+  if (!c || iters < 0) {
+    set_error("rlt2_iterate_async: invalid argument");
+    return RLT2_EINVAL;
+  }
+  if (iters == 0) return RLT2_OK;
+  return enqueue_many(c, iters);
+}
+
+extern "C" rlt2_status rlt2_iterate(rlt2_ctx* c, int iters, double* lb_hist, int* done) {
+  if (!c || iters < 0) {
+    set_error("rlt2_iterate: invalid argument");
+    return RLT2_EINVAL;
+  }
+  int total = 0;
+  for (int off = 0; off < iters; off += kRing) {
+    const int chunk = (iters - off) < kRing ? (iters - off) : kRing;
+    const int it0 = c->iter_host;
+    rlt2_status st = enqueue_many(c, chunk);
+    if (st != RLT2_OK) return st;
+    DevScalars h;
+    CK(cudaMemcpyAsync(&h, c->sc, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const int got = h.iter - it0;
+    c->iter_host = h.iter;
+    total += got;
+    if (lb_hist) {
+      std::vector<double> ring(kRing);
+      if (got > 0) CK(cudaMemcpy(ring.data(), c->ring, sizeof(double) * kRing, cudaMemcpyDeviceToHost));
+      for (int k = 0; k < chunk; ++k) lb_hist[off + k] = (k < got) ? ring[(it0 + k) & (kRing - 1)] : NAN;
+    }
+    if (got < chunk) {
+      if (lb_hist)
+        for (int k = off + chunk; k < iters; ++k) lb_hist[k] = NAN;
+      break;
+    }
+  }
+  if (done) *done = total;
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_bound(rlt2_ctx* c, double* lb, double* best_lb, double* ub, int* perm, int* ub_perm,
+                                  int* iters) {
+  if (!c) return RLT2_EINVAL;
+  DevScalars h;
+  std::vector<int> xp(c->n), up(c->n);
+  CK(cudaMemcpyAsync(&h, c->sc, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(xp.data(), c->xperm, sizeof(int) * c->n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(up.data(), c->ubperm, sizeof(int) * c->n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (lb) *lb = h.lb;
+  if (best_lb) *best_lb = h.best_lb;
+  if (ub) *ub = h.ub;
+  if (iters) *iters = h.iter;
+  int* outs[2] = {perm, ub_perm};
+  const std::vector<int>* srcs[2] = {&xp, &up};
+  for (int w = 0; w < 2; ++w) {
+    int* o = outs[w];
+    if (!o) continue;
+    for (int i = 0; i < c->n_full; ++i) o[i] = -1;
+    for (size_t x = 0; x < c->fixf.size(); ++x) o[c->fixf[x]] = c->fixl[x];
+    if (h.iter > 0)
+      for (int i = 0; i < c->n; ++i) o[c->fac[i]] = c->loc[(*srcs[w])[i]];
+  }
+  return RLT2_OK;
+}
+
+static rlt2_status copy_out(rlt2_ctx* c, double* dst, const double* src, size_t count, int on_device) {
+  if (!dst) return RLT2_OK;
+  CK(cudaMemcpyAsync(dst, src, count * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     c->stream));
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_duals(rlt2_ctx* c, double* alpha, double* beta, double* gamma, double* delta, double* xi,
+                                  double* psi, int on_device) {
+  if (!c) return RLT2_EINVAL;
+  const size_t n = c->n, yd = n * n * (n - 1), zd = (size_t)c->T * c->m;
+  rlt2_status st;
+  if ((st = copy_out(c, alpha, c->alpha, n, on_device)) != RLT2_OK) return st;
+  if ((st = copy_out(c, beta, c->beta, n, on_device)) != RLT2_OK) return st;
+  if ((st = copy_out(c, gamma, c->gamma, yd, on_device)) != RLT2_OK) return st;
+  if ((st = copy_out(c, delta, c->delta, yd, on_device)) != RLT2_OK) return st;
+  if ((st = copy_out(c, xi, c->xi, zd, on_device)) != RLT2_OK) return st;
+  if ((st = copy_out(c, psi, c->psi, zd, on_device)) != RLT2_OK) return st;
+  CK(cudaStreamSynchronize(c->stream));
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_reduced_costs(rlt2_ctx* c, double* pi_x, double* pi_y, double* pi_z, int on_device) {
+  if (!c) return RLT2_EINVAL;
+  rlt2_status st;
+  if ((st = copy_out(c, pi_x, c->pix, (size_t)c->n * c->n, on_device)) != RLT2_OK) return st;
+  if ((st = copy_out(c, pi_y, c->piy, (size_t)c->T, on_device)) != RLT2_OK) return st;
+  if (pi_z) {
+    double* dst = pi_z;
+    double* tmp = nullptr;
+    if (!on_device) {
+      CK(cudaMalloc((void**)&tmp, sizeof(double) * (size_t)c->E));
+      dst = tmp;
+    }
+    k_pi_z<<<4096, 256, 0, c->stream>>>(c->E, c->m, c->Dhat, c->xi, c->psi, dst);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && tmp)
+      e = cudaMemcpyAsync(pi_z, tmp, sizeof(double) * (size_t)c->E, cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "pi_z");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "pi_z sync");
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_export_state(rlt2_ctx* c, double* Dhat, double* Chat, int on_device) {
+  if (!c) return RLT2_EINVAL;
+  rlt2_status st;
+  if ((st = copy_out(c, Dhat, c->Dhat, (size_t)c->E, on_device)) != RLT2_OK) return st;
+  if ((st = copy_out(c, Chat, c->Chat, (size_t)c->T, on_device)) != RLT2_OK) return st;
+  CK(cudaStreamSynchronize(c->stream));
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_import_state(rlt2_ctx* c, const double* Dhat, const double* Chat, int on_device) {
+  if (!c) return RLT2_EINVAL;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (Dhat) CK(cudaMemcpyAsync(c->Dhat, Dhat, sizeof(double) * (size_t)c->E, k, c->stream));
+  if (Chat) CK(cudaMemcpyAsync(c->Chat, Chat, sizeof(double) * (size_t)c->T, k, c->stream));
+  const int zero = 0;
+  CK(cudaMemcpyAsync(&c->sc->have_snap, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(&c->sc->done, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_stats(rlt2_ctx* c, long long* out) {
+  if (!c || !out) return RLT2_EINVAL;
+  DevScalars h;
+  CK(cudaMemcpyAsync(&h, c->sc, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  out[0] = h.iter;
+  for (int k = 0; k < 6; ++k) out[1 + k] = (long long)h.stats[k];
+  out[7] = h.reason;
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_sizes(rlt2_ctx* c, int* n_res, long long* T, long long* E, double* cst) {
+  if (!c) return RLT2_EINVAL;
+  if (n_res) *n_res = c->n;
+  if (T) *T = c->T;
+  if (E) *E = c->E;
+  if (cst) *cst = c->cst_host;
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_set_timing(rlt2_ctx* c, int on) {
+  if (!c) return RLT2_EINVAL;
+  c->timing = on != 0;
+  for (int k = 0; k < kKinds; ++k) {
+    c->kms[k] = 0.0;
+    c->kcount[k] = 0;
+  }
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_kernel_times(rlt2_ctx* c, double* ms, long long* count, int nk) {
+  if (!c || nk < 0) return RLT2_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < nk && k < kKinds; ++k) {
+    if (ms) ms[k] = c->kms[k];
+    if (count) count[k] = c->kcount[k];
+  }
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_destroy(rlt2_ctx* c) {
+  if (!c) return RLT2_OK;
+  cudaStreamSynchronize(c->stream);
+  ctx_free(c);
+  return RLT2_OK;
+}
+
+extern "C" const char* rlt2_strerror(rlt2_status s) {
+  switch (s) {
+    case RLT2_OK: return "ok";
+    case RLT2_EINVAL: return "invalid argument";
+    case RLT2_ENOMEM: return "out of device memory";
+    case RLT2_ECUDA: return "CUDA error";
+    case RLT2_ETIMEOUT: return "device wait timed out";
+    case RLT2_EADMIT: return "node does not fit the memory budget";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* rlt2_last_error(void) { return g_last_error.c_str(); }

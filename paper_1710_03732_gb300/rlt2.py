@@ -1,0 +1,279 @@
+"""Thin ctypes binding of the C ABI in include/rlt2.h (argument marshalling only).
+
+Every function below has the name of the C entry point it calls and does no
+arithmetic of the method: all of it runs in the CUDA library.  Device buffers
+are torch CUDA tensors (PyTorch supplies memory and streams); host buffers are
+numpy arrays.  If the library is missing the import of a function fails loudly:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librlt2.so")
+
+RLT2_OK, RLT2_EINVAL, RLT2_ENOMEM, RLT2_ECUDA, RLT2_ETIMEOUT, RLT2_EADMIT = range(6)
+
+
+class rlt2_params(ctypes.Structure):
+    _fields_ = [("kz", ctypes.c_double), ("ky", ctypes.c_double), ("kx", ctypes.c_double),
+                ("phi_y", ctypes.c_double), ("phi_z", ctypes.c_double * 5), ("dual_mode", ctypes.c_int),
+                ("warm", ctypes.c_int), ("min_gap", ctypes.c_double), ("ub", ctypes.c_double),
+                ("feas_tol", ctypes.c_double)]
+
+
+class Rlt2Error(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status} ({detail})")
+        self.status = status
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+
+EXPORTS = ["rlt2_params_default", "rlt2_create", "rlt2_iterate", "rlt2_iterate_async", "rlt2_bound", "rlt2_duals",
+           "rlt2_reduced_costs", "rlt2_export_state", "rlt2_import_state", "rlt2_stats", "rlt2_sizes",
+           "rlt2_set_timing", "rlt2_kernel_times", "rlt2_destroy", "rlt2_lap_batched", "rlt2_strerror",
+           "rlt2_last_error"]
+
+
+def lib():
+    """Load librlt2.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    L.rlt2_params_default.argtypes = [ctypes.POINTER(rlt2_params)]
+    L.rlt2_params_default.restype = None
+    L.rlt2_create.argtypes = [ctypes.c_int, _dp, _dp, _dp, _ip, ctypes.POINTER(rlt2_params), _vp,
+                              ctypes.POINTER(_vp)]
+    L.rlt2_iterate.argtypes = [_vp, ctypes.c_int, _dp, _ip]
+    L.rlt2_iterate_async.argtypes = [_vp, ctypes.c_int]
+    L.rlt2_bound.argtypes = [_vp, _dp, _dp, _dp, _ip, _ip, _ip]
+    L.rlt2_duals.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int]
+    L.rlt2_reduced_costs.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int]
+    L.rlt2_export_state.argtypes = [_vp, _vp, _vp, ctypes.c_int]
+    L.rlt2_import_state.argtypes = [_vp, _vp, _vp, ctypes.c_int]
+    L.rlt2_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.rlt2_sizes.argtypes = [_vp, _ip, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), _dp]
+    L.rlt2_set_timing.argtypes = [_vp, ctypes.c_int]
+    L.rlt2_kernel_times.argtypes = [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
+    L.rlt2_destroy.argtypes = [_vp]
+    L.rlt2_lap_batched.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
+    L.rlt2_strerror.argtypes = [ctypes.c_int]
+    L.rlt2_strerror.restype = ctypes.c_char_p
+    L.rlt2_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("rlt2_params_default", "rlt2_strerror", "rlt2_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != RLT2_OK:
+        L = lib()
+        raise Rlt2Error(status, where, f"{L.rlt2_strerror(status).decode()}: {L.rlt2_last_error().decode()}")
+
+
+def _host_d(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def _ptr(buf) -> Optional[int]:
+    """Pointer of a torch tensor (device) or numpy array (host), None for None."""
+    if buf is None:
+        return None
+    if isinstance(buf, np.ndarray):
+        assert buf.flags.c_contiguous
+        return buf.ctypes.data
+    assert buf.is_contiguous()
+    return buf.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is not None:
+        return int(stream)
+    import torch
+    return int(torch.cuda.current_stream().cuda_stream) or None
+
+
+def params(kz=1.0, ky=0.5, kx=1.0, phi_y=0.5, phi_z=(0.2,) * 5, dual_mode=1, warm=0, min_gap=0.0, ub=0.0,
+           feas_tol=1e-9) -> rlt2_params:
+    p = rlt2_params()
+    lib().rlt2_params_default(ctypes.byref(p))
+    p.kz, p.ky, p.kx, p.phi_y = kz, ky, kx, phi_y
+    for i, x in enumerate(phi_z):
+        p.phi_z[i] = x
+    p.dual_mode, p.warm, p.min_gap, p.ub, p.feas_tol = dual_mode, warm, min_gap, ub, feas_tol
+    return p
+
+
+# ------------------------------------------------------------ C entry points --
+def rlt2_create(F: np.ndarray, D: np.ndarray, B: Optional[np.ndarray] = None, partial: Optional[np.ndarray] = None,
+                prm: Optional[rlt2_params] = None, stream=None) -> int:
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    B = None if B is None else np.ascontiguousarray(B, dtype=np.float64)
+    part = None if partial is None else np.ascontiguousarray(partial, dtype=np.int32)
+    out = _vp()
+    st = lib().rlt2_create(F.shape[0], _host_d(F), _host_d(D), _host_d(B),
+                           None if part is None else part.ctypes.data_as(_ip),
+                           None if prm is None else ctypes.byref(prm), _stream(stream), ctypes.byref(out))
+    _check(st, "rlt2_create")
+    return out.value
+
+
+def rlt2_iterate(ctx: int, iters: int):
+    """Returns (bounds per iteration as numpy, iterations performed)."""
+    hist = np.empty(iters, dtype=np.float64)
+    done = ctypes.c_int()
+    _check(lib().rlt2_iterate(ctx, iters, _host_d(hist), ctypes.byref(done)), "rlt2_iterate")
+    return hist, done.value
+
+
+def rlt2_iterate_async(ctx: int, iters: int):
+    _check(lib().rlt2_iterate_async(ctx, iters), "rlt2_iterate_async")
+
+
+def rlt2_bound(ctx: int, n_full: int):
+    lb, best, ub = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    perm = np.zeros(n_full, dtype=np.int32)
+    ub_perm = np.zeros(n_full, dtype=np.int32)
+    it = ctypes.c_int()
+    _check(lib().rlt2_bound(ctx, ctypes.byref(lb), ctypes.byref(best), ctypes.byref(ub), perm.ctypes.data_as(_ip),
+                            ub_perm.ctypes.data_as(_ip), ctypes.byref(it)), "rlt2_bound")
+    return lb.value, best.value, ub.value, perm, ub_perm, it.value
+
+
+def rlt2_duals(ctx: int, alpha=None, beta=None, gamma=None, delta=None, xi=None, psi=None, on_device=0):
+    _check(lib().rlt2_duals(ctx, _ptr(alpha), _ptr(beta), _ptr(gamma), _ptr(delta), _ptr(xi), _ptr(psi), on_device),
+           "rlt2_duals")
+
+
+def rlt2_reduced_costs(ctx: int, pi_x=None, pi_y=None, pi_z=None, on_device=0):
+    _check(lib().rlt2_reduced_costs(ctx, _ptr(pi_x), _ptr(pi_y), _ptr(pi_z), on_device), "rlt2_reduced_costs")
+
+
+def rlt2_export_state(ctx: int, Dhat=None, Chat=None, on_device=0):
+    _check(lib().rlt2_export_state(ctx, _ptr(Dhat), _ptr(Chat), on_device), "rlt2_export_state")
+
+
+def rlt2_import_state(ctx: int, Dhat=None, Chat=None, on_device=0):
+    _check(lib().rlt2_import_state(ctx, _ptr(Dhat), _ptr(Chat), on_device), "rlt2_import_state")
+
+
+def rlt2_stats(ctx: int) -> np.ndarray:
+    out = (ctypes.c_longlong * 8)()
+    _check(lib().rlt2_stats(ctx, out), "rlt2_stats")
+    return np.array(list(out), dtype=np.int64)
+
+
+def rlt2_sizes(ctx: int):
+    nr, T, E, cst = ctypes.c_int(), ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_double()
+    _check(lib().rlt2_sizes(ctx, ctypes.byref(nr), ctypes.byref(T), ctypes.byref(E), ctypes.byref(cst)), "rlt2_sizes")
+    return nr.value, T.value, E.value, cst.value
+
+
+def rlt2_set_timing(ctx: int, on: bool):
+    _check(lib().rlt2_set_timing(ctx, int(bool(on))), "rlt2_set_timing")
+
+
+KERNEL_KINDS = ["move_y", "move_z", "lap_z", "lap_y", "lap_x", "finalize"]
+
+
+def rlt2_kernel_times(ctx: int):
+    ms = (ctypes.c_double * 6)()
+    cnt = (ctypes.c_longlong * 6)()
+    _check(lib().rlt2_kernel_times(ctx, ms, cnt, 6), "rlt2_kernel_times")
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def rlt2_destroy(ctx: int):
+    _check(lib().rlt2_destroy(ctx), "rlt2_destroy")
+
+
+def rlt2_lap_batched(cost, value, u0=None, u=None, v=None, row_to_col=None, n_aug=None, dual_mode=1, stream=None):
+    """cost: CUDA tensor (batch, m, m) float64; outputs are CUDA tensors of matching batch."""
+    batch, m = int(cost.shape[0]), int(cost.shape[1])
+    _check(lib().rlt2_lap_batched(batch, m, _ptr(cost), _ptr(u0), _ptr(value), _ptr(u), _ptr(v), _ptr(row_to_col),
+                                  _ptr(n_aug), dual_mode, _stream(stream)), "rlt2_lap_batched")
+
+
+# ------------------------------------------------------------ convenience ----
+class Context:
+    """Owns one rlt2_ctx: ``Context(F, D).iterate(300)``."""
+
+    def __init__(self, F, D, B=None, partial=None, prm: Optional[rlt2_params] = None, stream=None):
+        self.n_full = int(np.asarray(F).shape[0])
+        self.ctx = rlt2_create(F, D, B, partial, prm, stream)
+        self.n, self.T, self.E, self.const = rlt2_sizes(self.ctx)
+
+    def iterate(self, iters: int):
+        return rlt2_iterate(self.ctx, iters)
+
+    def iterate_async(self, iters: int):
+        rlt2_iterate_async(self.ctx, iters)
+
+    def bound(self):
+        return rlt2_bound(self.ctx, self.n_full)
+
+    def duals(self):
+        n, T, m = self.n, self.T, self.n - 2
+        out = dict(alpha=np.empty(n), beta=np.empty(n), gamma=np.empty(n * n * (n - 1)),
+                   delta=np.empty(n * n * (n - 1)), xi=np.empty(T * m), psi=np.empty(T * m))
+        rlt2_duals(self.ctx, **out)
+        return out
+
+    def reduced_costs(self, with_z=True):
+        out = dict(pi_x=np.empty(self.n * self.n), pi_y=np.empty(self.T),
+                   pi_z=np.empty(self.E) if with_z else None)
+        rlt2_reduced_costs(self.ctx, **out)
+        return out
+
+    def export_state(self):
+        D, C = np.empty(self.E), np.empty(self.T)
+        rlt2_export_state(self.ctx, D, C)
+        return D, C
+
+    def import_state(self, Dhat, Chat):
+        rlt2_import_state(self.ctx, np.ascontiguousarray(Dhat, dtype=np.float64),
+                          np.ascontiguousarray(Chat, dtype=np.float64))
+
+    def stats(self):
+        return rlt2_stats(self.ctx)
+
+    def set_timing(self, on=True):
+        rlt2_set_timing(self.ctx, on)
+
+    def kernel_times(self):
+        return rlt2_kernel_times(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            rlt2_destroy(self.ctx)
+            self.ctx = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
