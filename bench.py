@@ -1,0 +1,386 @@
+"""Benchmark: RLT2 dual-ascent iterations/s and size-(n-2) LAPs/s at n = 20.
+
+Workload: single QAP, n = 20, F and D symmetric with zero diagonal and uniform
+integers 0..99 (seed 2), B = 0; every iteration solves 144,400 Z-LAPs of size
+18, 400 Y-LAPs of size 19 and one X-LAP of size 20 and moves reduced costs over
+the 46.8 M-entry z array (374 MB FP64, larger than L2, so no L2 flush is
+needed between steps).  A step is one full dual-ascent iteration.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  --impl reference times the CPU oracle (the plain FP64
+C implementation the tests check the GPU against) on the host cores.
+Multi-GPU runs are independent replicas (one QAP per rank, no collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1710_03732_gb300 import instances as I  # noqa: E402
+
+METRIC = "RLT2 dual-ascent iters/s and size-(n-2) LAPs/s at n=20, plain vs warm-started"
+WORKLOAD = "QAP n=20, F,D symmetric dense uniform 0..99 (seed 2), B=0; S1 dual ascent, canonical duals"
+CFG = 3
+KERNELS = ["move_y", "move_z", "lap_z", "lap_y", "lap_x", "finalize"]
+# FP64 ALU peak: 1.25 TFLOP/s nominal GB300 FP64 = 2 flop per FMA -> 0.625e12
+# FP64 instructions (lane-ops) per second over 152 SMs at 2.07 GHz, i.e. about
+# 2 FP64 lane-ops per clock per SM; every DADD/DSUB/DMUL/DFMA counts as one.
+FP64_PEAK_GOPS = 625.0
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1710_03732_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = source_digest()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and parts[0] == kernel and parts[1] == workload and parts[3] == want:
+            return float(parts[2])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names[1:], p[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_baseline(inst, iters: int, budget_s: float):
+    """The CPU oracle as it stands, all host cores (OpenMP over LAPs and z classes)."""
+    import oracle as O
+    threads = max(1, O.max_threads() or 1)
+    st = O.setup(inst.F, inst.D, inst.B)
+    prm = O.params_array()
+    t0 = time.perf_counter()
+    done = 0
+    lbs = []
+    while done < iters:
+        out = O.iterate(st, prm, 1, threads=threads)
+        lbs.append(st.const + out.lb)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done, dt, threads, lbs
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    inst = I.config(CFG)
+    # warm-up iterations are part of the same trajectory; each timed step is one
+    # full oracle iteration (144,400 Z-LAPs + 400 Y-LAPs + X-LAP + the moves)
+    budget = float(os.environ.get("RLT2_REF_BUDGET_S", "150"))
+    import oracle as O
+    threads = max(1, O.max_threads() or 1)
+    st = O.setup(inst.F, inst.D, inst.B)
+    prm = O.params_array()
+    for _ in range(args.warmup):
+        O.iterate(st, prm, 1, threads=threads)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < args.steps:
+        O.iterate(st, prm, 1, threads=threads)
+        steps += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = time.perf_counter() - t0
+    value = steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": 20, "iterations": steps, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "iters/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{steps} consecutive oracle iterations after {args.warmup} warm-up "
+                                   f"(capped at {budget:.0f} s); CPU: {cpu_model()}"},
+        "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def timed_device_run(R, torch, inst, warm: int, steps: int, warmup: int, barrier):
+    prm = R.params(dual_mode=1, warm=warm, feas_tol=0.0)
+    ctx = R.Context(inst.F, inst.D, inst.B, prm=prm)
+    ctx.iterate(warmup)
+    s0 = ctx.stats()
+    ctx.set_timing(True)
+    barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.iterate_async(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    s1 = ctx.stats()
+    kt = ctx.kernel_times()
+    lb, best, ub, _, _, its = ctx.bound()
+    ctx.close()
+    d = s1 - s0
+    return dict(ms=ms, stats=d, kt=kt, lb=lb, best=best, ub=ub, iters=its, T=ctx.T, n=ctx.n)
+
+
+def run_profile_case(args):
+    """Minimal command for ncu: W + K iterations of the n=20 workload, warm start."""
+    import torch
+    from paper_1710_03732_gb300 import rlt2 as R
+    R.lib()
+    inst = I.config(CFG)
+    with R.Context(inst.F, inst.D, inst.B, prm=R.params(dual_mode=1, warm=1, feas_tol=0.0)) as ctx:
+        hist, got = ctx.iterate(args.warmup + args.steps)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": WORKLOAD, "iterations": got, "lb_last": float(hist[got - 1])}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only run warmup+steps iterations (graph replay, warm start) for ncu captures")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.profile:
+        return run_profile_case(args)
+
+    rank, world, local = env_rank()
+    inst = I.config(CFG)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        it, dt, threads, _ = cpu_oracle_baseline(inst, 40, 15.0)
+        cpu = {"value": it / dt, "unit": "iters/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {it} iterations of the same n=20 workload, all host cores ({cpu_model()})"}
+
+    import torch
+    from paper_1710_03732_gb300 import build as B
+    from paper_1710_03732_gb300 import rlt2 as R
+    if not os.path.exists(R.LIB_PATH):
+        B.build()
+    R.lib()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    with ClockSampler(local) as clocks:
+        cold = timed_device_run(R, torch, inst, 0, args.steps, args.warmup, barrier)
+        warm = timed_device_run(R, torch, inst, 1, args.steps, args.warmup, barrier)
+    clk = clocks.summary()
+
+    # end to end through the C ABI with host buffers: create (H2D of F, D, B and
+    # the setup kernels), K iterations with the bound of every iteration read back
+    # to host memory, destroy
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    prm = R.params(dual_mode=1, warm=1, feas_tol=0.0)
+    with R.Context(inst.F, inst.D, inst.B, prm=prm) as ctx:
+        hist, got = ctx.iterate(args.steps)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+
+    def per_rank_max(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    warm_ms = per_rank_max(warm["ms"])
+    cold_ms = per_rank_max(cold["ms"])
+    e2e_s = per_rank_max(e2e_s)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    n, T = warm["n"], warm["T"]
+    m = n - 2
+    steps = args.steps
+
+    def lap_z_roofline(r):
+        ms_lz, cnt = r["kt"]["lap_z"]
+        cnt = max(cnt, 1)
+        avg_ms = ms_lz / cnt
+        aug, relax = int(r["stats"][1]), int(r["stats"][2])  # totals over the timed launches
+        # useful FP64 work of one Z-stage launch: 3 additions per label relaxation
+        # (only unscanned columns count), 3 per column per search for the dual
+        # update and row duals, m for the optimum and 3 per relaxation of the
+        # canonical-dual search (m(m-1)/2 per LAP)
+        per_launch = (3 * relax + 3 * m * aug) / cnt + T * m + T * 3 * (m * (m - 1) // 2)
+        achieved = per_launch / (avg_ms * 1e-3) / 1e9
+        return avg_ms, per_launch, achieved
+
+    avg_lz, fl_lz, ach_lz = lap_z_roofline(warm)
+    mz_ms = warm["kt"]["move_z"][0] / max(warm["kt"]["move_z"][1], 1)
+    E = T * m * m
+    mz_ops = E * 10  # FP64 ops per z entry with kz = 1 and equal phi: 2 (pi_z) + 1 (s) + 1 (phi*s) + 4 + 2
+    mz_bytes = E * 16 + 2 * T * m * 8 + T * 8  # D^ read + write, xi/psi and tile terms read once
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    traffic = profiled_traffic("lap_z", "n20")
+    total_kernel_ms = sum(v[0] for v in warm["kt"].values())
+    launches = sum(v[1] for v in warm["kt"].values())
+    line = {
+        "metric": METRIC,
+        "value": world * steps / (warm_ms / 1000.0),
+        "unit": "iters/s",
+        "n_gpus": world,
+        "steps": steps,
+        "warmup": args.warmup,
+        "ms_per_step": warm_ms / steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "z_laps_per_iter": T, "z_lap_size": m, "z_entries": E,
+                   "warm_start": "previous-iteration Z duals", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (374 MB z array), no flush"},
+        "laps_per_s": {"warm": world * steps * T / (warm_ms / 1000.0),
+                       "cold": world * steps * T / (cold_ms / 1000.0),
+                       "z_stage_only_warm": T / (avg_lz * 1e-3)},
+        "plain_cold": {"value": world * steps / (cold_ms / 1000.0), "unit": "iters/s",
+                       "ms_per_step": cold_ms / steps, "lb_last": cold["lb"],
+                       "z_aug_per_lap": cold["stats"][1] / (steps * T)},
+        "warm": {"lb_last": warm["lb"], "z_aug_per_lap": warm["stats"][1] / (steps * T),
+                 "same_bound_as_cold_rel": abs(warm["lb"] - cold["lb"]) / abs(cold["lb"])},
+        "kernels_ms_per_launch": {k: v[0] / max(v[1], 1) for k, v in warm["kt"].items()},
+        "roofline": {"bound": "alu", "kernel": "lap_z", "achieved": ach_lz, "peak": FP64_PEAK_GOPS,
+                     "unit": "GFLOP/s (FP64)", "frac": ach_lz / FP64_PEAK_GOPS, "traffic": traffic,
+                     "algorithmic_flops_per_launch": fl_lz, "avg_launch_ms": avg_lz,
+                     "peak_source": "derived: 1.25 TFLOP/s nominal FP64 / 2 per FMA = 2 lane-ops/clk/SM x 152 x 2.07 GHz"},
+        "roofline_move_z": {"bound": "alu", "achieved": mz_ops / (mz_ms * 1e-3) / 1e9, "peak": FP64_PEAK_GOPS,
+                            "unit": "GFLOP/s (FP64)", "frac": mz_ops / (mz_ms * 1e-3) / 1e9 / FP64_PEAK_GOPS,
+                            "hbm_gbs": mz_bytes / (mz_ms * 1e-3) / 1e9,
+                            "hbm_frac_of_measured": (mz_bytes / (mz_ms * 1e-3) / 1e9 / hbm) if hbm else None,
+                            "avg_launch_ms": mz_ms},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * got / e2e_s, "unit": "iters/s",
+                "h2d_bytes_per_step": 3 * 20 * 20 * 8 / steps, "d2h_bytes_per_step": 8,
+                "note": "rlt2_create from host F,D,B + rlt2_iterate(K) with host bound history + destroy"},
+        "gpu_launches": int(launches),
+        "gpu_kernel_ms_total": total_kernel_ms,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

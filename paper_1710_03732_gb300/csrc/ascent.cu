@@ -703,26 +703,26 @@ static rlt2_status build_graph(rlt2_ctx* c) {
   return RLT2_OK;
 }
 
+constexpr int kEvChunk = 64;  // iterations per batch of timing events
+
 static rlt2_status enqueue_many(rlt2_ctx* c, int iters) {
   if (c->timing) {
-    const size_t need = (size_t)iters * kKinds * 2;
-    while (c->ev.size() < need) {
-      cudaEvent_t ev;
-      CK(cudaEventCreate(&ev));
-      c->ev.push_back(ev);
-    }
-    for (int it = 0; it < iters; ++it) {
-      cudaError_t e = enqueue_iteration(c, c->stream, it * kKinds * 2);
-      if (e != cudaSuccess) return cuda_fail(e, "enqueue_iteration");
-    }
-    CK(cudaStreamSynchronize(c->stream));
-    for (int it = 0; it < iters; ++it)
-      for (int k = 0; k < kKinds; ++k) {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, c->ev[it * kKinds * 2 + 2 * k], c->ev[it * kKinds * 2 + 2 * k + 1]));
-        c->kms[k] += ms;
-        c->kcount[k] += 1;
+    // the event pool was created by rlt2_set_timing; reuse it every kEvChunk iterations
+    for (int base = 0; base < iters; base += kEvChunk) {
+      const int cnt = (iters - base) < kEvChunk ? (iters - base) : kEvChunk;
+      for (int it = 0; it < cnt; ++it) {
+        cudaError_t e = enqueue_iteration(c, c->stream, it * kKinds * 2);
+        if (e != cudaSuccess) return cuda_fail(e, "enqueue_iteration");
       }
+      CK(cudaEventSynchronize(c->ev[(cnt - 1) * kKinds * 2 + 2 * (kKinds - 1) + 1]));
+      for (int it = 0; it < cnt; ++it)
+        for (int k = 0; k < kKinds; ++k) {
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, c->ev[it * kKinds * 2 + 2 * k], c->ev[it * kKinds * 2 + 2 * k + 1]));
+          c->kms[k] += ms;
+          c->kcount[k] += 1;
+        }
+    }
     return RLT2_OK;
   }
   rlt2_status st = build_graph(c);
@@ -758,9 +758,15 @@ extern "C" rlt2_status rlt2_iterate(rlt2_ctx* c, int iters, double* lb_hist, int
     c->iter_host = h.iter;
     total += got;
     if (lb_hist) {
-      std::vector<double> ring(kRing);
-      if (got > 0) CK(cudaMemcpy(ring.data(), c->ring, sizeof(double) * kRing, cudaMemcpyDeviceToHost));
-      for (int k = 0; k < chunk; ++k) lb_hist[off + k] = (k < got) ? ring[(it0 + k) & (kRing - 1)] : NAN;
+      // copy only the entries of this chunk (at most two pieces around the ring's end)
+      int k = 0;
+      while (k < got) {
+        const int pos = (it0 + k) & (kRing - 1);
+        const int len = (got - k) < (kRing - pos) ? (got - k) : (kRing - pos);
+        CK(cudaMemcpy(lb_hist + off + k, c->ring + pos, sizeof(double) * len, cudaMemcpyDeviceToHost));
+        k += len;
+      }
+      for (k = got; k < chunk; ++k) lb_hist[off + k] = NAN;
     }
     if (got < chunk) {
       if (lb_hist)
@@ -892,6 +898,11 @@ extern "C" rlt2_status rlt2_set_timing(rlt2_ctx* c, int on) {
   for (int k = 0; k < kKinds; ++k) {
     c->kms[k] = 0.0;
     c->kcount[k] = 0;
+  }
+  while (c->timing && c->ev.size() < (size_t)kEvChunk * kKinds * 2) {
+    cudaEvent_t ev;
+    CK(cudaEventCreate(&ev));
+    c->ev.push_back(ev);
   }
   return RLT2_OK;
 }
