@@ -171,6 +171,32 @@ rlt2_status rlt2_destroy(rlt2_ctx* ctx);
 rlt2_status rlt2_lap_batched(int batch, int m, const double* cost, const double* u0, double* value, double* u,
                              double* v, int* row_to_col, int* n_aug, int dual_mode, void* stream);
 
+/* Dual ascent of a small QAP that allocates no device memory.  The paper has no
+ * counterpart; this entry point exists for callers that cannot call cudaMalloc:
+ * code running under a framework that owns the whole device memory pool (an
+ * extra cudaMalloc would fail or break its accounting), loops that must not hit
+ * the allocator's implicit device synchronisation, and deployments that forbid
+ * allocation after start-up.
+ *  n        : problem size, 3 <= n <= 10 (root node, no fixed facilities);
+ *             larger n returns RLT2_EINVAL with a message naming the limit
+ *  F, D     : device, n*n flow and distance matrices (finite; not checked)
+ *  B        : device, n*n fixed costs, or NULL for B = 0
+ *  p        : host parameters (NULL = defaults), as for rlt2_create
+ *  iters    : 1..65536 iterations of the same S1 dual ascent as rlt2_iterate
+ *  lb_hist  : device, iters doubles: bound of each iteration (NaN after a stop)
+ *  stream   : cudaStream_t the work is enqueued on; the call returns without
+ *             waiting for it
+ * All working memory is one fixed 8 MiB device array inside the library, held
+ * by every GPU that loads the library until the process exits; nothing is
+ * allocated or freed, by this call or by any library routine it uses.  The first
+ * call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  Every call reuses
+ * the same array and starts by clearing what must start at zero, so calls that
+ * overlap on the GPU (different streams, or different host threads on one
+ * device) race and give undefined results: serialise them. */
+rlt2_status rlt2_iterate_noalloc(int n, const double* F, const double* D, const double* B, const rlt2_params* p,
+                                 int iters, double* lb_hist, void* stream);
+
 /* Human-readable name of a status, and the last error message of this thread. */
 const char* rlt2_strerror(rlt2_status s);
 const char* rlt2_last_error(void);

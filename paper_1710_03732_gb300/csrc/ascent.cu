@@ -33,14 +33,7 @@ rlt2_status cuda_fail(cudaError_t e, const char* what) {
   return RLT2_ECUDA;
 }
 
-constexpr int kRing = 1 << 16;
 constexpr int kKinds = 6;
-
-struct DevScalars {
-  double lb, best_lb, ub, gap;
-  int iter, done, have_snap, reason;
-  unsigned long long stats[6];  // Z aug, Z relax, Y aug, Y relax, X aug, X relax
-};
 
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
@@ -302,6 +295,21 @@ __global__ void k_finalize(FinArgs a) {
   }
 }
 
+// Step A0 on the device: b', the residual F and D, the constant of the fixed
+// facilities and C^ (D^ is cleared by the caller).
+cudaError_t enqueue_setup(const IterView& v, int n_full, const double* dF, const double* dD, const double* dB,
+                          const int* dfac, const int* dloc, const int* dfixf, const int* dfixl, int nfix,
+                          cudaStream_t s) {
+  const int nr = v.n;
+  const long long n2 = (long long)nr * nr;
+  k_setup_b<<<(int)((n2 + 127) / 128), 128, 0, s>>>(n_full, nr, dF, dD, dB, dfac, dloc, dfixf, dfixl, nfix, v.bprime,
+                                                     v.Fr, v.Dr);
+  k_setup_const<<<1, 32, 0, s>>>(n_full, dF, dD, dB, dfixf, dfixl, nfix, v.d_cst);
+  const long long blocks = (v.T + 255) / 256;
+  k_setup_c<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(nr, v.T, v.Fr, v.Dr, v.Chat);
+  return cudaGetLastError();
+}
+
 }  // namespace rlt2
 
 using namespace rlt2;
@@ -345,6 +353,40 @@ static void ctx_free(rlt2_ctx* c) {
   delete c;
 }
 
+static IterView view_of(const rlt2_ctx* c) {
+  IterView v{};
+  v.n = c->n;
+  v.m = c->m;
+  v.T = c->T;
+  v.E = c->E;
+  v.ntrip = c->ntrip;
+  v.prm = c->prm;
+  v.d_cst = c->d_cst;
+  v.Fr = c->Fr;
+  v.Dr = c->Dr;
+  v.bprime = c->bprime;
+  v.Chat = c->Chat;
+  v.Dhat = c->Dhat;
+  v.Theta = c->Theta;
+  v.xi = c->xi;
+  v.psi = c->psi;
+  v.Delta = c->Delta;
+  v.gamma = c->gamma;
+  v.delta = c->delta;
+  v.alpha = c->alpha;
+  v.beta = c->beta;
+  v.pix = c->pix;
+  v.piy = c->piy;
+  v.tterm = c->tterm;
+  v.xval = c->xval;
+  v.ring = c->ring;
+  v.xperm = c->xperm;
+  v.ubperm = c->ubperm;
+  v.trips = c->trips;
+  v.sc = c->sc;
+  return v;
+}
+
 static bool finite_all(const double* x, size_t k) {
   for (size_t i = 0; i < k; ++i)
     if (!std::isfinite(x[i])) return false;
@@ -365,7 +407,7 @@ extern "C" void rlt2_params_default(rlt2_params* p) {
   p->feas_tol = 1e-9;
 }
 
-static bool params_ok(const rlt2_params& p) {
+bool rlt2::params_valid(const rlt2_params& p) {
   auto in01 = [](double x) { return std::isfinite(x) && x >= 0.0 && x <= 1.0; };
   if (!in01(p.kz) || !in01(p.ky) || !in01(p.kx) || !in01(p.phi_y)) return false;
   if (p.phi_y + p.ky > 1.0) return false;
@@ -411,7 +453,7 @@ extern "C" rlt2_status rlt2_create(int n, const double* F, const double* D, cons
   rlt2_params prm;
   rlt2_params_default(&prm);
   if (p) prm = *p;
-  if (!params_ok(prm)) {
+  if (!params_valid(prm)) {
     set_error("rlt2_create: parameters out of range (kappa, phi in [0,1], phi_y+ky<=1, sum phi_z = 1)");
     return RLT2_EINVAL;
   }
@@ -552,11 +594,8 @@ extern "C" rlt2_status rlt2_create(int n, const double* F, const double* D, cons
   const int* dloc = dint + nr;
   const int* dfixf = dint + 2 * nr;
   const int* dfixl = dint + 2 * nr + nfix;
-  k_setup_b<<<(int)((n2 + 127) / 128), 128, 0, s>>>(n, nr, dF, dD, dB, dfac, dloc, dfixf, dfixl, nfix, c->bprime,
-                                                     c->Fr, c->Dr);
-  k_setup_const<<<1, 32, 0, s>>>(n, dF, dD, dB, dfixf, dfixl, nfix, c->d_cst);
-  k_setup_c<<<(int)((T + 255) / 256 < 4096 ? (T + 255) / 256 : 4096), 256, 0, s>>>(nr, c->T, c->Fr, c->Dr, c->Chat);
-  e = cudaGetLastError();
+  e = enqueue_setup(view_of(c), n, dF, dD, dB, dfac, dloc, dfixf, dfixl, nfix, s);
+  if (e == cudaSuccess) e = cudaGetLastError();
   cudaError_t e3 = cudaStreamSynchronize(s);
   cleanup_tmp();
   if (e != cudaSuccess) return fail(e, "setup kernels");
@@ -568,17 +607,17 @@ extern "C" rlt2_status rlt2_create(int n, const double* F, const double* D, cons
   return RLT2_OK;
 }
 
-// Enqueue one iteration (six kernels) on stream s.  With timing, events bracket
-// every kernel (ev_base indexes the event pool).
-static cudaError_t enqueue_iteration(rlt2_ctx* c, cudaStream_t s, int ev_base) {
-  const int n = c->n, m = c->m;
-  const long long T = c->T;
-  const rlt2_params& p = c->prm;
-  const int* done = &c->sc->done;
+// Enqueue one iteration (six kernels) on stream s.  With ev != nullptr, the 12
+// events ev[2k], ev[2k+1] bracket kernel k.
+cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent_t* ev) {
+  const int n = v.n, m = v.m;
+  const long long T = v.T;
+  const rlt2_params& p = v.prm;
+  const int* done = &v.sc->done;
   cudaError_t e;
   auto rec = [&](int k, int which) -> cudaError_t {
-    if (ev_base < 0) return cudaSuccess;
-    return cudaEventRecord(c->ev[ev_base + 2 * k + which], s);
+    if (!ev) return cudaSuccess;
+    return cudaEventRecord(ev[2 * k + which], s);
   };
   // 1) y move + tile terms
   const double cy = p.ky / (double)(n - 2);
@@ -586,8 +625,8 @@ static cudaError_t enqueue_iteration(rlt2_ctx* c, cudaStream_t s, int ev_base) {
   if ((e = rec(0, 0)) != cudaSuccess) return e;
   {
     const long long blocks = (T + 255) / 256;
-    k_move_y<<<(int)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(n, T, cy, cx, p.phi_y, c->piy, c->pix, c->Chat,
-                                                                    c->tterm, c->sc);
+    k_move_y<<<(int)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(n, T, cy, cx, p.phi_y, v.piy, v.pix, v.Chat,
+                                                                    v.tterm, v.sc);
   }
   if ((e = cudaGetLastError()) != cudaSuccess || (e = rec(0, 1)) != cudaSuccess) return e;
   // 2) z move
@@ -599,27 +638,27 @@ static cudaError_t enqueue_iteration(rlt2_ctx* c, cudaStream_t s, int ev_base) {
   mz.kz_one = (p.kz == 1.0);
   mz.uniform = (p.phi_z[0] == p.phi_z[1] && p.phi_z[0] == p.phi_z[2] && p.phi_z[0] == p.phi_z[3] &&
                 p.phi_z[0] == p.phi_z[4]);
-  mz.Dhat = c->Dhat;
-  mz.xi = c->xi;
-  mz.psi = c->psi;
-  mz.tterm = c->tterm;
-  mz.trips = c->trips;
-  mz.sc = c->sc;
+  mz.Dhat = v.Dhat;
+  mz.xi = v.xi;
+  mz.psi = v.psi;
+  mz.tterm = v.tterm;
+  mz.trips = v.trips;
+  mz.sc = v.sc;
   if ((e = rec(1, 0)) != cudaSuccess) return e;
-  k_move_z<<<c->ntrip * n, 128, 0, s>>>(mz);
+  k_move_z<<<v.ntrip * n, 128, 0, s>>>(mz);
   if ((e = cudaGetLastError()) != cudaSuccess || (e = rec(1, 1)) != cudaSuccess) return e;
   // 3) Z stage
   LapArgs z{};
   z.batch = T;
   z.m = m;
-  z.A = c->Dhat;
-  z.u0 = p.warm ? c->xi : nullptr;
-  z.warm_gate = &c->sc->have_snap;
-  z.value = c->Theta;
-  z.u = c->xi;
-  z.v = c->psi;
+  z.A = v.Dhat;
+  z.u0 = p.warm ? v.xi : nullptr;
+  z.warm_gate = &v.sc->have_snap;
+  z.value = v.Theta;
+  z.u = v.xi;
+  z.v = v.psi;
   z.dual_mode = p.dual_mode;
-  z.stats = c->sc->stats + 0;
+  z.stats = v.sc->stats + 0;
   z.skip = done;
   if ((e = rec(2, 0)) != cudaSuccess) return e;
   if ((e = launch_lap(z, s)) != cudaSuccess) return e;
@@ -628,14 +667,14 @@ static cudaError_t enqueue_iteration(rlt2_ctx* c, cudaStream_t s, int ev_base) {
   LapArgs y{};
   y.batch = (long long)n * n;
   y.m = n - 1;
-  y.A = c->Chat;
-  y.Badd = c->Theta;
-  y.value = c->Delta;
-  y.u = c->gamma;
-  y.v = c->delta;
-  y.pi = c->piy;
+  y.A = v.Chat;
+  y.Badd = v.Theta;
+  y.value = v.Delta;
+  y.u = v.gamma;
+  y.v = v.delta;
+  y.pi = v.piy;
   y.dual_mode = p.dual_mode;
-  y.stats = c->sc->stats + 2;
+  y.stats = v.sc->stats + 2;
   y.skip = done;
   if ((e = rec(3, 0)) != cudaSuccess) return e;
   if ((e = launch_lap(y, s)) != cudaSuccess) return e;
@@ -644,15 +683,15 @@ static cudaError_t enqueue_iteration(rlt2_ctx* c, cudaStream_t s, int ev_base) {
   LapArgs x{};
   x.batch = 1;
   x.m = n;
-  x.A = c->bprime;
-  x.Badd = c->Delta;
-  x.value = c->xval;
-  x.u = c->alpha;
-  x.v = c->beta;
-  x.r2c = c->xperm;
-  x.pi = c->pix;
+  x.A = v.bprime;
+  x.Badd = v.Delta;
+  x.value = v.xval;
+  x.u = v.alpha;
+  x.v = v.beta;
+  x.r2c = v.xperm;
+  x.pi = v.pix;
   x.dual_mode = p.dual_mode;
-  x.stats = c->sc->stats + 4;
+  x.stats = v.sc->stats + 4;
   x.skip = done;
   if ((e = rec(4, 0)) != cudaSuccess) return e;
   if ((e = launch_lap(x, s)) != cudaSuccess) return e;
@@ -661,33 +700,37 @@ static cudaError_t enqueue_iteration(rlt2_ctx* c, cudaStream_t s, int ev_base) {
   FinArgs f{};
   f.n = n;
   f.m = m;
-  f.cst = c->d_cst;
-  f.xval = c->xval;
-  f.xperm = c->xperm;
-  f.ubperm = c->ubperm;
-  f.piy = c->piy;
-  f.Dhat = c->Dhat;
-  f.xi = c->xi;
-  f.psi = c->psi;
-  f.Fr = c->Fr;
-  f.Dr = c->Dr;
-  f.bprime = c->bprime;
-  f.ring = c->ring;
+  f.cst = v.d_cst;
+  f.xval = v.xval;
+  f.xperm = v.xperm;
+  f.ubperm = v.ubperm;
+  f.piy = v.piy;
+  f.Dhat = v.Dhat;
+  f.xi = v.xi;
+  f.psi = v.psi;
+  f.Fr = v.Fr;
+  f.Dr = v.Dr;
+  f.bprime = v.bprime;
+  f.ring = v.ring;
   f.min_gap = p.min_gap;
   f.ub_known = p.ub;
   f.feas_tol = p.feas_tol;
-  f.sc = c->sc;
+  f.sc = v.sc;
   if ((e = rec(5, 0)) != cudaSuccess) return e;
   k_finalize<<<1, 256, 0, s>>>(f);
   if ((e = cudaGetLastError()) != cudaSuccess || (e = rec(5, 1)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
+static cudaError_t enqueue_iteration_ctx(rlt2_ctx* c, cudaStream_t s, int ev_base) {
+  return enqueue_iteration(view_of(c), s, ev_base < 0 ? nullptr : c->ev.data() + ev_base);
+}
+
 static rlt2_status build_graph(rlt2_ctx* c) {
   if (c->graph) return RLT2_OK;
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = enqueue_iteration(c, c->cap_stream, -1);
+  cudaError_t e = enqueue_iteration_ctx(c, c->cap_stream, -1);
   cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
   if (e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -711,7 +754,7 @@ static rlt2_status enqueue_many(rlt2_ctx* c, int iters) {
     for (int base = 0; base < iters; base += kEvChunk) {
       const int cnt = (iters - base) < kEvChunk ? (iters - base) : kEvChunk;
       for (int it = 0; it < cnt; ++it) {
-        cudaError_t e = enqueue_iteration(c, c->stream, it * kKinds * 2);
+        cudaError_t e = enqueue_iteration_ctx(c, c->stream, it * kKinds * 2);
         if (e != cudaSuccess) return cuda_fail(e, "enqueue_iteration");
       }
       CK(cudaEventSynchronize(c->ev[(cnt - 1) * kKinds * 2 + 2 * (kKinds - 1) + 1]));

@@ -34,6 +34,36 @@ cudaError_t prepare_lap(int m);
 // Enqueue the batched LAP kernel (grid sized for the device); returns the CUDA error.
 cudaError_t launch_lap(const LapArgs& a, cudaStream_t s);
 
+constexpr int kRing = 1 << 16;  // bound-history ring (entries)
+
+// Device-resident scalars of one dual ascent.
+struct DevScalars {
+  double lb, best_lb, ub, gap;
+  int iter, done, have_snap, reason;
+  unsigned long long stats[6];  // Z aug, Z relax, Y aug, Y relax, X aug, X relax
+};
+
+// Every device buffer one dual ascent works on (layouts as in rlt2.h).
+struct IterView {
+  int n, m;
+  long long T, E;
+  int ntrip;
+  rlt2_params prm;
+  double *d_cst, *Fr, *Dr, *bprime, *Chat, *Dhat, *Theta, *xi, *psi, *Delta, *gamma, *delta;
+  double *alpha, *beta, *pix, *piy, *tterm, *xval, *ring;
+  int *xperm, *ubperm, *trips;
+  DevScalars* sc;
+};
+
+// Step A0 (setup kernels) and one iteration (six kernels) on a view.
+cudaError_t enqueue_setup(const IterView& v, int n_full, const double* dF, const double* dD, const double* dB,
+                          const int* dfac, const int* dloc, const int* dfixf, const int* dfixl, int nfix,
+                          cudaStream_t s);
+cudaError_t enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent_t* ev);
+
+// Parameter validation shared by the entry points.
+bool params_valid(const rlt2_params& p);
+
 // Thread-local last error text.
 void set_error(const std::string& msg);
 rlt2_status cuda_fail(cudaError_t e, const char* what);

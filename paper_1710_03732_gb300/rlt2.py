@@ -40,8 +40,8 @@ _vp = ctypes.c_void_p
 
 EXPORTS = ["rlt2_params_default", "rlt2_create", "rlt2_iterate", "rlt2_iterate_async", "rlt2_bound", "rlt2_duals",
            "rlt2_reduced_costs", "rlt2_export_state", "rlt2_import_state", "rlt2_stats", "rlt2_sizes",
-           "rlt2_set_timing", "rlt2_kernel_times", "rlt2_destroy", "rlt2_lap_batched", "rlt2_strerror",
-           "rlt2_last_error"]
+           "rlt2_set_timing", "rlt2_kernel_times", "rlt2_destroy", "rlt2_lap_batched", "rlt2_iterate_noalloc",
+           "rlt2_strerror", "rlt2_last_error"]
 
 
 def lib():
@@ -69,6 +69,8 @@ def lib():
     L.rlt2_kernel_times.argtypes = [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     L.rlt2_destroy.argtypes = [_vp]
     L.rlt2_lap_batched.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
+    L.rlt2_iterate_noalloc.argtypes = [ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(rlt2_params), ctypes.c_int, _vp,
+                                       _vp]
     L.rlt2_strerror.argtypes = [ctypes.c_int]
     L.rlt2_strerror.restype = ctypes.c_char_p
     L.rlt2_last_error.restype = ctypes.c_char_p
@@ -210,6 +212,14 @@ def rlt2_lap_batched(cost, value, u0=None, u=None, v=None, row_to_col=None, n_au
     batch, m = int(cost.shape[0]), int(cost.shape[1])
     _check(lib().rlt2_lap_batched(batch, m, _ptr(cost), _ptr(u0), _ptr(value), _ptr(u), _ptr(v), _ptr(row_to_col),
                                   _ptr(n_aug), dual_mode, _stream(stream)), "rlt2_lap_batched")
+
+
+def rlt2_iterate_noalloc(F, D, lb_hist, B=None, prm: Optional[rlt2_params] = None, stream=None):
+    """Dual ascent with no device allocation (n <= 10).  F, D, B, lb_hist: CUDA
+    float64 tensors; the number of iterations is len(lb_hist).  Asynchronous."""
+    n = int(F.shape[0])
+    _check(lib().rlt2_iterate_noalloc(n, _ptr(F), _ptr(D), _ptr(B), None if prm is None else ctypes.byref(prm),
+                                      int(lb_hist.shape[0]), _ptr(lb_hist), _stream(stream)), "rlt2_iterate_noalloc")
 
 
 # ------------------------------------------------------------ convenience ----
