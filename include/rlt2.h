@@ -64,7 +64,12 @@ typedef enum {
  *  ub         : known upper bound on the node's QAP value (<= 0: unknown)
  *  feas_tol   : tolerance of the feasibility check after Algorithm 1
  *               (relative to max(1, |LB|)); the check stops the ascent when
- *               every y and z of the X-LAP primal has |reduced cost| <= tol */
+ *               every y and z of the X-LAP primal has |reduced cost| <= tol
+ *               (<= 0 disables it)
+ *  stall_window, stall_tol : early termination of the branch-and-bound
+ *               experiments (Section 5): stop once the best bound improved by
+ *               less than stall_tol * |UB| over the last stall_window
+ *               iterations (stall_window <= 0 disables it; at most 64) */
 typedef struct rlt2_params {
   double kz, ky, kx, phi_y;
   double phi_z[5];
@@ -73,12 +78,15 @@ typedef struct rlt2_params {
   double min_gap;
   double ub;
   double feas_tol;
+  int stall_window;
+  double stall_tol;
 } rlt2_params;
 
 typedef struct rlt2_ctx rlt2_ctx;
 
 /* Default parameters: kz = kx = 1, ky = 1/2, phi_y = 1/2, phi_z = 1/5 each,
- * canonical duals, cold start, min_gap = 0, ub unknown, feas_tol = 1e-9. */
+ * canonical duals, cold start, min_gap = 0, ub unknown, feas_tol = 1e-9,
+ * no stall stop (stall_window = 0, stall_tol = 0.0002). */
 void rlt2_params_default(rlt2_params* p);
 
 /* Create a dual-ascent context for one QAP node (Eq. 1.1; a branch-and-bound

@@ -219,7 +219,8 @@ struct FinArgs {
   const double* Dr;
   const double* bprime;
   double* ring;
-  double min_gap, ub_known, feas_tol;
+  double min_gap, ub_known, feas_tol, stall_tol;
+  int stall_window;
   DevScalars* sc;
 };
 
@@ -285,12 +286,18 @@ __global__ void k_finalize(FinArgs a) {
     double ubk = sc->ub;
     if (a.ub_known > 0.0 && a.ub_known < ubk) ubk = a.ub_known;
     sc->gap = (ubk - sc->best_lb) / fabs(ubk);
+    sc->best_hist[it % kStallRing] = sc->best_lb;
     if (!bad) {
       sc->done = 1;
       sc->reason = 1;
     } else if (a.min_gap > 0.0 && sc->gap < a.min_gap) {
       sc->done = 1;
       sc->reason = 2;
+    } else if (a.stall_window > 0 && it >= a.stall_window &&
+               sc->best_lb - sc->best_hist[(it - a.stall_window) % kStallRing] <
+                   a.stall_tol * fmax(1.0, fabs(ubk))) {
+      sc->done = 1;
+      sc->reason = 3;
     }
   }
 }
@@ -405,6 +412,8 @@ extern "C" void rlt2_params_default(rlt2_params* p) {
   p->min_gap = 0.0;
   p->ub = 0.0;
   p->feas_tol = 1e-9;
+  p->stall_window = 0;
+  p->stall_tol = 0.0002;
 }
 
 bool rlt2::params_valid(const rlt2_params& p) {
@@ -420,6 +429,7 @@ bool rlt2::params_valid(const rlt2_params& p) {
   if (p.dual_mode != 0 && p.dual_mode != 1) return false;
   if (p.warm != 0 && p.warm != 1) return false;
   if (!std::isfinite(p.min_gap) || !std::isfinite(p.ub) || !std::isfinite(p.feas_tol)) return false;
+  if (p.stall_window < 0 || p.stall_window >= kStallRing || !std::isfinite(p.stall_tol)) return false;
   return true;
 }
 
@@ -715,6 +725,8 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   f.min_gap = p.min_gap;
   f.ub_known = p.ub;
   f.feas_tol = p.feas_tol;
+  f.stall_window = p.stall_window;
+  f.stall_tol = p.stall_tol;
   f.sc = v.sc;
   if ((e = rec(5, 0)) != cudaSuccess) return e;
   k_finalize<<<1, 256, 0, s>>>(f);

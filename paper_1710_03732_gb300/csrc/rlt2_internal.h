@@ -37,10 +37,12 @@ cudaError_t launch_lap(const LapArgs& a, cudaStream_t s);
 constexpr int kRing = 1 << 16;  // bound-history ring (entries)
 
 // Device-resident scalars of one dual ascent.
+constexpr int kStallRing = 64;  // best-bound history for the stall rule
 struct DevScalars {
   double lb, best_lb, ub, gap;
   int iter, done, have_snap, reason;
   unsigned long long stats[6];  // Z aug, Z relax, Y aug, Y relax, X aug, X relax
+  double best_hist[kStallRing];  // best bound after iteration it, at it % kStallRing
 };
 
 // Every device buffer one dual ascent works on (layouts as in rlt2.h).

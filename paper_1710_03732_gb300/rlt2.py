@@ -24,7 +24,7 @@ class rlt2_params(ctypes.Structure):
     _fields_ = [("kz", ctypes.c_double), ("ky", ctypes.c_double), ("kx", ctypes.c_double),
                 ("phi_y", ctypes.c_double), ("phi_z", ctypes.c_double * 5), ("dual_mode", ctypes.c_int),
                 ("warm", ctypes.c_int), ("min_gap", ctypes.c_double), ("ub", ctypes.c_double),
-                ("feas_tol", ctypes.c_double)]
+                ("feas_tol", ctypes.c_double), ("stall_window", ctypes.c_int), ("stall_tol", ctypes.c_double)]
 
 
 class Rlt2Error(RuntimeError):
@@ -113,13 +113,14 @@ def _stream(stream) -> Optional[int]:
 
 
 def params(kz=1.0, ky=0.5, kx=1.0, phi_y=0.5, phi_z=(0.2,) * 5, dual_mode=1, warm=0, min_gap=0.0, ub=0.0,
-           feas_tol=1e-9) -> rlt2_params:
+           feas_tol=1e-9, stall_window=0, stall_tol=0.0002) -> rlt2_params:
     p = rlt2_params()
     lib().rlt2_params_default(ctypes.byref(p))
     p.kz, p.ky, p.kx, p.phi_y = kz, ky, kx, phi_y
     for i, x in enumerate(phi_z):
         p.phi_z[i] = x
     p.dual_mode, p.warm, p.min_gap, p.ub, p.feas_tol = dual_mode, warm, min_gap, ub, feas_tol
+    p.stall_window, p.stall_tol = stall_window, stall_tol
     return p
 
 

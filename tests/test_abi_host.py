@@ -45,6 +45,7 @@ def test_params_default(L):
     p = rlt2.rlt2_params()
     L.rlt2_params_default(ctypes.byref(p))
     assert (p.kz, p.ky, p.kx, p.phi_y, p.dual_mode, p.warm) == (1.0, 0.5, 1.0, 0.5, 1, 0)
+    assert (p.stall_window, p.stall_tol, p.feas_tol) == (0, 0.0002, 1e-9)
     assert abs(sum(p.phi_z) - 1.0) < 1e-15
 
 
@@ -80,7 +81,8 @@ def test_create_rejects_bad_input(L):
 
 
 @pytest.mark.parametrize("field,value", [("kz", 1.5), ("ky", -0.1), ("phi_y", 0.8), ("dual_mode", 3),
-                                         ("warm", 7), ("phi_sum", 0.9)])
+                                         ("warm", 7), ("phi_sum", 0.9), ("stall_window", 64),
+                                         ("stall_window", -1)])
 def test_create_rejects_bad_params(L, field, value):
     p = rlt2.rlt2_params()
     L.rlt2_params_default(ctypes.byref(p))

@@ -324,3 +324,63 @@ def test_n20_full_size_sampled(R):
         assert abs(xi.sum() + psi.sum() - o.value) <= 1e-9 * scale * m
         assert (tile - xi[:, None] - psi[None, :]).min() >= -1e-9 * scale
         assert np.allclose(xi, o.u, atol=1e-9 * scale) and np.allclose(psi, o.v, atol=1e-9 * scale)
+
+
+def test_stall_and_gap_stops(R):
+    """Early termination (Section 5): the ascent stops once the best bound gains less
+    than stall_tol*|UB| over stall_window iterations; min_gap stops on the gap."""
+    inst = I.config(2)
+    with R.Context(inst.F, inst.D, inst.B, prm=R.params(feas_tol=0.0)) as ctx:
+        full, _ = ctx.iterate(200)
+        _, _, ub, _, _, _ = ctx.bound()
+    W, tol = 10, 0.0005
+    with R.Context(inst.F, inst.D, inst.B, prm=R.params(feas_tol=0.0, stall_window=W, stall_tol=tol)) as ctx:
+        lbs, done = ctx.iterate(200)
+        st = ctx.stats()
+        _, _, ub2, _, _, _ = ctx.bound()
+    assert st[7] == 3 and W < done < 200
+    assert np.array_equal(lbs[:done], full[:done])       # same trajectory up to the stop
+    best = np.maximum.accumulate(full)
+    k = done - 1
+    assert best[k] - best[k - W] < tol * ub2             # the rule fired at k ...
+    assert all(best[j] - best[j - W] >= tol * ub2 for j in range(W, k))   # ... and not before (same UB seen)
+    gap_stop = (ub - best[60]) / ub * (1 + 1e-9)
+    with R.Context(inst.F, inst.D, inst.B, prm=R.params(feas_tol=0.0, min_gap=gap_stop, ub=ub)) as ctx:
+        _, done = ctx.iterate(200)
+        assert ctx.stats()[7] == 2 and done <= 61
+
+
+def test_n30_full_size_sampled(R):
+    """n = 30, Manhattan 5x6 grid (756,900 Z-LAPs of size 28, 4.75 GB z array): the
+    first bound equals the Gilmore-Lawler closed form, the second matches the
+    oracle within 1e-6, sampled Z-LAPs re-solved by the oracle LAP."""
+    from scipy.optimize import linear_sum_assignment
+    inst = I.config(5)
+    n = 30
+    F, Dm = inst.F, inst.D
+    L = np.zeros((n, n))
+    for i in range(n):
+        for p in range(n):
+            L[i, p] = F[i, i] * Dm[p, p] + float(np.dot(np.sort(np.delete(F[i], i)), np.sort(np.delete(Dm[p], p))[::-1]))
+    r, c = linear_sum_assignment(L)
+    gl = L[r, c].sum()
+    with R.Context(inst.F, inst.D, inst.B, prm=R.params(feas_tol=0.0, warm=1)) as ctx:
+        lbs, _ = ctx.iterate(2)
+        m = n - 2
+        T = ctx.T
+        rng = np.random.default_rng(3)
+        pick = rng.choice(T, 60, replace=False)
+        D, _ = ctx.export_state()
+        tiles = {int(t): D[t * m * m:(t + 1) * m * m].reshape(m, m).copy() for t in pick}
+        del D
+        duals = ctx.duals()
+    assert abs(lbs[0] - gl) <= 1e-9 * gl
+    _, ref, _ = O.run(inst.F, inst.D, inst.B, iters=2, dual_mode=1, threads=O.max_threads() or 1)
+    assert np.max(np.abs(lbs - np.array(ref)) / np.abs(ref)) <= 1e-6
+    for t, tile in tiles.items():
+        o = O.lap(tile, canonical=True)
+        xi, psi = duals["xi"][t * m:(t + 1) * m], duals["psi"][t * m:(t + 1) * m]
+        scale = max(1.0, np.abs(tile).max())
+        assert abs(xi.sum() + psi.sum() - o.value) <= 1e-9 * scale * m
+        assert (tile - xi[:, None] - psi[None, :]).min() >= -1e-9 * scale
+        assert np.allclose(xi, o.u, atol=1e-9 * scale) and np.allclose(psi, o.v, atol=1e-9 * scale)
