@@ -7,105 +7,147 @@
 
 namespace rlt2 {
 
-constexpr int kWarpsPerBlock = 8;
+constexpr int kMaxWarpsPerBlock = 8;
 
 __host__ __device__ inline int tile_ld(int m) { return m | 1; }  // odd stride: conflict-free rows and columns
 
-// Shared memory per warp: the tile, u/v staging (64 doubles) and 32 ints.
-__host__ __device__ inline size_t warp_smem_bytes(int m) {
-  return (size_t)m * tile_ld(m) * sizeof(double) + 64 * sizeof(double) + 32 * sizeof(int);
+// Shared memory per warp: 32/G tiles, u/v staging (64 doubles) and 32 ints.
+__host__ __device__ inline size_t warp_smem_bytes(int m, int G) {
+  return (size_t)(32 / G) * m * tile_ld(m) * sizeof(double) + 64 * sizeof(double) + 32 * sizeof(int);
 }
 
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_lap(LapArgs a) {
+int default_group(int m) { return m <= 8 ? 8 : (m <= 16 ? 16 : 32); }
+
+// Grid-stride over LAPs, 32/G LAPs per warp per step; each group of G lanes
+// stages its own tile (coalesced: a group reads a contiguous m*m run).
+template <int G>
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap(LapArgs a) {
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int per = 32 / G;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
+  const int wpb = blockDim.x >> 5;
+  const int grp = lane / G, gl = lane & (G - 1);
   const int m = a.m;
   const int ld = tile_ld(m);
-  unsigned char* base = smem_raw + (size_t)wib * warp_smem_bytes(m);
-  double* cs = reinterpret_cast<double*>(base);
-  double* uv = cs + (size_t)m * ld;  // [0..31] u, [32..63] v
-  int* scr = reinterpret_cast<int*>(uv + 64);
+  unsigned char* base = smem_raw + (size_t)wib * warp_smem_bytes(m, G);
+  double* tile = reinterpret_cast<double*>(base) + (size_t)grp * m * ld;
+  double* uv = reinterpret_cast<double*>(base) + (size_t)per * m * ld;  // [0..31] u, [32..63] v
+  int* scr = reinterpret_cast<int*>(uv + 64) + grp * G;
   const bool warm = a.u0 != nullptr && (a.warm_gate == nullptr || *a.warm_gate != 0);
-  const long long nwarps = (long long)gridDim.x * kWarpsPerBlock;
+  const long long nwarps = (long long)gridDim.x * wpb;
   const int mm = m * m;
   unsigned long long aug_acc = 0, relax_acc = 0;
 
-  for (long long t = (long long)blockIdx.x * kWarpsPerBlock + wib; t < a.batch; t += nwarps) {
-    const double* src = a.A + t * mm;
-    const double* add = a.Badd ? a.Badd + t * mm : nullptr;
-    for (int e = lane; e < mm; e += 32) {
-      const int r = e / m, c = e - r * m;
-      double x = __ldcs(src + e);
-      if (add) x = __dadd_rn(x, __ldcs(add + e));
-      cs[r * ld + c] = x;
+  for (long long t0 = ((long long)blockIdx.x * wpb + wib) * per; t0 < a.batch; t0 += nwarps * per) {
+    const long long t = t0 + grp;
+    const bool have = t < a.batch;
+    if (have) {
+      const double* src = a.A + t * mm;
+      const double* add = a.Badd ? a.Badd + t * mm : nullptr;
+      for (int e = gl; e < mm; e += G) {
+        const int r = e / m, c = e - r * m;
+        double x = __ldcs(src + e);
+        if (add) x = __dadd_rn(x, __ldcs(add + e));
+        tile[r * ld + c] = x;
+      }
     }
     double u0 = 0.0;
-    if (warm && lane < m) u0 = a.u0[t * m + lane];
+    if (warm && have && gl < m) u0 = a.u0[t * m + gl];
     __syncwarp();
-    const WarpLapResult R = warp_lap(cs, ld, m, lane, warm, u0, a.dual_mode, scr);
-    if (lane < m) {
-      if (a.u) a.u[t * m + lane] = R.u;
-      if (a.v) a.v[t * m + lane] = R.v;
-      if (a.r2c) a.r2c[t * m + lane] = R.r2c;
+    const WarpLapResult R = group_lap<G>(tile, ld, have ? m : 0, lane, warm, u0, a.dual_mode, scr);
+    if (have && gl < m) {
+      if (a.u) a.u[t * m + gl] = R.u;
+      if (a.v) a.v[t * m + gl] = R.v;
+      if (a.r2c) a.r2c[t * m + gl] = R.r2c;
     }
-    if (lane == 0) {
+    if (have && gl == 0) {
       a.value[t] = R.value;
       if (a.naug) a.naug[t] = R.naug;
+      aug_acc += R.naug;
+      relax_acc += R.nrelax;
     }
     if (a.pi) {
       uv[lane] = R.u;
       uv[32 + lane] = R.v;
       __syncwarp();
-      double* dst = a.pi + t * mm;
-      for (int e = lane; e < mm; e += 32) {
-        const int r = e / m, c = e - r * m;
-        dst[e] = __dsub_rn(__dsub_rn(cs[r * ld + c], uv[r]), uv[32 + c]);
+      if (have) {
+        double* dst = a.pi + t * mm;
+        const double* ug = uv + grp * G;
+        const double* vg = uv + 32 + grp * G;
+        for (int e = gl; e < mm; e += G) {
+          const int r = e / m, c = e - r * m;
+          dst[e] = __dsub_rn(__dsub_rn(tile[r * ld + c], ug[r]), vg[c]);
+        }
       }
     }
-    aug_acc += R.naug;
-    relax_acc += R.nrelax;
     __syncwarp();
   }
-  if (a.stats && lane == 0 && (aug_acc | relax_acc)) {
+  if (a.stats && gl == 0 && (aug_acc | relax_acc)) {
     atomicAdd(a.stats + 0, aug_acc);
     atomicAdd(a.stats + 1, relax_acc);
   }
 }
 
-static int g_grid_cap[33];  // blocks per device for each LAP size (0 = not configured)
+// blocks per SM for (m, G, warps per block), 0 = not configured
+static int g_occ[33][3][2];
 
-cudaError_t prepare_lap(int m) {
-  if (m < 1 || m > 32) return cudaErrorInvalidValue;
-  if (g_grid_cap[m] > 0) return cudaSuccess;
-  static bool attr_set = false;
+static int gidx(int G) { return G == 8 ? 0 : (G == 16 ? 1 : 2); }
+
+template <int G>
+static cudaError_t prepare_one(int m, int wpb) {
+  int& slot = g_occ[m][gidx(G)][wpb == 4 ? 0 : 1];
+  if (slot > 0) return cudaSuccess;
+  static bool attr_set[3] = {false, false, false};
   cudaError_t e;
-  if (!attr_set) {
-    e = cudaFuncSetAttribute(k_lap, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(warp_smem_bytes(32) * kWarpsPerBlock));
+  if (!attr_set[gidx(G)]) {
+    e = cudaFuncSetAttribute(k_lap<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(warp_smem_bytes(32, 32) * kMaxWarpsPerBlock > warp_smem_bytes(G, G) * kMaxWarpsPerBlock
+                                       ? warp_smem_bytes(32, 32) * kMaxWarpsPerBlock
+                                       : warp_smem_bytes(G, G) * kMaxWarpsPerBlock));
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set[gidx(G)] = true;
   }
-  int dev = 0, sms = 0, occ = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lap, kWarpsPerBlock * 32,
-                                                    warp_smem_bytes(m) * kWarpsPerBlock);
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lap<G>, wpb * 32, warp_smem_bytes(m, G) * wpb);
   if (e != cudaSuccess) return e;
-  g_grid_cap[m] = sms * (occ < 1 ? 1 : occ);
+  slot = occ < 1 ? 1 : occ;
   return cudaSuccess;
+}
+
+static int g_sms = 0;
+
+cudaError_t prepare_lap(int m, int group, int warps_per_block) {
+  if (m < 1 || m > 32) return cudaErrorInvalidValue;
+  const int G = group ? group : default_group(m);
+  const int wpb = warps_per_block ? warps_per_block : kMaxWarpsPerBlock;
+  if (G < m || (G != 8 && G != 16 && G != 32) || (wpb != 4 && wpb != 8)) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if (!g_sms) {
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  }
+  if (G == 8) return prepare_one<8>(m, wpb);
+  if (G == 16) return prepare_one<16>(m, wpb);
+  return prepare_one<32>(m, wpb);
 }
 
 cudaError_t launch_lap(const LapArgs& a, cudaStream_t s) {
   if (a.batch <= 0) return cudaSuccess;
-  cudaError_t e = prepare_lap(a.m);
+  const int G = a.group ? a.group : default_group(a.m);
+  const int wpb = a.warps_per_block ? a.warps_per_block : kMaxWarpsPerBlock;
+  cudaError_t e = prepare_lap(a.m, G, wpb);
   if (e != cudaSuccess) return e;
-  const size_t smem = warp_smem_bytes(a.m) * kWarpsPerBlock;
-  const long long need = (a.batch + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  const long long cap = g_grid_cap[a.m];
+  const size_t smem = warp_smem_bytes(a.m, G) * wpb;
+  const long long per_block = (long long)wpb * (32 / G);
+  const long long need = (a.batch + per_block - 1) / per_block;
+  const long long cap = (long long)g_sms * g_occ[a.m][gidx(G)][wpb == 4 ? 0 : 1];
   const int grid = (int)(need < cap ? need : cap);
-  k_lap<<<grid, kWarpsPerBlock * 32, smem, s>>>(a);
+  if (G == 8) k_lap<8><<<grid, wpb * 32, smem, s>>>(a);
+  else if (G == 16) k_lap<16><<<grid, wpb * 32, smem, s>>>(a);
+  else k_lap<32><<<grid, wpb * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -25,11 +25,16 @@ struct LapArgs {
   int dual_mode;             // 0 raw, 1 canonical
   unsigned long long* stats; // nullable, [0] += augmentations, [1] += relaxations
   const int* skip;           // nullable: kernel does nothing when *skip != 0
+  int group;                 // lanes per LAP (8, 16 or 32); 0 = smallest that fits m
+  int warps_per_block;       // 4 or 8; 0 = 8
 };
+
+// Lanes per LAP the launcher would pick for size m (8, 16 or 32).
+int default_group(int m);
 
 // Configure the LAP kernel for size m (shared-memory limit, occupancy); call
 // outside stream capture before the first launch of that size.
-cudaError_t prepare_lap(int m);
+cudaError_t prepare_lap(int m, int group = 0, int warps_per_block = 0);
 
 // Enqueue the batched LAP kernel (grid sized for the device); returns the CUDA error.
 cudaError_t launch_lap(const LapArgs& a, cudaStream_t s);

@@ -1,7 +1,8 @@
-// Warp-per-LAP Hungarian for sm_103a (GB300).
+// Warp-level (group-per-LAP) Hungarian for sm_103a (GB300).
 //
 // Every LAP of the RLT2 dual ascent is small (Z: n-2, Y: n-1, X: n; n <= 32), so
-// one warp owns one LAP: lane c holds column c (dual v_c, Dijkstra label d_c,
+// a group of G = 8, 16 or 32 lanes owns one LAP (32/G LAPs per warp, in
+// lockstep): lane c holds column c (dual v_c, Dijkstra label d_c,
 // predecessor row, "scanned" flag, matched row) and lane r holds row r (dual
 // u_r, matched column).  The cost tile sits in shared memory with an odd row
 // stride so that both row reads (lanes = columns) and column reads (lanes =
@@ -58,21 +59,54 @@ __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a,
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 
 struct WarpLapResult {
-  double u;      // row dual of row `lane`
-  double v;      // column dual of column `lane`
-  int r2c;       // column matched to row `lane`
-  int c2r;       // row matched to column `lane`
-  double value;  // LAP optimum (all lanes)
+  double u;      // row dual of row `gl` (group lane)
+  double v;      // column dual of column `gl`
+  int r2c;       // column matched to row `gl`
+  int c2r;       // row matched to column `gl`
+  double value;  // LAP optimum (all lanes of the group)
   int naug;      // augmenting searches
   int nrelax;    // label relaxations (instrumentation for the roofline)
 };
 
-// Solve the m x m LAP in shared memory `cs` (row stride ld) with one warp.
-// `scr` is 32 ints of per-warp scratch.  u0 is this lane's starting row dual
-// (used only when warm).  Must be called by all 32 lanes.
-__device__ __forceinline__ WarpLapResult warp_lap(const double* __restrict__ cs, int ld, int m, int lane, bool warm,
-                                                  double u0, int dual_mode, int* scr) {
-  const bool cv = lane < m;
+// Lowest group lane holding the least key among the G lanes of this lane's
+// group (aligned groups of G lanes).  Every lane of the warp must call it.
+template <int G>
+__device__ __forceinline__ int group_argmin(unsigned long long key, int gb) {
+  if constexpr (G == 32) {
+    return warp_argmin(key);
+  } else {
+    unsigned long long k = key;
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(kFull, k, off);
+      k = o < k ? o : k;
+    }
+    const unsigned ball = __ballot_sync(kFull, key == k);
+    return __ffs((ball >> gb) & ((1u << G) - 1u)) - 1;
+  }
+}
+
+template <int G>
+__device__ __forceinline__ unsigned group_bits(unsigned ball, int gb) {
+  if constexpr (G == 32) return ball;
+  else return (ball >> gb) & ((1u << G) - 1u);
+}
+
+// Solve one LAP per group of G lanes (32/G LAPs per warp) in lockstep: every
+// intrinsic is executed by all 32 lanes with the full mask and all loops are
+// warp-uniform (they run while any group still has work; idle groups only
+// predicate their updates), so the LAPs of one warp share every instruction.
+// Group lane gl = lane % G holds row gl and column gl of its LAP.  `cs` is the
+// group's m x m tile (row stride ld) in shared memory, `scr` G ints of group
+// scratch, m the group's LAP size (0 = no LAP, 1 <= m <= G otherwise).  The
+// arithmetic is identical for every G.
+template <int G>
+__device__ __forceinline__ WarpLapResult group_lap(const double* __restrict__ cs, int ld, int m, int lane, bool warm,
+                                                   double u0, int dual_mode, int* scr) {
+  const int gl = lane & (G - 1);
+  const int gb = lane - gl;
+  const bool cv = gl < m;
+  const int M = (G == 32) ? m : (int)__reduce_max_sync(kFull, (unsigned)m);
   WarpLapResult R;
   double u = (cv && warm) ? u0 : 0.0;
   double v = 0.0;
@@ -81,10 +115,10 @@ __device__ __forceinline__ WarpLapResult warp_lap(const double* __restrict__ cs,
   // column reduction with the argmin row
   unsigned long long bestk = ~0ull;
   int arg = -1;
-  for (int r = 0; r < m; ++r) {
-    const double ur = __shfl_sync(kFull, u, r);
-    if (cv) {
-      const double c = cs[r * ld + lane];
+  for (int r = 0; r < M; ++r) {
+    const double ur = __shfl_sync(kFull, u, gb + r);
+    if (cv && r < m) {
+      const double c = cs[r * ld + gl];
       const double x = warm ? dsub(c, ur) : c;  // c - 0 == c exactly
       const unsigned long long k = okey(x);
       if (arg < 0 || k < bestk) {
@@ -95,44 +129,50 @@ __device__ __forceinline__ WarpLapResult warp_lap(const double* __restrict__ cs,
     }
   }
   // greedy: the lowest column among those sharing an argmin row takes it
-  const int marg = cv ? arg : (64 + lane);
+  const int marg = cv ? ((lane / G) << 6) + arg : (1 << 20) + lane;
   const unsigned same = __match_any_sync(kFull, marg);
   const bool win = cv && (__ffs(same) - 1) == lane;
   int c2r = win ? arg : -1;
-  scr[lane] = -1;
+  scr[gl] = -1;
   __syncwarp();
-  if (win) scr[arg] = lane;
+  if (win) scr[arg] = gl;
   __syncwarp();
-  int r2c = cv ? scr[lane] : -1;
+  int r2c = cv ? scr[gl] : -1;
   __syncwarp();
 
-  unsigned freerows = __ballot_sync(kFull, cv && r2c < 0);
-  while (freerows) {
-    const int i = __ffs(freerows) - 1;
-    freerows &= freerows - 1;
-    ++naug;
-    const double ui = __shfl_sync(kFull, u, i);
-    double d = cv ? dsub(dsub(cs[i * ld + lane], ui), v) : 0.0;
+  unsigned freerows = group_bits<G>(__ballot_sync(kFull, cv && r2c < 0), gb);
+  while (__any_sync(kFull, freerows != 0)) {
+    const bool act = freerows != 0;  // this group runs a search in this round
+    const int i = act ? __ffs(freerows) - 1 : 0;
+    if (act) {
+      freerows &= freerows - 1;
+      ++naug;
+      nrelax += m;
+    }
+    const double ui = __shfl_sync(kFull, u, gb + i);
+    double d = (act && cv) ? dsub(dsub(cs[i * ld + gl], ui), v) : 0.0;
     unsigned long long dk = okey(d);
     int pred = i;
-    bool scanned = !cv;
-    nrelax += m;
-    const unsigned freecols = __ballot_sync(kFull, cv && c2r < 0);
-    int sink;
-    double dlast;
-    for (;;) {
-      const int c = warp_argmin(scanned ? ~0ull : dk);
-      const double dm = __shfl_sync(kFull, d, c);
-      if (lane == c) scanned = true;
-      if ((freecols >> c) & 1u) {
+    bool scanned = !(act && cv);
+    const unsigned freecols = group_bits<G>(__ballot_sync(kFull, cv && c2r < 0), gb);
+    bool searching = act;
+    int sink = 0;
+    double dlast = 0.0;
+    while (__any_sync(kFull, searching)) {
+      const int c = group_argmin<G>(scanned ? ~0ull : dk, gb);
+      const double dm = __shfl_sync(kFull, d, gb + c);
+      if (searching && gl == c) scanned = true;
+      const bool found = searching && ((freecols >> c) & 1u);
+      if (found) {
         sink = c;
         dlast = dm;
-        break;
       }
-      const int r = __shfl_sync(kFull, c2r, c);
-      const double ur = __shfl_sync(kFull, u, r);
-      if (!scanned) {
-        const double nd = dadd(dm, dsub(dsub(cs[r * ld + lane], ur), v));
+      const bool relaxing = searching && !found;
+      const int r0 = __shfl_sync(kFull, c2r, gb + c);
+      const int r = r0 < 0 ? 0 : r0;
+      const double ur = __shfl_sync(kFull, u, gb + r);
+      if (relaxing && !scanned) {
+        const double nd = dadd(dm, dsub(dsub(cs[r * ld + gl], ur), v));
         const unsigned long long nk = okey(nd);
         if (nk < dk) {
           d = nd;
@@ -140,48 +180,54 @@ __device__ __forceinline__ WarpLapResult warp_lap(const double* __restrict__ cs,
           pred = r;
         }
       }
-      nrelax += __popc(__ballot_sync(kFull, !scanned));
+      const int unsc = __popc(group_bits<G>(__ballot_sync(kFull, !scanned), gb));
+      if (relaxing) nrelax += unsc;
+      searching = relaxing;
     }
-    if (cv && scanned) v = dadd(v, dsub(d, dlast));
-    // augment back to row i
+    if (act && cv && scanned) v = dadd(v, dsub(d, dlast));
+    // augment back to row i (groups walk their own chains in lockstep)
+    bool walking = act;
     int col = sink;
-    for (;;) {
-      const int r = __shfl_sync(kFull, pred, col);
-      const int nxt = __shfl_sync(kFull, r2c, r);
-      if (lane == col) c2r = r;
-      if (lane == r) r2c = col;
-      if (r == i) break;
-      col = nxt;
+    while (__any_sync(kFull, walking)) {
+      const int r = __shfl_sync(kFull, pred, gb + col);
+      const int nxt = __shfl_sync(kFull, r2c, gb + r);
+      if (walking) {
+        if (gl == col) c2r = r;
+        if (gl == r) r2c = col;
+        if (r == i) walking = false;
+        else col = nxt;
+      }
     }
     const int mc = (cv && r2c >= 0) ? r2c : 0;
-    const double vm = __shfl_sync(kFull, v, mc);
-    if (cv && r2c >= 0) u = dsub(cs[lane * ld + r2c], vm);
+    const double vm = __shfl_sync(kFull, v, gb + mc);
+    if (act && cv && r2c >= 0) u = dsub(cs[gl * ld + r2c], vm);
   }
 
   // optimum, summed in increasing row order
-  const double xr = cv ? cs[lane * ld + r2c] : 0.0;
+  const double xr = cv ? cs[gl * ld + r2c] : 0.0;
   double val = 0.0;
-  for (int r = 0; r < m; ++r) {
-    const double t = __shfl_sync(kFull, xr, r);
-    if (lane == 0) val = dadd(val, t);
+  for (int r = 0; r < M; ++r) {
+    const double t = __shfl_sync(kFull, xr, gb + r);
+    if (gl == 0 && r < m) val = dadd(val, t);
   }
-  val = __shfl_sync(kFull, val, 0);
+  val = __shfl_sync(kFull, val, gb);
 
-  if (dual_mode == 1 && m > 1) {
+  if (dual_mode == 1) {
     // shortest paths from row 0 on reduced weights pi(r, sigma(r')) >= 0
-    const int s0 = __shfl_sync(kFull, r2c, 0);
-    const double vs0 = __shfl_sync(kFull, v, s0);
-    double dist = (cv && lane != 0) ? dsub(dsub(cs[lane * ld + s0], u), vs0) : 0.0;
+    const int s0 = __shfl_sync(kFull, r2c, gb);
+    const double vs0 = __shfl_sync(kFull, v, gb + (s0 < 0 ? 0 : s0));
+    double dist = (cv && gl != 0) ? dsub(dsub(cs[gl * ld + s0], u), vs0) : 0.0;
     unsigned long long dk = okey(dist);
-    bool done = !cv || lane == 0;
-    for (int it = 0; it < m - 2; ++it) {
-      const int rs = warp_argmin(done ? ~0ull : dk);
-      const double dr = __shfl_sync(kFull, dist, rs);
-      if (lane == rs) done = true;
-      const int s = __shfl_sync(kFull, r2c, rs);
-      const double vs = __shfl_sync(kFull, v, s);
-      if (!done) {
-        const double nd = dadd(dr, dsub(dsub(cs[lane * ld + s], u), vs));
+    bool done = !cv || gl == 0;
+    for (int it = 0; it < M - 2; ++it) {
+      const bool stepping = it < m - 2;
+      const int rs = group_argmin<G>(done ? ~0ull : dk, gb);
+      const double dr = __shfl_sync(kFull, dist, gb + rs);
+      if (stepping && gl == rs) done = true;
+      const int s = __shfl_sync(kFull, r2c, gb + rs);
+      const double vs = __shfl_sync(kFull, v, gb + (s < 0 ? 0 : s));
+      if (stepping && !done) {
+        const double nd = dadd(dr, dsub(dsub(cs[gl * ld + s], u), vs));
         const unsigned long long nk = okey(nd);
         if (nk < dk) {
           dist = nd;
@@ -189,16 +235,13 @@ __device__ __forceinline__ WarpLapResult warp_lap(const double* __restrict__ cs,
         }
       }
     }
-    const double u0r = __shfl_sync(kFull, u, 0);
-    const double ucan = cv ? dadd(dist, dsub(u, u0r)) : 0.0;
+    const double u0r = __shfl_sync(kFull, u, gb);
+    const double ucan = cv ? (m > 1 ? dadd(dist, dsub(u, u0r)) : 0.0) : 0.0;
     const int rr = cv ? c2r : 0;
-    const double ucr = __shfl_sync(kFull, ucan, rr);
-    const double vcan = cv ? dsub(cs[rr * ld + lane], ucr) : 0.0;
+    const double ucr = __shfl_sync(kFull, ucan, gb + rr);
+    const double vcan = cv ? (m > 1 ? dsub(cs[rr * ld + gl], ucr) : cs[0]) : 0.0;
     u = ucan;
     v = vcan;
-  } else if (dual_mode == 1 && m == 1) {
-    v = cv ? cs[0] : 0.0;
-    u = 0.0;
   }
   R.u = u;
   R.v = v;
