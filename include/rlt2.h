@@ -179,6 +179,34 @@ rlt2_status rlt2_destroy(rlt2_ctx* ctx);
 rlt2_status rlt2_lap_batched(int batch, int m, const double* cost, const double* u0, double* value, double* u,
                              double* v, int* row_to_col, int* n_aug, int dual_mode, void* stream);
 
+/* Bound a batch of branch-and-bound nodes (Section 4: a node fixes some
+ * facilities; its bound is the constant of the fixed part plus the RLT2 dual
+ * ascent bound of the residual QAP, see rlt2_create).  Nodes are admitted into
+ * waves whose arenas fit `mem_budget`; within a wave every stage of an
+ * iteration runs as one launch over all nodes (a persistent LAP kernel pulling
+ * work from a device queue), and the iteration is replayed as one CUDA graph.
+ *  n, F, D, B : as for rlt2_create (host)
+ *  n_nodes    : number of nodes, >= 1
+ *  partials   : host, n_nodes*n ints, row k = partial assignment of node k
+ *               (-1 = free); every node's residual size must be in [3, 32]
+ *  p          : parameters (NULL = defaults), shared by all nodes
+ *  iters      : iterations per node, 1..65536 (a node stops early on its own
+ *               feasibility / gap / stall rule)
+ *  mem_budget : device bytes the node arenas may use (0 = 80 % of free memory)
+ *  lb_out     : host, n_nodes doubles: best bound of each node
+ *  lb_hist    : host, n_nodes*iters doubles (nullable): bound per iteration,
+ *               NaN after a node stopped
+ *  iters_out  : host, n_nodes ints (nullable): iterations each node ran
+ *  stats_out  : host, 5 long longs (nullable): {waves, Z augmentations,
+ *               Z relaxations, lanes per Z-LAP, warps per block} where the
+ *               last two are the autotuned Z-stage launch shape
+ *  stream     : cudaStream_t; the call synchronises it before returning
+ * Errors: EINVAL (bad input), EADMIT (a node alone exceeds mem_budget),
+ * ENOMEM, ECUDA.  Device memory is allocated for the call and freed on return. */
+rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D, const double* B, int n_nodes,
+                             const int* partials, const rlt2_params* p, int iters, size_t mem_budget, double* lb_out,
+                             double* lb_hist, int* iters_out, long long* stats_out, void* stream);
+
 /* Dual ascent of a small QAP that allocates no device memory.  The paper has no
  * counterpart; this entry point exists for callers that cannot call cudaMalloc:
  * code running under a framework that owns the whole device memory pool (an

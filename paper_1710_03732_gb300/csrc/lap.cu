@@ -151,6 +151,149 @@ cudaError_t launch_lap(const LapArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Batched branch-and-bound nodes: one persistent launch per stage over the LAPs
+// of every node of a wave.  Warps pull 32/G LAPs at a time from a device queue
+// (atomic head, no waiting), so nodes of uneven size share the GPU.
+template <int G>
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap_nodes(NodeLapArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int per = 32 / G;
+  long long* s_prefix = reinterpret_cast<long long*>(smem_raw);
+  for (int i = threadIdx.x; i <= a.nnodes; i += blockDim.x) s_prefix[i] = a.prefix[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int grp = lane / G, gl = lane & (G - 1);
+  const size_t pre = (((size_t)(a.nnodes + 1) * sizeof(long long)) + 255) & ~size_t(255);
+  const int MM = a.max_m;
+  unsigned char* base = smem_raw + pre + (size_t)wib * warp_smem_bytes(MM, G);
+  double* tile = reinterpret_cast<double*>(base) + (size_t)grp * MM * tile_ld(MM);
+  double* uv = reinterpret_cast<double*>(base) + (size_t)per * MM * tile_ld(MM);
+  int* scr = reinterpret_cast<int*>(uv + 64) + grp * G;
+  unsigned long long aug_acc = 0, relax_acc = 0;
+  for (;;) {
+    unsigned long long b0 = 0;
+    if (lane == 0) b0 = atomicAdd(a.head, (unsigned long long)per);
+    b0 = __shfl_sync(kFull, b0, 0);
+    if (b0 >= (unsigned long long)a.total) break;
+    const long long t = (long long)b0 + grp;
+    bool have = t < a.total;
+    int k = 0;
+    long long li = 0;
+    NodeLapItem it{};
+    if (have) {
+      int lo = 0, hi = a.nnodes - 1;
+      while (lo < hi) {  // largest k with prefix[k] <= t
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_prefix[mid] <= t) lo = mid;
+        else hi = mid - 1;
+      }
+      k = lo;
+      li = t - s_prefix[k];
+      it = a.items[k];
+      if (*it.skip) have = false;
+    }
+    const int m = have ? it.m : 0;
+    const int ld = tile_ld(m);
+    const int mm = m * m;
+    if (have) {
+      const double* src = it.A + li * mm;
+      const double* add = it.Badd ? it.Badd + li * mm : nullptr;
+      for (int e = gl; e < mm; e += G) {
+        const int r = e / m, c = e - r * m;
+        double x = __ldcs(src + e);
+        if (add) x = __dadd_rn(x, __ldcs(add + e));
+        tile[r * ld + c] = x;
+      }
+    }
+    const bool warm = have && it.u0 != nullptr && *it.warm_gate != 0;
+    const double u0 = (warm && gl < m) ? it.u0[li * m + gl] : 0.0;
+    __syncwarp();
+    const WarpLapResult R = group_lap<G>(tile, ld, m, lane, warm, u0, a.dual_mode, scr);
+    if (have && gl < m) {
+      if (it.u) it.u[li * m + gl] = R.u;
+      if (it.v) it.v[li * m + gl] = R.v;
+      if (it.r2c) it.r2c[li * m + gl] = R.r2c;
+    }
+    if (have && gl == 0) {
+      it.value[li] = R.value;
+      aug_acc += R.naug;
+      relax_acc += R.nrelax;
+    }
+    uv[lane] = R.u;
+    uv[32 + lane] = R.v;
+    __syncwarp();
+    if (have && it.pi) {
+      double* dst = it.pi + li * mm;
+      const double* ug = uv + grp * G;
+      const double* vg = uv + 32 + grp * G;
+      for (int e = gl; e < mm; e += G) {
+        const int r = e / m, c = e - r * m;
+        dst[e] = __dsub_rn(__dsub_rn(tile[r * ld + c], ug[r]), vg[c]);
+      }
+    }
+    __syncwarp();
+  }
+  if (a.stats && gl == 0 && (aug_acc | relax_acc)) {
+    atomicAdd(a.stats + 0, aug_acc);
+    atomicAdd(a.stats + 1, relax_acc);
+  }
+}
+
+static int g_occ_nodes[33][3][2];
+
+cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s) {
+  if (a.total <= 0) return cudaSuccess;
+  if (a.max_m < 1 || a.max_m > 32 || a.nnodes < 1 || a.nnodes > kMaxWaveNodes) return cudaErrorInvalidValue;
+  const int G = a.group ? a.group : default_group(a.max_m);
+  const int wpb = a.warps_per_block ? a.warps_per_block : kMaxWarpsPerBlock;
+  if (G < a.max_m || (wpb != 4 && wpb != 8)) return cudaErrorInvalidValue;
+  const size_t pre = (((size_t)(a.nnodes + 1) * sizeof(long long)) + 255) & ~size_t(255);
+  const size_t smem = pre + warp_smem_bytes(a.max_m, G) * wpb;
+  cudaError_t e;
+  if (!g_sms) {
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  }
+  static bool attr_set[3] = {false, false, false};
+  const size_t cap_smem = (((size_t)(kMaxWaveNodes + 1) * sizeof(long long)) + 255) / 256 * 256 +
+                          warp_smem_bytes(32, 32) * kMaxWarpsPerBlock;
+  int& occ = g_occ_nodes[a.max_m][gidx(G)][wpb == 4 ? 0 : 1];
+  if (G == 8) {
+    if (!attr_set[0] && (e = cudaFuncSetAttribute(k_lap_nodes<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)cap_smem)) != cudaSuccess)
+      return e;
+    attr_set[0] = true;
+    if (!occ && (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lap_nodes<8>, wpb * 32, smem)) != cudaSuccess)
+      return e;
+  } else if (G == 16) {
+    if (!attr_set[1] && (e = cudaFuncSetAttribute(k_lap_nodes<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)cap_smem)) != cudaSuccess)
+      return e;
+    attr_set[1] = true;
+    if (!occ && (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lap_nodes<16>, wpb * 32, smem)) != cudaSuccess)
+      return e;
+  } else {
+    if (!attr_set[2] && (e = cudaFuncSetAttribute(k_lap_nodes<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)cap_smem)) != cudaSuccess)
+      return e;
+    attr_set[2] = true;
+    if (!occ && (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lap_nodes<32>, wpb * 32, smem)) != cudaSuccess)
+      return e;
+  }
+  if (occ < 1) occ = 1;
+  const long long per_block = (long long)wpb * (32 / G);
+  const long long need = (a.total + per_block - 1) / per_block;
+  const long long cap = (long long)g_sms * occ;
+  const int grid = (int)(need < cap ? need : cap);
+  if (G == 8) k_lap_nodes<8><<<grid, wpb * 32, smem, s>>>(a);
+  else if (G == 16) k_lap_nodes<16><<<grid, wpb * 32, smem, s>>>(a);
+  else k_lap_nodes<32><<<grid, wpb * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace rlt2
 
 using namespace rlt2;

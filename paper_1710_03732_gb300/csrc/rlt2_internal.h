@@ -29,6 +29,39 @@ struct LapArgs {
   int warps_per_block;       // 4 or 8; 0 = 8
 };
 
+// The LAPs of one stage of one branch-and-bound node.
+struct NodeLapItem {
+  long long count;     // LAPs of this node in this stage
+  int m;               // their size
+  const double* A;     // cost tiles (+ Badd if set)
+  const double* Badd;
+  const double* u0;    // warm-start row duals or nullptr
+  const int* warm_gate;
+  const int* skip;     // the node's done flag
+  double* value;
+  double* u;
+  double* v;
+  int* r2c;
+  double* pi;
+};
+
+constexpr int kMaxWaveNodes = 1024;
+
+// One stage of all nodes of a wave as one persistent launch: warps take LAPs
+// from a device queue (head must be zero at launch), nodes looked up by prefix.
+struct NodeLapArgs {
+  int nnodes;
+  const NodeLapItem* items;  // device [nnodes]
+  const long long* prefix;   // device [nnodes + 1]
+  long long total;
+  int max_m;
+  int dual_mode;
+  unsigned long long* head;
+  unsigned long long* stats;  // device [2]: augmentations, relaxations (nullable)
+  int group, warps_per_block;
+};
+cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s);
+
 // Lanes per LAP the launcher would pick for size m (8, 16 or 32).
 int default_group(int m);
 

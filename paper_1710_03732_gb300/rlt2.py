@@ -40,7 +40,8 @@ _vp = ctypes.c_void_p
 
 EXPORTS = ["rlt2_params_default", "rlt2_create", "rlt2_iterate", "rlt2_iterate_async", "rlt2_bound", "rlt2_duals",
            "rlt2_reduced_costs", "rlt2_export_state", "rlt2_import_state", "rlt2_stats", "rlt2_sizes",
-           "rlt2_set_timing", "rlt2_kernel_times", "rlt2_destroy", "rlt2_lap_batched", "rlt2_iterate_noalloc",
+           "rlt2_set_timing", "rlt2_kernel_times", "rlt2_destroy", "rlt2_lap_batched", "rlt2_bound_nodes",
+           "rlt2_iterate_noalloc",
            "rlt2_strerror", "rlt2_last_error"]
 
 
@@ -69,6 +70,8 @@ def lib():
     L.rlt2_kernel_times.argtypes = [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     L.rlt2_destroy.argtypes = [_vp]
     L.rlt2_lap_batched.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
+    L.rlt2_bound_nodes.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, _ip, ctypes.POINTER(rlt2_params),
+                                   ctypes.c_int, ctypes.c_size_t, _dp, _dp, _ip, ctypes.POINTER(ctypes.c_longlong), _vp]
     L.rlt2_iterate_noalloc.argtypes = [ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(rlt2_params), ctypes.c_int, _vp,
                                        _vp]
     L.rlt2_strerror.argtypes = [ctypes.c_int]
@@ -213,6 +216,26 @@ def rlt2_lap_batched(cost, value, u0=None, u=None, v=None, row_to_col=None, n_au
     batch, m = int(cost.shape[0]), int(cost.shape[1])
     _check(lib().rlt2_lap_batched(batch, m, _ptr(cost), _ptr(u0), _ptr(value), _ptr(u), _ptr(v), _ptr(row_to_col),
                                   _ptr(n_aug), dual_mode, _stream(stream)), "rlt2_lap_batched")
+
+
+def rlt2_bound_nodes(F, D, partials, iters: int, B=None, prm: Optional[rlt2_params] = None, mem_budget: int = 0,
+                     stream=None):
+    """Bound every node (row of `partials`); returns (best bounds, bound history
+    [n_nodes, iters], iterations per node, stats {waves, z_aug, z_relax, group, wpb})."""
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    B = None if B is None else np.ascontiguousarray(B, dtype=np.float64)
+    part = np.ascontiguousarray(partials, dtype=np.int32)
+    nn, n = part.shape
+    lb = np.empty(nn)
+    hist = np.empty((nn, iters))
+    its = np.zeros(nn, dtype=np.int32)
+    st = (ctypes.c_longlong * 5)()
+    _check(lib().rlt2_bound_nodes(n, _host_d(F), _host_d(D), _host_d(B), nn, part.ctypes.data_as(_ip),
+                                  None if prm is None else ctypes.byref(prm), iters, mem_budget, _host_d(lb),
+                                  _host_d(hist), its.ctypes.data_as(_ip), st, _stream(stream)), "rlt2_bound_nodes")
+    stats = dict(zip(["waves", "z_aug", "z_relax", "group", "wpb"], list(st)))
+    return lb, hist, its, stats
 
 
 def rlt2_iterate_noalloc(F, D, lb_hist, B=None, prm: Optional[rlt2_params] = None, stream=None):

@@ -104,3 +104,25 @@ def test_lap_batched_rejects_bad_sizes(L):
 def test_strerror(L):
     assert L.rlt2_strerror(rlt2.RLT2_EINVAL) == b"invalid argument"
     assert L.rlt2_destroy(None) == rlt2.RLT2_OK
+
+
+def test_bound_nodes_rejects_bad_input(L):
+    n = 6
+    F = np.ones((n, n))
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lb = np.zeros(2)
+
+    def call(parts, iters=5):
+        parts = np.ascontiguousarray(parts, dtype=np.int32)
+        return L.rlt2_bound_nodes(n, F.ctypes.data_as(dp), F.ctypes.data_as(dp), None, parts.shape[0],
+                                  parts.ctypes.data_as(ip), None, iters, 0, lb.ctypes.data_as(dp), None, None, None,
+                                  None)
+    ok = -np.ones((2, n))
+    assert call(ok, iters=0) == rlt2.RLT2_EINVAL
+    bad = ok.copy()
+    bad[1, :2] = [3, 3]                          # not injective
+    assert call(bad) == rlt2.RLT2_EINVAL
+    bad = ok.copy()
+    bad[0, :4] = [0, 1, 2, 3]                    # residual size 2
+    assert call(bad) == rlt2.RLT2_EINVAL
