@@ -74,6 +74,17 @@ def lib():
         L.or_iterate.argtypes = ([ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
                                   _dp, _dp, _dp, _dp, _ip, _dp, _dp, _lp, ctypes.c_int])
         L.or_have_openmp.restype = ctypes.c_int
+        _fp = ctypes.POINTER(ctypes.c_float)
+        L.or_f32_trunc.argtypes = [ctypes.c_double]
+        L.or_f32_trunc.restype = ctypes.c_float
+        L.or_bf16_round.argtypes = [ctypes.c_float]
+        L.or_bf16_round.restype = ctypes.c_float
+        L.or_mlp_features.argtypes = [ctypes.c_int, _dp, _dp, _dp, _fp, _fp, _fp]
+        L.or_mlp_forward.argtypes = [ctypes.c_int, ctypes.c_int, _fp, _fp, _fp, _fp, _fp, _fp, ctypes.c_double,
+                                     ctypes.c_int, _dp, _dp, _dp]
+        L.or_mlp_backward.argtypes = [ctypes.c_int, ctypes.c_int, _fp, _fp, _fp, ctypes.c_int, _dp, _dp, _dp, _dp,
+                                      _dp, _dp, _dp, _dp, _dp, _dp]
+        L.or_mlp_backward.restype = ctypes.c_double
     return _lib
 
 
@@ -293,3 +304,59 @@ def z_index(n, i, j, k, p, q, r):
     kk = k - (k > i) - (k > j)
     rr = r - (r > p) - (r > q)
     return tile_index(n, i, p, j, q) * m * m + kk * m + rr
+
+
+# --------------------------------------------------------------------------
+# learned warm start: features and FP64 reference MLP
+# --------------------------------------------------------------------------
+MLP_IN = 34
+
+
+def _f(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def f32_trunc(x: float) -> float:
+    return float(lib().or_f32_trunc(float(x)))
+
+
+def bf16_round(x: float) -> float:
+    return float(lib().or_bf16_round(float(x)))
+
+
+def mlp_features(tile, prev_u=None, target_u=None):
+    """Row features (m x 34, float32), scaled targets (m, float32) and the tile scale."""
+    c = _f64(tile)
+    m = c.shape[0]
+    feat = np.zeros((m, MLP_IN), dtype=np.float32)
+    tgt = np.zeros(m, dtype=np.float32)
+    sc = ctypes.c_float()
+    pu = None if prev_u is None else _f64(prev_u)
+    tu = None if target_u is None else _f64(target_u)
+    lib().or_mlp_features(m, _d(c), _d(pu), _d(tu), _f(feat), _f(tgt), ctypes.byref(sc))
+    return feat, tgt, sc.value
+
+
+def mlp_forward(X, W1, b1, W2, b2, w3, b3, bf16_acts=True):
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    N, H = X.shape[0], W1.shape[1]
+    out = np.zeros(N)
+    h1 = np.zeros((N, H))
+    h2 = np.zeros((N, H))
+    args = [np.ascontiguousarray(a, dtype=np.float32) for a in (W1, b1, W2, b2, w3)]
+    lib().or_mlp_forward(N, H, _f(X), *(_f(a) for a in args), float(b3), int(bf16_acts), _d(out), _d(h1), _d(h2))
+    return out, h1, h2
+
+
+def mlp_grads(X, W1, b1, W2, b2, w3, b3, t, bf16_acts=True):
+    """Loss and FP64 gradients (gW1, gb1, gW2, gb2, gw3, gb3)."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    N, H = X.shape[0], W1.shape[1]
+    out, h1, h2 = mlp_forward(X, W1, b1, W2, b2, w3, b3, bf16_acts)
+    g = [np.zeros((MLP_IN, H)), np.zeros(H), np.zeros((H, H)), np.zeros(H), np.zeros(H)]
+    gb3 = ctypes.c_double()
+    W2c = np.ascontiguousarray(W2, dtype=np.float32)
+    w3c = np.ascontiguousarray(w3, dtype=np.float32)
+    loss = lib().or_mlp_backward(N, H, _f(X), _f(W2c), _f(w3c), int(bf16_acts), _d(out), _d(h1), _d(h2),
+                                 _d(_f64(t)), *(_d(a) for a in g), ctypes.byref(gb3))
+    return loss, g[0], g[1], g[2], g[3], g[4], gb3.value

@@ -600,3 +600,165 @@ int or_have_openmp(void) {
   return 0;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned warm start (not in the paper): features, FP64 reference MLP.     */
+/* ------------------------------------------------------------------------ */
+/* FP64 -> FP32 by truncating the significand (exponent clamped to the FP32
+ * range; below it -> signed zero, above it -> +-FLT_MAX).  Done on bits so the
+ * GPU can reproduce it with integer instructions. */
+float or_f32_trunc(double x) {
+  uint64_t b;
+  memcpy(&b, &x, 8);
+  uint32_t sign = (uint32_t)(b >> 63) << 31;
+  int e = (int)((b >> 52) & 0x7ff);
+  uint32_t out;
+  if (e == 0) {
+    out = sign;
+  } else {
+    int ef = e - 1023 + 127;
+    if (ef <= 0) out = sign;
+    else if (ef >= 255) out = sign | 0x7f7fffffu;
+    else out = sign | ((uint32_t)ef << 23) | (uint32_t)((b >> 29) & 0x7fffff);
+  }
+  float f;
+  memcpy(&f, &out, 4);
+  return f;
+}
+
+/* FP32 -> BF16 (round to nearest even), returned as the FP32 value it represents. */
+float or_bf16_round(float x) {
+  uint32_t b;
+  memcpy(&b, &x, 4);
+  uint32_t lsb = (b >> 16) & 1u;
+  b = (b + 0x7fffu + lsb) & 0xffff0000u;
+  float f;
+  memcpy(&f, &b, 4);
+  return f;
+}
+
+#define OR_MLP_IN 34
+/* Row features of one m x m tile (m <= 32), all in FP32:
+ *  cf = trunc32(c); colmin_j = min_i cf_ij; R = cf - colmin;
+ *  s = max R (1 if 0); inv = 1/s; row i: sort(R_i * inv) ascending, padded with
+ *  zeros to 32; feature 32 = trunc32(prev_u_i) * inv (0 without prev);
+ *  feature 33 = m/32.  Target (optional): trunc32(u*_i) * inv. */
+void or_mlp_features(int m, const double* tile, const double* prev_u, const double* target_u, float* feat,
+                     float* target_out, float* scale_out) {
+  float cf[32 * 32], cmin[32], s = 0.0f;
+  for (int i = 0; i < m; i++)
+    for (int j = 0; j < m; j++) cf[i * 32 + j] = or_f32_trunc(tile[i * m + j]);
+  for (int j = 0; j < m; j++) {
+    float mn = cf[j];
+    for (int i = 1; i < m; i++)
+      if (cf[i * 32 + j] < mn) mn = cf[i * 32 + j];
+    cmin[j] = mn;
+  }
+  for (int i = 0; i < m; i++)
+    for (int j = 0; j < m; j++) {
+      float r = cf[i * 32 + j] - cmin[j];
+      if (r > s) s = r;
+    }
+  if (!(s > 0.0f)) s = 1.0f;
+  float inv = 1.0f / s;
+  for (int i = 0; i < m; i++) {
+    float row[32];
+    for (int j = 0; j < m; j++) row[j] = (cf[i * 32 + j] - cmin[j]) * inv;
+    for (int a = 1; a < m; a++) { /* insertion sort */
+      float x = row[a];
+      int b = a - 1;
+      while (b >= 0 && row[b] > x) {
+        row[b + 1] = row[b];
+        b--;
+      }
+      row[b + 1] = x;
+    }
+    for (int k = 0; k < 32; k++) feat[i * OR_MLP_IN + k] = k < m ? row[k] : 0.0f;
+    feat[i * OR_MLP_IN + 32] = prev_u ? or_f32_trunc(prev_u[i]) * inv : 0.0f;
+    feat[i * OR_MLP_IN + 33] = (float)m / 32.0f;
+    if (target_u && target_out) target_out[i] = or_f32_trunc(target_u[i]) * inv;
+  }
+  if (scale_out) *scale_out = s;
+}
+
+/* FP64 forward pass of the 3-layer MLP on N rows of 34 features:
+ *  h1 = relu(X W1 + b1), h2 = relu(h1 W2 + b2), out = h2 . w3 + b3,
+ *  W1: 34 x H, W2: H x H (row-major, input index first).  With bf16_acts the
+ *  inputs of every matrix product (X, h1, h2) are rounded to BF16, as the
+ *  tensor-core path stores them. */
+void or_mlp_forward(int N, int H, const float* X, const float* W1, const float* b1, const float* W2,
+                    const float* b2, const float* w3, double b3, int bf16_acts, double* out, double* h1,
+                    double* h2) {
+  for (int r = 0; r < N; r++) {
+    double* a1 = h1 + (size_t)r * H;
+    double* a2 = h2 + (size_t)r * H;
+    for (int j = 0; j < H; j++) {
+      double s = b1[j];
+      for (int k = 0; k < OR_MLP_IN; k++) {
+        double x = bf16_acts ? (double)or_bf16_round(X[r * OR_MLP_IN + k]) : (double)X[r * OR_MLP_IN + k];
+        s += x * (double)W1[k * H + j];
+      }
+      a1[j] = s > 0.0 ? s : 0.0;
+      if (bf16_acts) a1[j] = (double)or_bf16_round((float)a1[j]);
+    }
+    for (int j = 0; j < H; j++) {
+      double s = b2[j];
+      for (int k = 0; k < H; k++) s += a1[k] * (double)W2[(size_t)k * H + j];
+      a2[j] = s > 0.0 ? s : 0.0;
+      if (bf16_acts) a2[j] = (double)or_bf16_round((float)a2[j]);
+    }
+    double s = b3;
+    for (int k = 0; k < H; k++) s += a2[k] * (double)w3[k];
+    out[r] = s;
+  }
+}
+
+/* Gradients of L = 1/(2N) sum_r (out_r - t_r)^2 (after or_mlp_forward with the
+ * same arguments).  With bf16_acts the back-propagated activation gradients
+ * dh2 and dh1 are rounded to BF16 where the tensor-core path stores them. */
+double or_mlp_backward(int N, int H, const float* X, const float* W2, const float* w3, int bf16_acts,
+                       const double* out, const double* h1, const double* h2, const double* t, double* gW1,
+                       double* gb1, double* gW2, double* gb2, double* gw3, double* gb3) {
+  double loss = 0.0;
+  memset(gW1, 0, sizeof(double) * OR_MLP_IN * H);
+  memset(gb1, 0, sizeof(double) * H);
+  memset(gW2, 0, sizeof(double) * (size_t)H * H);
+  memset(gb2, 0, sizeof(double) * H);
+  memset(gw3, 0, sizeof(double) * H);
+  *gb3 = 0.0;
+  double* d2 = (double*)malloc(sizeof(double) * H);
+  double* d1 = (double*)malloc(sizeof(double) * H);
+  for (int r = 0; r < N; r++) {
+    double e = out[r] - t[r];
+    loss += 0.5 * e * e / N;
+    double dout = e / N;
+    const double* a1 = h1 + (size_t)r * H;
+    const double* a2 = h2 + (size_t)r * H;
+    *gb3 += dout;
+    for (int k = 0; k < H; k++) {
+      gw3[k] += a2[k] * dout;
+      d2[k] = a2[k] > 0.0 ? dout * (double)w3[k] : 0.0;
+      if (bf16_acts) d2[k] = (double)or_bf16_round((float)d2[k]);
+    }
+    for (int j = 0; j < H; j++) {
+      gb2[j] += d2[j];
+      for (int k = 0; k < H; k++) gW2[(size_t)k * H + j] += a1[k] * d2[j];
+    }
+    for (int k = 0; k < H; k++) {
+      double s = 0.0;
+      for (int j = 0; j < H; j++) s += (double)W2[(size_t)k * H + j] * d2[j];
+      d1[k] = a1[k] > 0.0 ? s : 0.0;
+      if (bf16_acts) d1[k] = (double)or_bf16_round((float)d1[k]);
+    }
+    for (int j = 0; j < H; j++) {
+      gb1[j] += d1[j];
+      for (int k = 0; k < OR_MLP_IN; k++) {
+        double x = bf16_acts ? (double)or_bf16_round(X[r * OR_MLP_IN + k]) : (double)X[r * OR_MLP_IN + k];
+        gW1[k * H + j] += x * d1[j];
+      }
+    }
+  }
+  free(d2);
+  free(d1);
+  return loss;
+}
