@@ -59,7 +59,9 @@ typedef enum {
  *               pointwise-largest optimal row duals with u_0 = 0; unique for a
  *               given cost matrix, so warm and cold solves agree)
  *  warm       : 0 = cold Z-LAPs, 1 = start each Z-LAP from its previous
- *               iteration's row duals (column-min repair keeps them feasible)
+ *               iteration's row duals, 2 = start from row duals predicted by
+ *               the network attached with rlt2_set_mlp (column-min repair
+ *               keeps any start feasible; the bound does not depend on it)
  *  min_gap    : stop once (UB - LB)/UB < min_gap (needs ub > 0 or a found UB)
  *  ub         : known upper bound on the node's QAP value (<= 0: unknown)
  *  feas_tol   : tolerance of the feasibility check after Algorithm 1
@@ -232,6 +234,46 @@ rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D, const doub
  * device) race and give undefined results: serialise them. */
 rlt2_status rlt2_iterate_noalloc(int n, const double* F, const double* D, const double* B, const rlt2_params* p,
                                  int iters, double* lb_hist, void* stream);
+
+/* ---- learned warm start (not in the paper) ------------------------------
+ * A per-row network predicts each Z-LAP row dual from the row's sorted,
+ * column-min-reduced, max-scaled costs (FP32), the row's previous dual and
+ * m/32 (34 features); 34 -> hidden -> hidden -> 1, ReLU, BF16 weights and
+ * activations, FP32 accumulation on the tensor cores.  Predictions only seed
+ * the exact Hungarian.  An rlt2_mlp is not thread-safe and must not be used by
+ * two contexts whose work overlaps on the GPU. */
+typedef struct rlt2_mlp rlt2_mlp;
+
+/* hidden: multiple of 64 in [64, 1024]; seed: deterministic initialisation. */
+rlt2_status rlt2_mlp_create(int hidden, unsigned long long seed, void* stream, rlt2_mlp** out);
+rlt2_status rlt2_mlp_destroy(rlt2_mlp* m);
+/* Host FP32 copies: W1 34*hidden (input index first), b1 hidden, W2
+ * hidden*hidden, b2 hidden, w3 hidden, b3 1.  set_weights rounds W1, W2 to
+ * BF16 for the tensor cores and resets the optimiser state. */
+rlt2_status rlt2_mlp_get_weights(rlt2_mlp* m, float* W1, float* b1, float* W2, float* b2, float* w3, float* b3);
+rlt2_status rlt2_mlp_set_weights(rlt2_mlp* m, const float* W1, const float* b1, const float* W2, const float* b2,
+                                 const float* w3, const float* b3);
+/* Append training rows: ntiles m x m tiles (device), their previous row duals
+ * (device, nullable) and their optimal (canonical) row duals (device). */
+rlt2_status rlt2_mlp_add_samples(rlt2_mlp* m, long long ntiles, int mz, const double* tiles, const double* prev_u,
+                                 const double* target_u);
+/* Number of rows; optional host copies of the BF16 feature rows (rows*64 of
+ * 2-byte values, 34 used) and FP32 targets (rows). */
+rlt2_status rlt2_mlp_samples(rlt2_mlp* m, long long* rows, void* X_bf16, float* targets);
+rlt2_status rlt2_mlp_clear_samples(rlt2_mlp* m);
+/* Loss 1/(2N) sum (out - target)^2 on the first `rows` samples (<= 262144) and
+ * its gradients (host, same shapes as the weights); no update. */
+rlt2_status rlt2_mlp_grad(rlt2_mlp* m, long long rows, double* loss, float* gW1, float* gb1, float* gW2,
+                          float* gb2, float* gw3, float* gb3);
+/* `steps` AdamW steps on minibatches of batch_rows (multiple of 64, <= 262144)
+ * drawn from the samples; loss_hist (host, steps, nullable). */
+rlt2_status rlt2_mlp_fit(rlt2_mlp* m, int steps, int batch_rows, double lr, double weight_decay,
+                         unsigned long long seed, double* loss_hist);
+/* Predicted row duals u0 (device, ntiles*mz) for device tiles / previous duals. */
+rlt2_status rlt2_mlp_predict(rlt2_mlp* m, long long ntiles, int mz, const double* tiles, const double* prev_u,
+                             double* u0);
+/* Attach a network to a context (used when its params have warm == 2). */
+rlt2_status rlt2_set_mlp(rlt2_ctx* ctx, rlt2_mlp* m);
 
 /* Human-readable name of a status, and the last error message of this thread. */
 const char* rlt2_strerror(rlt2_status s);

@@ -163,6 +163,8 @@ struct rlt2_ctx {
   long long kcount[kKinds] = {0, 0, 0, 0, 0, 0};
   int iter_host = 0;
   double cst_host = 0.0;
+  rlt2_mlp* mlp = nullptr;
+  double* u0buf = nullptr;
 };
 
 static void ctx_free(rlt2_ctx* c) {
@@ -175,11 +177,14 @@ static void ctx_free(rlt2_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->u0buf) cudaFree(c->u0buf);
   delete c;
 }
 
 static IterView view_of(const rlt2_ctx* c) {
   IterView v{};
+  v.mlp = c->mlp;
+  v.u0buf = c->u0buf;
   v.n = c->n;
   v.m = c->m;
   v.T = c->T;
@@ -245,7 +250,7 @@ bool rlt2::params_valid(const rlt2_params& p) {
   }
   if (std::fabs(s - 1.0) > 1e-12) return false;
   if (p.dual_mode != 0 && p.dual_mode != 1) return false;
-  if (p.warm != 0 && p.warm != 1) return false;
+  if (p.warm < 0 || p.warm > 2) return false;
   if (!std::isfinite(p.min_gap) || !std::isfinite(p.ub) || !std::isfinite(p.feas_tol)) return false;
   if (p.stall_window < 0 || p.stall_window >= kStallRing || !std::isfinite(p.stall_tol)) return false;
   return true;
@@ -512,8 +517,14 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   z.batch = T;
   z.m = m;
   z.A = v.Dhat;
-  z.u0 = p.warm ? v.xi : nullptr;
+  z.u0 = p.warm == 1 ? v.xi : nullptr;
   z.warm_gate = &v.sc->have_snap;
+  if (p.warm == 2 && v.mlp && v.u0buf) {
+    // learned start from the tile and the row's previous dual (zero before the first solve)
+    if ((e = mlp_predict_enqueue(v.mlp, T, m, v.Dhat, v.xi, v.u0buf, s)) != cudaSuccess) return e;
+    z.u0 = v.u0buf;
+    z.warm_gate = nullptr;
+  }
   z.value = v.Theta;
   z.u = v.xi;
   z.v = v.psi;
@@ -591,6 +602,10 @@ static rlt2_status build_graph(rlt2_ctx* c) {
 constexpr int kEvChunk = 64;  // iterations per batch of timing events
 
 static rlt2_status enqueue_many(rlt2_ctx* c, int iters) {
+  if (c->prm.warm == 2 && !c->mlp) {
+    set_error("warm == 2 needs a network: call rlt2_set_mlp first");
+    return RLT2_EINVAL;
+  }
   if (c->timing) {
     // the event pool was created by rlt2_set_timing; reuse it every kEvChunk iterations
     for (int base = 0; base < iters; base += kEvChunk) {
@@ -798,6 +813,18 @@ extern "C" rlt2_status rlt2_kernel_times(rlt2_ctx* c, double* ms, long long* cou
   for (int k = 0; k < nk && k < kKinds; ++k) {
     if (ms) ms[k] = c->kms[k];
     if (count) count[k] = c->kcount[k];
+  }
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_set_mlp(rlt2_ctx* c, rlt2_mlp* m) {
+  if (!c) return RLT2_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  if (m && !c->u0buf) CK(cudaMalloc((void**)&c->u0buf, sizeof(double) * (size_t)c->T * c->m));
+  c->mlp = m;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
   }
   return RLT2_OK;
 }

@@ -85,6 +85,8 @@ struct DevScalars {
 
 // Every device buffer one dual ascent works on (layouts as in rlt2.h).
 struct IterView {
+  rlt2_mlp* mlp;   // learned warm start (warm == 2)
+  double* u0buf;   // its predictions, T*m
   int n, m;
   long long T, E;
   int ntrip;
@@ -100,6 +102,10 @@ cudaError_t enqueue_setup(const IterView& v, int n_full, const double* dF, const
                           const int* dfac, const int* dloc, const int* dfixf, const int* dfixl, int nfix,
                           cudaStream_t s);
 cudaError_t enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent_t* ev);
+
+// Predicted Z-LAP row duals for ntiles tiles of size mz (mlp.cu).
+cudaError_t mlp_predict_enqueue(rlt2_mlp* m, long long ntiles, int mz, const double* tiles, const double* prev_u,
+                                double* u0, cudaStream_t s);
 
 // Parameter validation shared by the entry points.
 bool params_valid(const rlt2_params& p);

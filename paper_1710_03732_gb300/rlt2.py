@@ -41,7 +41,9 @@ _vp = ctypes.c_void_p
 EXPORTS = ["rlt2_params_default", "rlt2_create", "rlt2_iterate", "rlt2_iterate_async", "rlt2_bound", "rlt2_duals",
            "rlt2_reduced_costs", "rlt2_export_state", "rlt2_import_state", "rlt2_stats", "rlt2_sizes",
            "rlt2_set_timing", "rlt2_kernel_times", "rlt2_destroy", "rlt2_lap_batched", "rlt2_bound_nodes",
-           "rlt2_iterate_noalloc",
+           "rlt2_iterate_noalloc", "rlt2_mlp_create", "rlt2_mlp_destroy", "rlt2_mlp_get_weights",
+           "rlt2_mlp_set_weights", "rlt2_mlp_add_samples", "rlt2_mlp_samples", "rlt2_mlp_clear_samples",
+           "rlt2_mlp_grad", "rlt2_mlp_fit", "rlt2_mlp_predict", "rlt2_set_mlp",
            "rlt2_strerror", "rlt2_last_error"]
 
 
@@ -74,6 +76,19 @@ def lib():
                                    ctypes.c_int, ctypes.c_size_t, _dp, _dp, _ip, ctypes.POINTER(ctypes.c_longlong), _vp]
     L.rlt2_iterate_noalloc.argtypes = [ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(rlt2_params), ctypes.c_int, _vp,
                                        _vp]
+    _fp = ctypes.POINTER(ctypes.c_float)
+    L.rlt2_mlp_create.argtypes = [ctypes.c_int, ctypes.c_ulonglong, _vp, ctypes.POINTER(_vp)]
+    L.rlt2_mlp_destroy.argtypes = [_vp]
+    L.rlt2_mlp_get_weights.argtypes = [_vp, _fp, _fp, _fp, _fp, _fp, _fp]
+    L.rlt2_mlp_set_weights.argtypes = [_vp, _fp, _fp, _fp, _fp, _fp, _fp]
+    L.rlt2_mlp_add_samples.argtypes = [_vp, ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp]
+    L.rlt2_mlp_samples.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong), _vp, _fp]
+    L.rlt2_mlp_clear_samples.argtypes = [_vp]
+    L.rlt2_mlp_grad.argtypes = [_vp, ctypes.c_longlong, _dp, _fp, _fp, _fp, _fp, _fp, _fp]
+    L.rlt2_mlp_fit.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_ulonglong,
+                               _dp]
+    L.rlt2_mlp_predict.argtypes = [_vp, ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp]
+    L.rlt2_set_mlp.argtypes = [_vp, _vp]
     L.rlt2_strerror.argtypes = [ctypes.c_int]
     L.rlt2_strerror.restype = ctypes.c_char_p
     L.rlt2_last_error.restype = ctypes.c_char_p
@@ -246,6 +261,97 @@ def rlt2_iterate_noalloc(F, D, lb_hist, B=None, prm: Optional[rlt2_params] = Non
                                       int(lb_hist.shape[0]), _ptr(lb_hist), _stream(stream)), "rlt2_iterate_noalloc")
 
 
+def _fptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    assert a.dtype == np.float32 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class Mlp:
+    """Owns one rlt2_mlp (learned warm start network)."""
+
+    IN = 34
+
+    def __init__(self, hidden=256, seed=1, stream=None):
+        self.H = hidden
+        out = _vp()
+        _check(lib().rlt2_mlp_create(hidden, seed, _stream(stream), ctypes.byref(out)), "rlt2_mlp_create")
+        self.ptr = out.value
+
+    def get_weights(self):
+        H = self.H
+        W1, b1 = np.zeros((self.IN, H), np.float32), np.zeros(H, np.float32)
+        W2, b2 = np.zeros((H, H), np.float32), np.zeros(H, np.float32)
+        w3, b3 = np.zeros(H, np.float32), np.zeros(1, np.float32)
+        _check(lib().rlt2_mlp_get_weights(self.ptr, _fptr(W1), _fptr(b1), _fptr(W2), _fptr(b2), _fptr(w3), _fptr(b3)),
+               "rlt2_mlp_get_weights")
+        return W1, b1, W2, b2, w3, float(b3[0])
+
+    def set_weights(self, W1, b1, W2, b2, w3, b3):
+        arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (W1, b1, W2, b2, w3)]
+        b3a = np.array([b3], dtype=np.float32)
+        _check(lib().rlt2_mlp_set_weights(self.ptr, *(_fptr(a) for a in arrs), _fptr(b3a)), "rlt2_mlp_set_weights")
+
+    def add_samples(self, tiles, target_u, prev_u=None):
+        """tiles: CUDA float64 (ntiles, m, m); target_u / prev_u: CUDA float64 (ntiles, m)."""
+        nt, m = int(tiles.shape[0]), int(tiles.shape[1])
+        _check(lib().rlt2_mlp_add_samples(self.ptr, nt, m, _ptr(tiles), _ptr(prev_u), _ptr(target_u)),
+               "rlt2_mlp_add_samples")
+
+    def samples(self):
+        rows = ctypes.c_longlong()
+        _check(lib().rlt2_mlp_samples(self.ptr, ctypes.byref(rows), None, None), "rlt2_mlp_samples")
+        X = np.zeros((rows.value, 64), dtype=np.uint16)
+        T = np.zeros(rows.value, dtype=np.float32)
+        _check(lib().rlt2_mlp_samples(self.ptr, ctypes.byref(rows), X.ctypes.data, _fptr(T)), "rlt2_mlp_samples")
+        Xf = (X.astype(np.uint32) << 16).view(np.float32)
+        return Xf[:, :self.IN].copy(), T
+
+    def clear_samples(self):
+        _check(lib().rlt2_mlp_clear_samples(self.ptr), "rlt2_mlp_clear_samples")
+
+    def grad(self, rows):
+        H = self.H
+        g = [np.zeros((self.IN, H), np.float32), np.zeros(H, np.float32), np.zeros((H, H), np.float32),
+             np.zeros(H, np.float32), np.zeros(H, np.float32), np.zeros(1, np.float32)]
+        loss = ctypes.c_double()
+        _check(lib().rlt2_mlp_grad(self.ptr, rows, ctypes.byref(loss), *(_fptr(a) for a in g)), "rlt2_mlp_grad")
+        return loss.value, g[0], g[1], g[2], g[3], g[4], float(g[5][0])
+
+    def fit(self, steps, batch_rows=8192, lr=1e-3, weight_decay=1e-4, seed=0):
+        hist = np.zeros(steps)
+        _check(lib().rlt2_mlp_fit(self.ptr, steps, batch_rows, lr, weight_decay, seed, _host_d(hist)), "rlt2_mlp_fit")
+        return hist
+
+    def predict(self, tiles, u0, prev_u=None):
+        nt, m = int(tiles.shape[0]), int(tiles.shape[1])
+        _check(lib().rlt2_mlp_predict(self.ptr, nt, m, _ptr(tiles), _ptr(prev_u), _ptr(u0)), "rlt2_mlp_predict")
+
+    def save(self, path):
+        W1, b1, W2, b2, w3, b3 = self.get_weights()
+        np.savez(path, W1=W1, b1=b1, W2=W2, b2=b2, w3=w3, b3=np.float32(b3))
+
+    def load(self, path):
+        d = np.load(path)
+        self.set_weights(d["W1"], d["b1"], d["W2"], d["b2"], d["w3"], float(d["b3"]))
+
+    def close(self):
+        if self.ptr:
+            _check(lib().rlt2_mlp_destroy(self.ptr), "rlt2_mlp_destroy")
+            self.ptr = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rlt2_set_mlp(ctx: int, mlp: Optional["Mlp"]):
+    _check(lib().rlt2_set_mlp(ctx, mlp.ptr if mlp is not None else None), "rlt2_set_mlp")
+
+
 # ------------------------------------------------------------ convenience ----
 class Context:
     """Owns one rlt2_ctx: ``Context(F, D).iterate(300)``."""
@@ -288,6 +394,10 @@ class Context:
 
     def stats(self):
         return rlt2_stats(self.ctx)
+
+    def set_mlp(self, mlp):
+        self._mlp = mlp  # keep the network alive while attached
+        rlt2_set_mlp(self.ctx, mlp)
 
     def set_timing(self, on=True):
         rlt2_set_timing(self.ctx, on)

@@ -1,0 +1,128 @@
+"""Learned warm start on the GPU: features, tensor-core forward/backward and the
+exact-bound guarantee, against the CPU oracle's FP64 reference."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1710_03732_gb300 import instances as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_1710_03732_gb300 import build, rlt2
+    build.build()
+    rlt2.lib()
+    return rlt2
+
+
+def _tiles(rng, nt, m):
+    kind = rng.integers(0, 3)
+    if kind == 0:
+        return rng.integers(0, 40, (nt, m, m)).astype(np.float64)
+    return rng.normal(size=(nt, m, m)) * 10 ** rng.uniform(-2, 3)
+
+
+def _bf(x):
+    return np.array([O.bf16_round(float(v)) for v in np.ravel(x)], dtype=np.float32).reshape(np.shape(x))
+
+
+@pytest.mark.parametrize("m", [1, 5, 12, 18, 28, 32])
+def test_features_bit_identical(R, m):
+    rng = np.random.default_rng(m)
+    nt = 40
+    tiles = _tiles(rng, nt, m)
+    prev = rng.normal(size=(nt, m)) * 3
+    tgt = rng.normal(size=(nt, m)) * 3
+    mlp = R.Mlp(64, seed=1)
+    mlp.add_samples(torch.from_numpy(tiles).cuda(), torch.from_numpy(tgt).cuda(), torch.from_numpy(prev).cuda())
+    X, T = mlp.samples()
+    assert X.shape == (nt * m, 34)
+    for t in range(nt):
+        f, tt, _ = O.mlp_features(tiles[t], prev_u=prev[t], target_u=tgt[t])
+        assert np.array_equal(X[t * m:(t + 1) * m], _bf(f))
+        assert np.array_equal(T[t * m:(t + 1) * m], tt)
+
+
+def _random_weights(rng, H):
+    W1 = _bf(rng.normal(size=(34, H)).astype(np.float32) * 0.3)
+    W2 = _bf(rng.normal(size=(H, H)).astype(np.float32) / np.sqrt(H))
+    return [W1, (rng.normal(size=H) * 0.1).astype(np.float32), W2, (rng.normal(size=H) * 0.1).astype(np.float32),
+            (rng.normal(size=H) * 0.2).astype(np.float32), 0.07]
+
+
+@pytest.mark.parametrize("H", [64, 256])
+def test_forward_matches_oracle(R, H):
+    rng = np.random.default_rng(H)
+    m, nt = 18, 300
+    tiles = _tiles(rng, nt, m)
+    prev = rng.normal(size=(nt, m))
+    net = _random_weights(rng, H)
+    mlp = R.Mlp(H)
+    mlp.set_weights(*net)
+    u0 = torch.empty(nt, m, dtype=torch.float64, device="cuda")
+    mlp.predict(torch.from_numpy(tiles).cuda(), u0, torch.from_numpy(prev).cuda())
+    u0 = u0.cpu().numpy()
+    for t in range(0, nt, 7):
+        f, _, s = O.mlp_features(tiles[t], prev_u=prev[t])
+        out, _, _ = O.mlp_forward(f, *net, bf16_acts=True)
+        ref = np.float32(out.astype(np.float32)) * np.float32(s)
+        assert np.allclose(u0[t], ref, rtol=2e-3, atol=2e-3 * abs(s)), (u0[t], ref)
+
+
+@pytest.mark.parametrize("H", [64, 256])
+def test_gradients_match_oracle(R, H):
+    """Tensor-core backward (BF16 activations, FP32 accumulation) vs the FP64
+    oracle with the same BF16 rounding points: relative error <= 1e-2 per block."""
+    rng = np.random.default_rng(10 + H)
+    m, nt = 14, 150
+    tiles = _tiles(rng, nt, m)
+    prev = rng.normal(size=(nt, m))
+    tgt = rng.normal(size=(nt, m))
+    net = _random_weights(rng, H)
+    mlp = R.Mlp(H)
+    mlp.set_weights(*net)
+    mlp.add_samples(torch.from_numpy(tiles).cuda(), torch.from_numpy(tgt).cuda(), torch.from_numpy(prev).cuda())
+    X, T = mlp.samples()
+    rows = X.shape[0]
+    loss, *g = mlp.grad(rows)
+    oloss, *og = O.mlp_grads(X, *net, T.astype(np.float64), bf16_acts=True)
+    assert abs(loss - oloss) <= 1e-3 * abs(oloss)
+    for name, a, b in zip(["W1", "b1", "W2", "b2", "w3", "b3"], g, og):
+        a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+        err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        assert err <= 1e-2, (name, err)
+
+
+def test_training_reduces_loss_and_augmentations(R):
+    """Train on (tile, canonical dual) pairs harvested from an n=12 ascent, then
+    warm-start another n=12 ascent: bounds identical to the cold run (canonical
+    duals), fewer augmenting searches than cold."""
+    inst = I.config(2)
+    n, m = 12, 10
+    T = n * n * (n - 1) * (n - 1)
+    mlp = R.Mlp(256, seed=3)
+    with R.Context(inst.F, inst.D, prm=R.params(feas_tol=0.0)) as ctx:
+        prev = None
+        for it in range(12):
+            ctx.iterate(1)
+            D, _ = ctx.export_state()
+            xi = ctx.duals()["xi"]
+            if it >= 2:
+                mlp.add_samples(torch.from_numpy(D.reshape(T, m, m)).cuda(), torch.from_numpy(xi.reshape(T, m)).cuda(),
+                                torch.from_numpy(prev.reshape(T, m)).cuda())
+            prev = xi.copy()
+    hist = mlp.fit(300, batch_rows=8192, lr=2e-3)
+    assert hist[-20:].mean() < 0.5 * hist[:5].mean()
+    inst2 = I.grid_instance("n12b", 3, 4, 9, 0.5, 11, 40)
+    res = {}
+    for warm in (0, 2):
+        with R.Context(inst2.F, inst2.D, prm=R.params(feas_tol=0.0, warm=warm)) as ctx:
+            if warm == 2:
+                ctx.set_mlp(mlp)
+            lbs, _ = ctx.iterate(40)
+            res[warm] = (lbs, ctx.stats())
+    assert np.max(np.abs(res[2][0] - res[0][0]) / np.abs(res[0][0])) <= 1e-6
+    assert res[2][1][1] < res[0][1][1]
