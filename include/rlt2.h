@@ -192,6 +192,7 @@ rlt2_status rlt2_lap_batched(int batch, int m, const double* cost, const double*
  *  partials   : host, n_nodes*n ints, row k = partial assignment of node k
  *               (-1 = free); every node's residual size must be in [3, 32]
  *  p          : parameters (NULL = defaults), shared by all nodes
+ *  mlp        : network for warm == 2 (learned starts), else NULL
  *  iters      : iterations per node, 1..65536 (a node stops early on its own
  *               feasibility / gap / stall rule)
  *  mem_budget : device bytes the node arenas may use (0 = 80 % of free memory)
@@ -205,9 +206,10 @@ rlt2_status rlt2_lap_batched(int batch, int m, const double* cost, const double*
  *  stream     : cudaStream_t; the call synchronises it before returning
  * Errors: EINVAL (bad input), EADMIT (a node alone exceeds mem_budget),
  * ENOMEM, ECUDA.  Device memory is allocated for the call and freed on return. */
+typedef struct rlt2_mlp rlt2_mlp;
 rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D, const double* B, int n_nodes,
-                             const int* partials, const rlt2_params* p, int iters, size_t mem_budget, double* lb_out,
-                             double* lb_hist, int* iters_out, long long* stats_out, void* stream);
+                             const int* partials, const rlt2_params* p, rlt2_mlp* mlp, int iters, size_t mem_budget,
+                             double* lb_out, double* lb_hist, int* iters_out, long long* stats_out, void* stream);
 
 /* Dual ascent of a small QAP that allocates no device memory.  The paper has no
  * counterpart; this entry point exists for callers that cannot call cudaMalloc:
@@ -236,13 +238,13 @@ rlt2_status rlt2_iterate_noalloc(int n, const double* F, const double* D, const 
                                  int iters, double* lb_hist, void* stream);
 
 /* ---- learned warm start (not in the paper) ------------------------------
- * A per-row network predicts each Z-LAP row dual from the row's sorted,
- * column-min-reduced, max-scaled costs (FP32), the row's previous dual and
- * m/32 (34 features); 34 -> hidden -> hidden -> 1, ReLU, BF16 weights and
- * activations, FP32 accumulation on the tensor cores.  Predictions only seed
+ * A per-row network predicts the change of each Z-LAP row dual since the
+ * previous iteration from the row's sorted, column-min-reduced, max-scaled
+ * costs (FP32), the row's previous dual and m/32 (34 features); the start is
+ * u0 = u_prev + scale * prediction.  34 -> hidden -> hidden -> 1, ReLU, BF16
+ * weights and activations, FP32 accumulation on the tensor cores.  Predictions only seed
  * the exact Hungarian.  An rlt2_mlp is not thread-safe and must not be used by
  * two contexts whose work overlaps on the GPU. */
-typedef struct rlt2_mlp rlt2_mlp;
 
 /* hidden: multiple of 64 in [64, 1024]; seed: deterministic initialisation. */
 rlt2_status rlt2_mlp_create(int hidden, unsigned long long seed, void* stream, rlt2_mlp** out);
@@ -254,7 +256,8 @@ rlt2_status rlt2_mlp_get_weights(rlt2_mlp* m, float* W1, float* b1, float* W2, f
 rlt2_status rlt2_mlp_set_weights(rlt2_mlp* m, const float* W1, const float* b1, const float* W2, const float* b2,
                                  const float* w3, const float* b3);
 /* Append training rows: ntiles m x m tiles (device), their previous row duals
- * (device, nullable) and their optimal (canonical) row duals (device). */
+ * (device, nullable) and their optimal (canonical) row duals (device); the
+ * stored target is the scaled change (optimal - previous). */
 rlt2_status rlt2_mlp_add_samples(rlt2_mlp* m, long long ntiles, int mz, const double* tiles, const double* prev_u,
                                  const double* target_u);
 /* Number of rows; optional host copies of the BF16 feature rows (rows*64 of
@@ -269,6 +272,9 @@ rlt2_status rlt2_mlp_grad(rlt2_mlp* m, long long rows, double* loss, float* gW1,
  * drawn from the samples; loss_hist (host, steps, nullable). */
 rlt2_status rlt2_mlp_fit(rlt2_mlp* m, int steps, int batch_rows, double lr, double weight_decay,
                          unsigned long long seed, double* loss_hist);
+/* Drop predicted changes smaller than `gate` (in units of the tile scale):
+ * such rows start from their previous dual exactly (default 0). */
+rlt2_status rlt2_mlp_set_gate(rlt2_mlp* m, double gate);
 /* Predicted row duals u0 (device, ntiles*mz) for device tiles / previous duals. */
 rlt2_status rlt2_mlp_predict(rlt2_mlp* m, long long ntiles, int mz, const double* tiles, const double* prev_u,
                              double* u0);

@@ -642,7 +642,8 @@ float or_bf16_round(float x) {
  *  cf = trunc32(c); colmin_j = min_i cf_ij; R = cf - colmin;
  *  s = max R (1 if 0); inv = 1/s; row i: sort(R_i * inv) ascending, padded with
  *  zeros to 32; feature 32 = trunc32(prev_u_i) * inv (0 without prev);
- *  feature 33 = m/32.  Target (optional): trunc32(u*_i) * inv. */
+ *  feature 33 = m/32.  Target (optional): the change of the row dual,
+ *  trunc32(u*_i - prev_u_i) * inv (trunc32(u*_i) * inv without prev). */
 void or_mlp_features(int m, const double* tile, const double* prev_u, const double* target_u, float* feat,
                      float* target_out, float* scale_out) {
   float cf[32 * 32], cmin[32], s = 0.0f;
@@ -676,7 +677,7 @@ void or_mlp_features(int m, const double* tile, const double* prev_u, const doub
     for (int k = 0; k < 32; k++) feat[i * OR_MLP_IN + k] = k < m ? row[k] : 0.0f;
     feat[i * OR_MLP_IN + 32] = prev_u ? or_f32_trunc(prev_u[i]) * inv : 0.0f;
     feat[i * OR_MLP_IN + 33] = (float)m / 32.0f;
-    if (target_u && target_out) target_out[i] = or_f32_trunc(target_u[i]) * inv;
+    if (target_u && target_out) target_out[i] = or_f32_trunc(prev_u ? target_u[i] - prev_u[i] : target_u[i]) * inv;
   }
   if (scale_out) *scale_out = s;
 }

@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap_nodes(NodeLapArg
         tile[r * ld + c] = x;
       }
     }
-    const bool warm = have && it.u0 != nullptr && *it.warm_gate != 0;
+    const bool warm = have && it.u0 != nullptr && (it.warm_gate == nullptr || *it.warm_gate != 0);
     const double u0 = (warm && gl < m) ? it.u0[li * m + gl] : 0.0;
     __syncwarp();
     const WarpLapResult R = group_lap<G>(tile, ld, m, lane, warm, u0, a.dual_mode, scr);

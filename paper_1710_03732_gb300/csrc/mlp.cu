@@ -1,10 +1,10 @@
 // Learned warm start for the Z-LAPs (not in the paper; the paper's only warm
 // start is parent -> child multipliers in branch and bound, Section 4).
 //
-// A per-row network predicts each row dual of a Z-LAP from that row's sorted,
-// column-min-reduced, max-scaled costs, the row's dual from the previous
-// iteration and m/32 (34 features, so one set of weights serves every LAP size
-// m <= 32).  The prediction only seeds the exact Hungarian: the column-min
+// A per-row network predicts how much each row dual of a Z-LAP changed since
+// the previous iteration, from that row's sorted, column-min-reduced,
+// max-scaled costs, the row's previous dual and m/32 (34 features, so one set
+// of weights serves every LAP size m <= 32): u0 = u_prev + scale * net.  The prediction only seeds the exact Hungarian: the column-min
 // repair makes it feasible and the searches finish the solve, so bounds are
 // exactly those of a cold start; what the network saves is augmenting searches.
 //
@@ -103,7 +103,12 @@ __global__ void __launch_bounds__(256) k_features(long long ntiles, int m, const
       if (lane == 1) hi = (float)m / 32.0f;
       xr[32 + lane] = __float2bfloat16_rn(hi);
     }
-    if (target && target_u && lane < m) target[t * m + lane] = __fmul_rn(f32_trunc(target_u[t * m + lane]), inv);
+    if (target && target_u && lane < m) {
+      // the network predicts the change of the row dual since the previous iteration
+      const long long r = t * m + lane;
+      const double d = prev_u ? __dsub_rn(target_u[r], prev_u[r]) : target_u[r];
+      target[r] = __fmul_rn(f32_trunc(d), inv);
+    }
   }
 }
 
@@ -275,11 +280,16 @@ __global__ void k_out(long long rows, int H, const bf16* __restrict__ H2, const 
   }
 }
 
-// u0 = out * scale of the row's tile (FP32 product, widened exactly)
+// u0 = prev + out * scale of the row's tile (FP32 product, widened exactly);
+// predicted changes below `gate` (in scaled units) are dropped so that the row
+// keeps its previous dual exactly
 __global__ void k_u0(long long rows, int m, const float* __restrict__ out, const float* __restrict__ scale,
-                     double* __restrict__ u0) {
-  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x)
-    u0[r] = (double)__fmul_rn(out[r], scale[r / m]);
+                     const double* __restrict__ prev_u, float gate, double* __restrict__ u0) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x) {
+    const float o = fabsf(out[r]) < gate ? 0.0f : out[r];
+    const double d = (double)__fmul_rn(o, scale[r / m]);
+    u0[r] = prev_u ? __dadd_rn(prev_u[r], d) : d;
+  }
 }
 
 // dout = (out - t)/nvalid on valid rows; loss += 0.5 e^2 / nvalid
@@ -399,6 +409,7 @@ struct rlt2_mlp {
   float* grad = nullptr; // nparams, same packing as the parameters
   long long nparams = 0;
   int adam_t = 0;
+  float gate = 0.0f;
   // dataset (feature rows + targets)
   bf16* Xd = nullptr;
   float* Td = nullptr;
@@ -525,8 +536,8 @@ cudaError_t mlp_predict_enqueue(rlt2_mlp* m, long long ntiles, int mz, const dou
                             cudaSuccess)
       return e;
     if ((e = forward(m, m->Xc, prows, m->out, s)) != cudaSuccess) return e;
-    k_u0<<<(int)std::min<long long>(4096, (rows + 255) / 256), 256, 0, s>>>(rows, mz, m->out, m->scale,
-                                                                            u0 + t0 * mz);
+    k_u0<<<(int)std::min<long long>(4096, (rows + 255) / 256), 256, 0, s>>>(
+        rows, mz, m->out, m->scale, prev_u ? prev_u + t0 * mz : nullptr, m->gate, u0 + t0 * mz);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -757,6 +768,12 @@ extern "C" rlt2_status rlt2_mlp_fit(rlt2_mlp* m, int steps, int batch_rows, doub
   CKM(cudaStreamSynchronize(s));
   if (loss_hist)
     for (int st = 0; st < steps; ++st) loss_hist[st] = losses[st];
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_mlp_set_gate(rlt2_mlp* m, double gate) {
+  if (!m || !(gate >= 0.0)) return RLT2_EINVAL;
+  m->gate = (float)gate;
   return RLT2_OK;
 }
 

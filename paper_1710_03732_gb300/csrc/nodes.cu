@@ -112,6 +112,7 @@ void carve(NodeHost& h, char* base, const rlt2_params& prm) {
   v.sc = ar.take<DevScalars>(1);
   v.xperm = ar.take<int>(n);
   v.ubperm = ar.take<int>(n);
+  v.u0buf = prm.warm == 2 ? ar.take<double>(T * m) : nullptr;
   h.dfac = ar.take<int>((size_t)2 * n + h.fixf.size() * 2 + v.ntrip);
   v.trips = h.dfac ? h.dfac + 2 * n + 2 * h.fixf.size() : nullptr;
   h.bytes = ar.used;
@@ -136,7 +137,17 @@ struct WaveDev {
   unsigned long long* stats = nullptr;  // [6]
 };
 
+struct LearnedStart {
+  long long T;
+  int m;
+  const double* Dhat;
+  const double* xi;
+  double* u0;
+};
+
 struct Wave {
+  rlt2_mlp* mlp = nullptr;
+  std::vector<LearnedStart> learned;  // one per node when warm == 2
   int nn = 0;
   long long total[3] = {0, 0, 0};
   int max_m[3] = {0, 0, 0};
@@ -154,6 +165,8 @@ cudaError_t enqueue_wave_iteration(const Wave& w, const WaveDev& d, int dual_mod
   }
   k_move_z_nodes<<<dim3(w.max_blocks, w.nn), 128, 0, s>>>(d.mz, d.mz_blocks);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  for (const LearnedStart& ls : w.learned)
+    if ((e = mlp_predict_enqueue(w.mlp, ls.T, ls.m, ls.Dhat, ls.xi, ls.u0, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(d.heads, 0, 3 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
   for (int stage = 0; stage < 3; ++stage) {
     NodeLapArgs a{};
@@ -190,7 +203,8 @@ using namespace rlt2;
   } while (0)
 
 extern "C" rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D, const double* B, int n_nodes,
-                                        const int* partials, const rlt2_params* p, int iters, size_t mem_budget,
+                                        const int* partials, const rlt2_params* p, rlt2_mlp* mlp, int iters,
+                                        size_t mem_budget,
                                         double* lb_out, double* lb_hist, int* iters_out, long long* stats_out,
                                         void* stream) {
   if (n < 3 || n > 64 || !F || !D || n_nodes < 1 || !partials || iters < 1 || iters > kRing || !lb_out) {
@@ -208,6 +222,10 @@ extern "C" rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D,
   if (p) prm = *p;
   if (!params_valid(prm)) {
     set_error("rlt2_bound_nodes: parameters out of range");
+    return RLT2_EINVAL;
+  }
+  if (prm.warm == 2 && !mlp) {
+    set_error("rlt2_bound_nodes: warm == 2 needs a network");
     return RLT2_EINVAL;
   }
   // per-node residual problems
@@ -308,6 +326,7 @@ extern "C" rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D,
   for (auto& wr : waves) {
     Wave w;
     w.nn = wr.second - wr.first;
+    w.mlp = prm.warm == 2 ? mlp : nullptr;
     // carve the arenas and upload each node's index lists
     char* cur = pool;
     std::vector<NodeLapItem> items(3 * kMaxWaveNodes);
@@ -346,8 +365,9 @@ extern "C" rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D,
       z.count = v.T;
       z.m = nr - 2;
       z.A = v.Dhat;
-      z.u0 = prm.warm ? v.xi : nullptr;
-      z.warm_gate = &v.sc->have_snap;
+      z.u0 = prm.warm == 1 ? v.xi : (prm.warm == 2 ? v.u0buf : nullptr);
+      z.warm_gate = prm.warm == 2 ? nullptr : &v.sc->have_snap;
+      if (prm.warm == 2) w.learned.push_back(LearnedStart{v.T, nr - 2, v.Dhat, v.xi, v.u0buf});
       z.skip = &v.sc->done;
       z.value = v.Theta;
       z.u = v.xi;

@@ -43,7 +43,7 @@ EXPORTS = ["rlt2_params_default", "rlt2_create", "rlt2_iterate", "rlt2_iterate_a
            "rlt2_set_timing", "rlt2_kernel_times", "rlt2_destroy", "rlt2_lap_batched", "rlt2_bound_nodes",
            "rlt2_iterate_noalloc", "rlt2_mlp_create", "rlt2_mlp_destroy", "rlt2_mlp_get_weights",
            "rlt2_mlp_set_weights", "rlt2_mlp_add_samples", "rlt2_mlp_samples", "rlt2_mlp_clear_samples",
-           "rlt2_mlp_grad", "rlt2_mlp_fit", "rlt2_mlp_predict", "rlt2_set_mlp",
+           "rlt2_mlp_grad", "rlt2_mlp_fit", "rlt2_mlp_set_gate", "rlt2_mlp_predict", "rlt2_set_mlp",
            "rlt2_strerror", "rlt2_last_error"]
 
 
@@ -72,7 +72,7 @@ def lib():
     L.rlt2_kernel_times.argtypes = [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     L.rlt2_destroy.argtypes = [_vp]
     L.rlt2_lap_batched.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp]
-    L.rlt2_bound_nodes.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, _ip, ctypes.POINTER(rlt2_params),
+    L.rlt2_bound_nodes.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, _ip, ctypes.POINTER(rlt2_params), _vp,
                                    ctypes.c_int, ctypes.c_size_t, _dp, _dp, _ip, ctypes.POINTER(ctypes.c_longlong), _vp]
     L.rlt2_iterate_noalloc.argtypes = [ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(rlt2_params), ctypes.c_int, _vp,
                                        _vp]
@@ -88,6 +88,7 @@ def lib():
     L.rlt2_mlp_fit.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_ulonglong,
                                _dp]
     L.rlt2_mlp_predict.argtypes = [_vp, ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp]
+    L.rlt2_mlp_set_gate.argtypes = [_vp, ctypes.c_double]
     L.rlt2_set_mlp.argtypes = [_vp, _vp]
     L.rlt2_strerror.argtypes = [ctypes.c_int]
     L.rlt2_strerror.restype = ctypes.c_char_p
@@ -234,7 +235,7 @@ def rlt2_lap_batched(cost, value, u0=None, u=None, v=None, row_to_col=None, n_au
 
 
 def rlt2_bound_nodes(F, D, partials, iters: int, B=None, prm: Optional[rlt2_params] = None, mem_budget: int = 0,
-                     stream=None):
+                     stream=None, mlp=None):
     """Bound every node (row of `partials`); returns (best bounds, bound history
     [n_nodes, iters], iterations per node, stats {waves, z_aug, z_relax, group, wpb})."""
     F = np.ascontiguousarray(F, dtype=np.float64)
@@ -247,7 +248,8 @@ def rlt2_bound_nodes(F, D, partials, iters: int, B=None, prm: Optional[rlt2_para
     its = np.zeros(nn, dtype=np.int32)
     st = (ctypes.c_longlong * 5)()
     _check(lib().rlt2_bound_nodes(n, _host_d(F), _host_d(D), _host_d(B), nn, part.ctypes.data_as(_ip),
-                                  None if prm is None else ctypes.byref(prm), iters, mem_budget, _host_d(lb),
+                                  None if prm is None else ctypes.byref(prm), None if mlp is None else mlp.ptr, iters,
+                                  mem_budget, _host_d(lb),
                                   _host_d(hist), its.ctypes.data_as(_ip), st, _stream(stream)), "rlt2_bound_nodes")
     stats = dict(zip(["waves", "z_aug", "z_relax", "group", "wpb"], list(st)))
     return lb, hist, its, stats
@@ -323,6 +325,9 @@ class Mlp:
         hist = np.zeros(steps)
         _check(lib().rlt2_mlp_fit(self.ptr, steps, batch_rows, lr, weight_decay, seed, _host_d(hist)), "rlt2_mlp_fit")
         return hist
+
+    def set_gate(self, gate: float):
+        _check(lib().rlt2_mlp_set_gate(self.ptr, float(gate)), "rlt2_mlp_set_gate")
 
     def predict(self, tiles, u0, prev_u=None):
         nt, m = int(tiles.shape[0]), int(tiles.shape[1])

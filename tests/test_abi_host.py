@@ -116,8 +116,8 @@ def test_bound_nodes_rejects_bad_input(L):
     def call(parts, iters=5):
         parts = np.ascontiguousarray(parts, dtype=np.int32)
         return L.rlt2_bound_nodes(n, F.ctypes.data_as(dp), F.ctypes.data_as(dp), None, parts.shape[0],
-                                  parts.ctypes.data_as(ip), None, iters, 0, lb.ctypes.data_as(dp), None, None, None,
-                                  None)
+                                  parts.ctypes.data_as(ip), None, None, iters, 0, lb.ctypes.data_as(dp), None, None,
+                                  None, None)
     ok = -np.ones((2, n))
     assert call(ok, iters=0) == rlt2.RLT2_EINVAL
     bad = ok.copy()

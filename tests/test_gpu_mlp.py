@@ -68,7 +68,7 @@ def test_forward_matches_oracle(R, H):
     for t in range(0, nt, 7):
         f, _, s = O.mlp_features(tiles[t], prev_u=prev[t])
         out, _, _ = O.mlp_forward(f, *net, bf16_acts=True)
-        ref = np.float32(out.astype(np.float32)) * np.float32(s)
+        ref = prev[t] + (np.float32(out.astype(np.float32)) * np.float32(s)).astype(np.float64)
         assert np.allclose(u0[t], ref, rtol=2e-3, atol=2e-3 * abs(s)), (u0[t], ref)
 
 
