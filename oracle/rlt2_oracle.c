@@ -32,10 +32,14 @@
  *   - all reduced costs come from one snapshot before any cost moves (Jacobi);
  *   - LAP duals: raw (this Hungarian's own) or canonical (pointwise-maximal
  *     row duals with u_0 = 0 among all optimal duals; unique);
- *   - per z entry a=(i,j,k,p,q,r), s(a) = kz*pi_z(a) + (cy*pi_y(ijpq) + cx*pi_x(ip)),
+ *   - per z entry a=(i,j,k,p,q,r), s(a) = fma(kz, pi_z(a), cy*pi_y(ijpq) + cx*pi_x(ip)),
  *     cy = ky/(n-2), cx = kx/((n-1)(n-2))  (Eq. 2.20, 2.22, 2.23 combined as
  *     in the proof of Theorem 1), and
- *     D^'(a) = (D^(a) - s(a)) + sum over the five partners b of phi(b->a)*s(b);
+ *     D^'(a) = (D^(a) - s(a)) + sum over the five partners b of phi(b->a)*s(b),
+ *     the partner terms added one fused multiply-add (C99 fma) at a time; with
+ *     all phi equal, D^'(a) = fma(phi, S - s(a), D^(a) - s(a)), S = sum of the
+ *     class's six s in member order;
+ *   - an LAP optimum is summed as a pairwise tree;
  *   - y move (Eq. 2.21): C^'_ijpq = (C^_ijpq - phi_y*pi_y(ijpq)) + phi_y*pi_y(jiqp).
  */
 #include <math.h>
@@ -155,9 +159,15 @@ int or_lap(int m, const double* c, const double* u0, double* value, double* u, d
     for (int r = 0; r < m; r++)
       if (row_to_col[r] >= 0) u[r] = c[r * m + row_to_col[r]] - v[row_to_col[r]];
   }
-  double val = 0.0;
-  for (int r = 0; r < m; r++) val = val + c[r * m + row_to_col[r]];
-  if (value) *value = val;
+  /* optimum: pairwise tree sum over P = next power of two >= m leaves (rows
+   * beyond m are empty), adding s[i] + s[i + h] for h = P/2, ..., 1 */
+  double leaf[64];
+  int P = 1;
+  while (P < m) P <<= 1;
+  for (int r = 0; r < P; r++) leaf[r] = r < m ? c[r * m + row_to_col[r]] : 0.0;
+  for (int h = P / 2; h >= 1; h /= 2)
+    for (int r = 0; r < h; r++) leaf[r] = leaf[r] + leaf[r + h];
+  if (value) *value = leaf[0];
   if (n_aug) *n_aug = aug;
   if (n_relax) *n_relax = relax;
   free(col_to_row);
@@ -489,6 +499,7 @@ void or_redistribute_z(int n, const double* prm, double* Dhat, const double* xi,
     for (int b = 0; b < 6; b++) gives[a][b] = 0.0;
     for (int l = 0; l < 5; l++) gives[a][pmap[a][l]] = phi[l];
   }
+  int uniform = phi[0] == phi[1] && phi[0] == phi[2] && phi[0] == phi[3] && phi[0] == phi[4];
   int ntrip = 0;
   int(*trip)[3] = (int(*)[3])malloc(sizeof(int[3]) * (size_t)(n * n * n / 6 + 1));
   for (int i = 0; i < n; i++)
@@ -519,19 +530,26 @@ void or_redistribute_z(int n, const double* prm, double* Dhat, const double* xi,
             int li = l3[M[a][0]], lj = l3[M[a][1]], lk = l3[M[a][2]];
             double pz = piz_at(n, Dhat, xi, psi, fi, fj, fk, li, lj, lk);
             double ty = cy * piy[tile_of(n, fi, li, fj, lj)] + cx * pix[fi * n + li];
-            s[a] = kz * pz + ty;
+            s[a] = fma(kz, pz, ty);
             idx[a] = zidx(n, fi, fj, fk, li, lj, lk);
           }
           double newv[6];
-          for (int a = 0; a < 6; a++) {
-            /* inflow from a's partners b1..b5, summed in that order */
-            double inflow = 0.0;
-            for (int l = 0; l < 5; l++) {
-              int b = pmap[a][l];
-              double term = gives[b][a] * s[b];
-              inflow = (l == 0) ? term : inflow + term;
+          if (uniform) {
+            /* all phi equal: a receives phi * (sum of the other five s) */
+            double S = s[0];
+            for (int b = 1; b < 6; b++) S = S + s[b];
+            for (int a = 0; a < 6; a++) newv[a] = fma(phi[0], S - s[a], Dhat[idx[a]] - s[a]);
+          } else {
+            /* inflow from a's partners b1..b5 added in that order, one fused
+             * multiply-add each, onto D^ - s */
+            for (int a = 0; a < 6; a++) {
+              double acc = Dhat[idx[a]] - s[a];
+              for (int l = 0; l < 5; l++) {
+                int b = pmap[a][l];
+                acc = fma(gives[b][a], s[b], acc);
+              }
+              newv[a] = acc;
             }
-            newv[a] = (Dhat[idx[a]] - s[a]) + inflow;
           }
           for (int a = 0; a < 6; a++) Dhat[idx[a]] = newv[a];
         }

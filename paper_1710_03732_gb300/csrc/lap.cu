@@ -20,7 +20,7 @@ int default_group(int m) { return m <= 8 ? 8 : (m <= 16 ? 16 : 32); }
 
 // Grid-stride over LAPs, 32/G LAPs per warp per step; each group of G lanes
 // stages its own tile (coalesced: a group reads a contiguous m*m run).
-template <int G>
+template <int G, bool PRE>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap(LapArgs a) {
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -56,7 +56,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap(LapArgs a) {
     double u0 = 0.0;
     if (warm && have && gl < m) u0 = a.u0[t * m + gl];
     __syncwarp();
-    const WarpLapResult R = group_lap<G>(tile, ld, have ? m : 0, lane, warm, u0, a.dual_mode, scr);
+    // without a reduced-cost output (PRE) the tile may be overwritten by the canonical pass
+    const WarpLapResult R = group_lap<G, PRE>(tile, ld, have ? m : 0, lane, warm, u0, a.dual_mode, scr, uv + grp * G);
     if (have && gl < m) {
       if (a.u) a.u[t * m + gl] = R.u;
       if (a.v) a.v[t * m + gl] = R.v;
@@ -101,17 +102,20 @@ static cudaError_t prepare_one(int m, int wpb) {
   if (slot > 0) return cudaSuccess;
   static bool attr_set[3] = {false, false, false};
   cudaError_t e;
+  const int cap = (int)(warp_smem_bytes(32, 32) * kMaxWarpsPerBlock);
   if (!attr_set[gidx(G)]) {
-    e = cudaFuncSetAttribute(k_lap<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(warp_smem_bytes(32, 32) * kMaxWarpsPerBlock > warp_smem_bytes(G, G) * kMaxWarpsPerBlock
-                                       ? warp_smem_bytes(32, 32) * kMaxWarpsPerBlock
-                                       : warp_smem_bytes(G, G) * kMaxWarpsPerBlock));
-    if (e != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_lap<G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess)
+      return e;
+    if ((e = cudaFuncSetAttribute(k_lap<G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess)
+      return e;
     attr_set[gidx(G)] = true;
   }
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lap<G>, wpb * 32, warp_smem_bytes(m, G) * wpb);
+  int occ = 0, occ2 = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lap<G, true>, wpb * 32, warp_smem_bytes(m, G) * wpb);
   if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_lap<G, false>, wpb * 32, warp_smem_bytes(m, G) * wpb);
+  if (e != cudaSuccess) return e;
+  occ = occ < occ2 ? occ : occ2;
   slot = occ < 1 ? 1 : occ;
   return cudaSuccess;
 }
@@ -145,9 +149,17 @@ cudaError_t launch_lap(const LapArgs& a, cudaStream_t s) {
   const long long need = (a.batch + per_block - 1) / per_block;
   const long long cap = (long long)g_sms * g_occ[a.m][gidx(G)][wpb == 4 ? 0 : 1];
   const int grid = (int)(need < cap ? need : cap);
-  if (G == 8) k_lap<8><<<grid, wpb * 32, smem, s>>>(a);
-  else if (G == 16) k_lap<16><<<grid, wpb * 32, smem, s>>>(a);
-  else k_lap<32><<<grid, wpb * 32, smem, s>>>(a);
+  const bool pre = a.pi == nullptr;
+  if (G == 8) {
+    if (pre) k_lap<8, true><<<grid, wpb * 32, smem, s>>>(a);
+    else k_lap<8, false><<<grid, wpb * 32, smem, s>>>(a);
+  } else if (G == 16) {
+    if (pre) k_lap<16, true><<<grid, wpb * 32, smem, s>>>(a);
+    else k_lap<16, false><<<grid, wpb * 32, smem, s>>>(a);
+  } else {
+    if (pre) k_lap<32, true><<<grid, wpb * 32, smem, s>>>(a);
+    else k_lap<32, false><<<grid, wpb * 32, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -155,7 +167,7 @@ cudaError_t launch_lap(const LapArgs& a, cudaStream_t s) {
 // Batched branch-and-bound nodes: one persistent launch per stage over the LAPs
 // of every node of a wave.  Warps pull 32/G LAPs at a time from a device queue
 // (atomic head, no waiting), so nodes of uneven size share the GPU.
-template <int G>
+template <int G, bool PRE>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap_nodes(NodeLapArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int per = 32 / G;
@@ -210,7 +222,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap_nodes(NodeLapArg
     const bool warm = have && it.u0 != nullptr && (it.warm_gate == nullptr || *it.warm_gate != 0);
     const double u0 = (warm && gl < m) ? it.u0[li * m + gl] : 0.0;
     __syncwarp();
-    const WarpLapResult R = group_lap<G>(tile, ld, m, lane, warm, u0, a.dual_mode, scr);
+    const WarpLapResult R = group_lap<G, PRE>(tile, ld, m, lane, warm, u0, a.dual_mode, scr, uv + grp * G);
     if (have && gl < m) {
       if (it.u) it.u[li * m + gl] = R.u;
       if (it.v) it.v[li * m + gl] = R.v;
@@ -261,36 +273,55 @@ cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s) {
   const size_t cap_smem = (((size_t)(kMaxWaveNodes + 1) * sizeof(long long)) + 255) / 256 * 256 +
                           warp_smem_bytes(32, 32) * kMaxWarpsPerBlock;
   int& occ = g_occ_nodes[a.max_m][gidx(G)][wpb == 4 ? 0 : 1];
-  if (G == 8) {
-    if (!attr_set[0] && (e = cudaFuncSetAttribute(k_lap_nodes<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)cap_smem)) != cudaSuccess)
-      return e;
-    attr_set[0] = true;
-    if (!occ && (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lap_nodes<8>, wpb * 32, smem)) != cudaSuccess)
-      return e;
-  } else if (G == 16) {
-    if (!attr_set[1] && (e = cudaFuncSetAttribute(k_lap_nodes<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)cap_smem)) != cudaSuccess)
-      return e;
-    attr_set[1] = true;
-    if (!occ && (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lap_nodes<16>, wpb * 32, smem)) != cudaSuccess)
-      return e;
-  } else {
-    if (!attr_set[2] && (e = cudaFuncSetAttribute(k_lap_nodes<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)cap_smem)) != cudaSuccess)
-      return e;
-    attr_set[2] = true;
-    if (!occ && (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lap_nodes<32>, wpb * 32, smem)) != cudaSuccess)
-      return e;
+  auto setup = [&](auto kern) -> cudaError_t {
+    cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap_smem);
+    if (e2 != cudaSuccess) return e2;
+    int o = 0;
+    e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, wpb * 32, smem);
+    if (e2 != cudaSuccess) return e2;
+    if (!occ || o < occ) occ = o;
+    return cudaSuccess;
+  };
+  if (!attr_set[gidx(G)]) {
+    if (G == 8) {
+      if ((e = setup(k_lap_nodes<8, true>)) != cudaSuccess || (e = setup(k_lap_nodes<8, false>)) != cudaSuccess) return e;
+    } else if (G == 16) {
+      if ((e = setup(k_lap_nodes<16, true>)) != cudaSuccess || (e = setup(k_lap_nodes<16, false>)) != cudaSuccess)
+        return e;
+    } else {
+      if ((e = setup(k_lap_nodes<32, true>)) != cudaSuccess || (e = setup(k_lap_nodes<32, false>)) != cudaSuccess)
+        return e;
+    }
+    attr_set[gidx(G)] = true;
+  } else if (!occ) {
+    int o1 = 0, o2 = 0;
+    if (G == 8) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_lap_nodes<8, true>, wpb * 32, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_lap_nodes<8, false>, wpb * 32, smem);
+    } else if (G == 16) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_lap_nodes<16, true>, wpb * 32, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_lap_nodes<16, false>, wpb * 32, smem);
+    } else {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_lap_nodes<32, true>, wpb * 32, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_lap_nodes<32, false>, wpb * 32, smem);
+    }
+    occ = o1 < o2 ? o1 : o2;
   }
   if (occ < 1) occ = 1;
   const long long per_block = (long long)wpb * (32 / G);
   const long long need = (a.total + per_block - 1) / per_block;
   const long long cap = (long long)g_sms * occ;
   const int grid = (int)(need < cap ? need : cap);
-  if (G == 8) k_lap_nodes<8><<<grid, wpb * 32, smem, s>>>(a);
-  else if (G == 16) k_lap_nodes<16><<<grid, wpb * 32, smem, s>>>(a);
-  else k_lap_nodes<32><<<grid, wpb * 32, smem, s>>>(a);
+  if (G == 8) {
+    if (a.pre) k_lap_nodes<8, true><<<grid, wpb * 32, smem, s>>>(a);
+    else k_lap_nodes<8, false><<<grid, wpb * 32, smem, s>>>(a);
+  } else if (G == 16) {
+    if (a.pre) k_lap_nodes<16, true><<<grid, wpb * 32, smem, s>>>(a);
+    else k_lap_nodes<16, false><<<grid, wpb * 32, smem, s>>>(a);
+  } else {
+    if (a.pre) k_lap_nodes<32, true><<<grid, wpb * 32, smem, s>>>(a);
+    else k_lap_nodes<32, false><<<grid, wpb * 32, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -180,6 +180,7 @@ cudaError_t enqueue_wave_iteration(const Wave& w, const WaveDev& d, int dual_mod
     a.stats = d.stats + 2 * stage;
     a.group = stage == 0 ? zgroup : 0;
     a.warps_per_block = stage == 0 ? zwpb : 0;
+    a.pre = stage == 0;  // the Z stage writes no reduced costs
     if (stage == 0 && zev0 && (e = cudaEventRecord(zev0, s)) != cudaSuccess) return e;
     if ((e = launch_lap_nodes(a, s)) != cudaSuccess) return e;
     if (stage == 0 && zev1 && (e = cudaEventRecord(zev1, s)) != cudaSuccess) return e;

@@ -52,7 +52,7 @@ struct MoveZArgs {
   double kz;
   double w[5];  // weight received from partner l (phi permuted by h_widx)
   int kz_one;   // kz == 1: kz*x == x exactly, skip the product
-  int uniform;  // all phi equal: each s_b is scaled once
+  int uniform;  // all phi equal: member b gets phi * (class sum - s_b)
   double* Dhat;
   const double* xi;
   const double* psi;
@@ -93,26 +93,24 @@ __device__ __forceinline__ void move_z_block(const MoveZArgs& a, int blk) {
       idx[b] = t * mm + kr * m + cc;
       Dv[b] = a.Dhat[idx[b]];
       const double pz = dsub_(dsub_(Dv[b], __ldg(a.xi + t * m + kr)), __ldg(a.psi + t * m + cc));
-      s[b] = dadd_(a.kz_one ? pz : dmul_(a.kz, pz), __ldg(a.tterm + t));
+      // s = kz*pi_z + tile term in one rounding (kz = 1: an exact fma(1, x, y) is x + y)
+      s[b] = a.kz_one ? dadd_(pz, __ldg(a.tterm + t)) : __fma_rn(a.kz, pz, __ldg(a.tterm + t));
     }
     if (a.uniform) {
-      double ws[6];
+      // all phi equal: member b receives phi * (S - s_b), S the class sum in member order
+      double S = s[0];
 #pragma unroll
-      for (int b = 0; b < 6; ++b) ws[b] = dmul_(a.w[0], s[b]);
+      for (int b = 1; b < 6; ++b) S = dadd_(S, s[b]);
 #pragma unroll
-      for (int b = 0; b < 6; ++b) {
-        double in = ws[kPart[b][0]];
-#pragma unroll
-        for (int l = 1; l < 5; ++l) in = dadd_(in, ws[kPart[b][l]]);
-        a.Dhat[idx[b]] = dadd_(dsub_(Dv[b], s[b]), in);
-      }
+      for (int b = 0; b < 6; ++b) a.Dhat[idx[b]] = __fma_rn(a.w[0], dsub_(S, s[b]), dsub_(Dv[b], s[b]));
     } else {
+      // partner inflows one fused multiply-add at a time, partners in Eq. 2.20 order
 #pragma unroll
       for (int b = 0; b < 6; ++b) {
-        double in = dmul_(a.w[0], s[kPart[b][0]]);
+        double acc = dsub_(Dv[b], s[b]);
 #pragma unroll
-        for (int l = 1; l < 5; ++l) in = dadd_(in, dmul_(a.w[l], s[kPart[b][l]]));
-        a.Dhat[idx[b]] = dadd_(dsub_(Dv[b], s[b]), in);
+        for (int l = 0; l < 5; ++l) acc = __fma_rn(a.w[l], s[kPart[b][l]], acc);
+        a.Dhat[idx[b]] = acc;
       }
     }
   }

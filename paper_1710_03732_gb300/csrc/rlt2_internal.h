@@ -59,6 +59,7 @@ struct NodeLapArgs {
   unsigned long long* head;
   unsigned long long* stats;  // device [2]: augmentations, relaxations (nullable)
   int group, warps_per_block;
+  bool pre;  // no node of the stage writes reduced costs (the tile may be reduced in place)
 };
 cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s);
 

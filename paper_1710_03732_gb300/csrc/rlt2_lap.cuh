@@ -26,7 +26,7 @@
 //             relax only on strict '<'; stop at the first free column.
 //   duals     v_c = v_c + (d_c - d_sink) on scanned columns, augment, then
 //             u_r = c_{r,sigma(r)} - v_{sigma(r)} for every matched row
-//   value     sum_r c_{r,sigma(r)} in increasing r
+//   value     sum_r c_{r,sigma(r)} as a pairwise tree (lane i += lane i+h, h = P/2..1)
 //   canonical (dual_mode 1) Dijkstra from row 0 over arcs r'->r with weight
 //             pi(r, sigma(r')) (>= 0), u^c_r = dist_r + (u_r - u_0),
 //             v^c_c = c_{sigma^-1(c),c} - u^c_{sigma^-1(c)}
@@ -100,9 +100,11 @@ __device__ __forceinline__ unsigned group_bits(unsigned ball, int gb) {
 // group's m x m tile (row stride ld) in shared memory, `scr` G ints of group
 // scratch, m the group's LAP size (0 = no LAP, 1 <= m <= G otherwise).  The
 // arithmetic is identical for every G.
-template <int G>
-__device__ __forceinline__ WarpLapResult group_lap(const double* __restrict__ cs, int ld, int m, int lane, bool warm,
-                                                   double u0, int dual_mode, int* scr) {
+// PRE: the caller does not need the tile afterwards, so the canonical pass may
+// replace it by its reduced costs first (uvs: 64 doubles of group staging).
+template <int G, bool PRE>
+__device__ __forceinline__ WarpLapResult group_lap(double* __restrict__ cs, int ld, int m, int lane, bool warm,
+                                                   double u0, int dual_mode, int* scr, double* uvs) {
   const int gl = lane & (G - 1);
   const int gb = lane - gl;
   const bool cv = gl < m;
@@ -203,20 +205,39 @@ __device__ __forceinline__ WarpLapResult group_lap(const double* __restrict__ cs
     if (act && cv && r2c >= 0) u = dsub(cs[gl * ld + r2c], vm);
   }
 
-  // optimum, summed in increasing row order
+  // optimum: pairwise tree over P = next power of two >= m rows (empty rows add
+  // nothing), lane i adding lane i + h for h = P/2, ..., 1
   const double xr = cv ? cs[gl * ld + r2c] : 0.0;
-  double val = 0.0;
-  for (int r = 0; r < M; ++r) {
-    const double t = __shfl_sync(kFull, xr, gb + r);
-    if (gl == 0 && r < m) val = dadd(val, t);
+  int P = 1;
+  while (P < m) P <<= 1;
+  const int PM = (G == 32) ? P : (int)__reduce_max_sync(kFull, (unsigned)P);
+  double val = xr;
+  for (int h = PM >> 1; h >= 1; h >>= 1) {
+    const double o = __shfl_xor_sync(kFull, val, h);
+    if (h < P) val = dadd(val, o);
   }
   val = __shfl_sync(kFull, val, gb);
 
   if (dual_mode == 1) {
-    // shortest paths from row 0 on reduced weights pi(r, sigma(r')) >= 0
+    // canonical duals: shortest paths from row 0 on reduced weights
+    // pi(r, sigma(r')) = (c_{r,sigma(r')} - u_r) - v_{sigma(r')} >= 0
     const int s0 = __shfl_sync(kFull, r2c, gb);
+    if constexpr (PRE) {
+      uvs[gl] = u;
+      uvs[32 + gl] = v;
+      __syncwarp();
+      for (int e = gl; e < m * m; e += G) {
+        const int r = e / m, c = e - r * m;
+        cs[r * ld + c] = dsub(dsub(cs[r * ld + c], uvs[r]), uvs[32 + c]);
+      }
+      __syncwarp();
+    }
     const double vs0 = __shfl_sync(kFull, v, gb + (s0 < 0 ? 0 : s0));
-    double dist = (cv && gl != 0) ? dsub(dsub(cs[gl * ld + s0], u), vs0) : 0.0;
+    double dist = 0.0;
+    if (cv && gl != 0) {
+      if constexpr (PRE) dist = cs[gl * ld + s0];
+      else dist = dsub(dsub(cs[gl * ld + s0], u), vs0);
+    }
     unsigned long long dk = okey(dist);
     bool done = !cv || gl == 0;
     for (int it = 0; it < M - 2; ++it) {
@@ -227,7 +248,10 @@ __device__ __forceinline__ WarpLapResult group_lap(const double* __restrict__ cs
       const int s = __shfl_sync(kFull, r2c, gb + rs);
       const double vs = __shfl_sync(kFull, v, gb + (s < 0 ? 0 : s));
       if (stepping && !done) {
-        const double nd = dadd(dr, dsub(dsub(cs[gl * ld + s], u), vs));
+        double w;
+        if constexpr (PRE) w = cs[gl * ld + s];
+        else w = dsub(dsub(cs[gl * ld + s], u), vs);
+        const double nd = dadd(dr, w);
         const unsigned long long nk = okey(nd);
         if (nk < dk) {
           dist = nd;
@@ -237,11 +261,12 @@ __device__ __forceinline__ WarpLapResult group_lap(const double* __restrict__ cs
     }
     const double u0r = __shfl_sync(kFull, u, gb);
     const double ucan = cv ? (m > 1 ? dadd(dist, dsub(u, u0r)) : 0.0) : 0.0;
+    // v_c = c_{sigma^-1(c), c} - u_{sigma^-1(c)}, from the matched row's own entry
+    const double wrow = dsub(xr, ucan);
     const int rr = cv ? c2r : 0;
-    const double ucr = __shfl_sync(kFull, ucan, gb + rr);
-    const double vcan = cv ? (m > 1 ? dsub(cs[rr * ld + gl], ucr) : cs[0]) : 0.0;
+    const double vcan = __shfl_sync(kFull, wrow, gb + rr);
     u = ucan;
-    v = vcan;
+    v = cv ? vcan : 0.0;
   }
   R.u = u;
   R.v = v;
