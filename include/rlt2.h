@@ -58,10 +58,11 @@ typedef enum {
  *  dual_mode  : 0 = the Hungarian's own duals, 1 = canonical duals (the
  *               pointwise-largest optimal row duals with u_0 = 0; unique for a
  *               given cost matrix, so warm and cold solves agree)
- *  warm       : 0 = cold Z-LAPs, 1 = start each Z-LAP from its previous
- *               iteration's row duals, 2 = start from row duals predicted by
- *               the network attached with rlt2_set_mlp (column-min repair
- *               keeps any start feasible; the bound does not depend on it)
+ *  warm       : 0 = cold LAPs, 1 = start every Z, Y and X LAP from its
+ *               previous iteration's row duals, 2 = as 1 but the Z-LAPs start
+ *               from row duals predicted by the network attached with
+ *               rlt2_set_mlp (column-min repair keeps any start feasible; with
+ *               canonical duals the bound does not depend on the start)
  *  min_gap    : stop once (UB - LB)/UB < min_gap (needs ub > 0 or a found UB)
  *  ub         : known upper bound on the node's QAP value (<= 0: unknown)
  *  feas_tol   : tolerance of the feasibility check after Algorithm 1

@@ -65,14 +65,14 @@ def lib():
         L.or_num_z.restype = ctypes.c_longlong
         L.or_setup.argtypes = [ctypes.c_int, _dp, _dp, _dp, _ip, _ip, _dp, _dp, _dp, _dp]
         L.or_stage_z.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _lp, _lp, ctypes.c_int]
-        L.or_stage_y.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _lp, _lp]
-        L.or_stage_x.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _ip, _lp, _lp]
+        L.or_stage_y.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _lp, _lp]
+        L.or_stage_x.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _ip, _lp, _lp]
         L.or_reduced_xy.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
         L.or_redistribute_z.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
         L.or_redistribute_y.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp]
         L.or_feasibility.argtypes = [ctypes.c_int, _ip, _dp, _dp, _dp, _dp, ctypes.c_double]
-        L.or_iterate.argtypes = ([ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
-                                  _dp, _dp, _dp, _dp, _ip, _dp, _dp, _lp, ctypes.c_int])
+        L.or_iterate.argtypes = ([ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                  _dp, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _lp, ctypes.c_int])
         L.or_have_openmp.restype = ctypes.c_int
         _fp = ctypes.POINTER(ctypes.c_float)
         L.or_f32_trunc.argtypes = [ctypes.c_double]
@@ -227,7 +227,7 @@ class IterOut:
 
 
 def iterate(st: State, prm: np.ndarray, dual_mode: int = 1, u0z: Optional[np.ndarray] = None,
-            threads: int = 1) -> IterOut:
+            threads: int = 1, u0y: Optional[np.ndarray] = None, u0x: Optional[np.ndarray] = None) -> IterOut:
     """One S1 iteration in place on st.Chat / st.Dhat; returns the bound and all duals
     (the bound is of the multipliers before this iteration's ascent step)."""
     n = st.n
@@ -239,7 +239,9 @@ def iterate(st: State, prm: np.ndarray, dual_mode: int = 1, u0z: Optional[np.nda
     lb = ctypes.c_double()
     prm = _f64(prm)
     u0c = None if u0z is None else _f64(u0z)
-    rc = lib().or_iterate(n, _d(prm), dual_mode, _d(st.bprime), _d(st.Chat), _d(st.Dhat), _d(u0c),
+    u0yc = None if u0y is None else _f64(u0y)
+    u0xc = None if u0x is None else _f64(u0x)
+    rc = lib().or_iterate(n, _d(prm), dual_mode, _d(st.bprime), _d(st.Chat), _d(st.Dhat), _d(u0c), _d(u0yc), _d(u0xc),
                           ctypes.byref(lb), _d(o.Theta), _d(o.xi), _d(o.psi), _d(o.Delta), _d(o.gamma),
                           _d(o.delta), _d(o.alpha), _d(o.beta), _i(o.xperm), _d(o.pix), _d(o.piy),
                           o.stats.ctypes.data_as(_lp), threads)
@@ -284,11 +286,11 @@ def run(F, D, B=None, iters=10, prm=None, dual_mode=1, partial=None, threads=1, 
     prm = params_array() if prm is None else prm
     lbs = []
     out = None
-    u0 = None
     for _ in range(iters):
-        out = iterate(st, prm, dual_mode, u0z=u0 if warm else None, threads=threads)
+        w = warm and out is not None
+        out = iterate(st, prm, dual_mode, u0z=out.xi.copy() if w else None, threads=threads,
+                      u0y=out.gamma.copy() if w else None, u0x=out.alpha.copy() if w else None)
         lbs.append(st.const + out.lb)
-        u0 = out.xi.copy()
     return st, lbs, out
 
 

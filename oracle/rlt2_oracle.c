@@ -404,8 +404,8 @@ void or_stage_z(int n, int dual_mode, const double* Dhat, const double* u0, doub
 }
 
 /* Y stage: n^2 LAPs of size n-1 with cost C^ + Theta (Figure 1, second stage). */
-void or_stage_y(int n, int dual_mode, const double* Chat, const double* Theta, double* Delta, double* gamma,
-                double* delta, long long* naug, long long* nrelax) {
+void or_stage_y(int n, int dual_mode, const double* Chat, const double* Theta, const double* u0y, double* Delta,
+                double* gamma, double* delta, long long* naug, long long* nrelax) {
   int m = n - 1;
   double* cost = (double*)malloc(sizeof(double) * m * m);
   long long aug_tot = 0, relax_tot = 0;
@@ -416,7 +416,8 @@ void or_stage_y(int n, int dual_mode, const double* Chat, const double* Theta, d
       int perm[64];
       int aug;
       long long relax;
-      solve_one(m, cost, NULL, dual_mode, &Delta[i * n + p], gamma + (i * n + p) * m, delta + (i * n + p) * m,
+      solve_one(m, cost, u0y ? u0y + (i * n + p) * m : NULL, dual_mode, &Delta[i * n + p], gamma + (i * n + p) * m,
+                delta + (i * n + p) * m,
                 perm, &aug, &relax);
       aug_tot += aug;
       relax_tot += relax;
@@ -427,13 +428,13 @@ void or_stage_y(int n, int dual_mode, const double* Chat, const double* Theta, d
 }
 
 /* X stage: one LAP of size n with cost b' + Delta; its value is the bound. */
-void or_stage_x(int n, int dual_mode, const double* bprime, const double* Delta, double* lb, double* alpha,
-                double* beta, int* xperm, long long* naug, long long* nrelax) {
+void or_stage_x(int n, int dual_mode, const double* bprime, const double* Delta, const double* u0x, double* lb,
+                double* alpha, double* beta, int* xperm, long long* naug, long long* nrelax) {
   double* cost = (double*)malloc(sizeof(double) * n * n);
   for (int e = 0; e < n * n; e++) cost[e] = bprime[e] + Delta[e];
   int aug;
   long long relax;
-  solve_one(n, cost, NULL, dual_mode, lb, alpha, beta, xperm, &aug, &relax);
+  solve_one(n, cost, u0x, dual_mode, lb, alpha, beta, xperm, &aug, &relax);
   free(cost);
   if (naug) *naug = aug;
   if (nrelax) *nrelax = relax;
@@ -593,17 +594,18 @@ int or_feasibility(int n, const int* xperm, const double* piy, const double* Dha
   return 1;
 }
 
-/* One S1 iteration (Algorithm 1 steps 3-5, then the ascent step).
+/* One S1 iteration (Algorithm 1 steps 3-5, then the ascent step).  u0z, u0y,
+ * u0x (nullable): starting row duals of the Z, Y and X LAPs (warm starts).
  * prm = {kz, ky, kx, phi_y, phi_1..phi_5}; stats[6] = {aug,relax} for Z, Y, X. */
 int or_iterate(int n, const double* prm, int dual_mode, const double* bprime, double* Chat, double* Dhat,
-               const double* u0z, double* lb, double* Theta, double* xi, double* psi, double* Delta, double* gamma,
+               const double* u0z, const double* u0y, const double* u0x, double* lb, double* Theta, double* xi, double* psi, double* Delta, double* gamma,
                double* delta, double* alpha, double* beta, int* xperm, double* pix, double* piy, long long* stats,
                int nthreads) {
   if (n < 3) return OR_EINVAL;
   long long st[6] = {0, 0, 0, 0, 0, 0};
   or_stage_z(n, dual_mode, Dhat, u0z, Theta, xi, psi, &st[0], &st[1], nthreads);
-  or_stage_y(n, dual_mode, Chat, Theta, Delta, gamma, delta, &st[2], &st[3]);
-  or_stage_x(n, dual_mode, bprime, Delta, lb, alpha, beta, xperm, &st[4], &st[5]);
+  or_stage_y(n, dual_mode, Chat, Theta, u0y, Delta, gamma, delta, &st[2], &st[3]);
+  or_stage_x(n, dual_mode, bprime, Delta, u0x, lb, alpha, beta, xperm, &st[4], &st[5]);
   or_reduced_xy(n, bprime, Delta, alpha, beta, Chat, Theta, gamma, delta, pix, piy);
   or_redistribute_z(n, prm, Dhat, xi, psi, piy, pix, nthreads);
   or_redistribute_y(n, prm[3], Chat, piy);

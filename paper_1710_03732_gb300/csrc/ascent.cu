@@ -98,7 +98,7 @@ __global__ void k_move_y(int n, long long T, double cy, double cx, double phi_y,
                (long long)gridDim.x * blockDim.x);
 }
 
-__global__ void __launch_bounds__(128) k_move_z(MoveZArgs a) {
+__global__ void __launch_bounds__(512) k_move_z(MoveZArgs a) {
   if (!a.sc->have_snap || a.sc->done) return;
   move_z_block(a, blockIdx.x);
 }
@@ -510,7 +510,8 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   // 2) z move
   const MoveZArgs mz = make_move_z(v);
   if ((e = rec(1, 0)) != cudaSuccess) return e;
-  k_move_z<<<v.ntrip * n, 128, 0, s>>>(mz);
+  // one thread per (q, r) class of the block's (triple, p): round to whole warps
+  k_move_z<<<v.ntrip * n, move_z_threads(n), 0, s>>>(mz);
   if ((e = cudaGetLastError()) != cudaSuccess || (e = rec(1, 1)) != cudaSuccess) return e;
   // 3) Z stage
   LapArgs z{};
@@ -542,6 +543,8 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   y.Badd = v.Theta;
   y.value = v.Delta;
   y.u = v.gamma;
+  y.u0 = p.warm >= 1 ? v.gamma : nullptr;  // previous iteration's row duals
+  y.warm_gate = &v.sc->have_snap;
   y.v = v.delta;
   y.pi = v.piy;
   y.dual_mode = p.dual_mode;
@@ -558,6 +561,8 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   x.Badd = v.Delta;
   x.value = v.xval;
   x.u = v.alpha;
+  x.u0 = p.warm >= 1 ? v.alpha : nullptr;
+  x.warm_gate = &v.sc->have_snap;
   x.v = v.beta;
   x.r2c = v.xperm;
   x.pi = v.pix;

@@ -45,7 +45,7 @@ __global__ void k_move_y_nodes(const MoveYNode* nodes) {
                blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
-__global__ void __launch_bounds__(128) k_move_z_nodes(const MoveZArgs* nodes, const int* nblocks) {
+__global__ void __launch_bounds__(512) k_move_z_nodes(const MoveZArgs* nodes, const int* nblocks) {
   if ((int)blockIdx.x >= nblocks[blockIdx.y]) return;
   const MoveZArgs a = nodes[blockIdx.y];
   if (!a.sc->have_snap || a.sc->done) return;
@@ -153,6 +153,7 @@ struct Wave {
   int max_m[3] = {0, 0, 0};
   int max_blocks = 0;
   int max_T = 0;
+  int max_n = 0;
 };
 
 cudaError_t enqueue_wave_iteration(const Wave& w, const WaveDev& d, int dual_mode, int zgroup, int zwpb,
@@ -163,7 +164,7 @@ cudaError_t enqueue_wave_iteration(const Wave& w, const WaveDev& d, int dual_mod
     k_move_y_nodes<<<dim3(bx, w.nn), 256, 0, s>>>(d.my);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  k_move_z_nodes<<<dim3(w.max_blocks, w.nn), 128, 0, s>>>(d.mz, d.mz_blocks);
+  k_move_z_nodes<<<dim3(w.max_blocks, w.nn), move_z_threads(w.max_n), 0, s>>>(d.mz, d.mz_blocks);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (const LearnedStart& ls : w.learned)
     if ((e = mlp_predict_enqueue(w.mlp, ls.T, ls.m, ls.Dhat, ls.xi, ls.u0, s)) != cudaSuccess) return e;
@@ -377,6 +378,7 @@ extern "C" rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D,
       y.m = nr - 1;
       y.A = v.Chat;
       y.Badd = v.Theta;
+      y.u0 = prm.warm >= 1 ? v.gamma : nullptr;
       y.warm_gate = &v.sc->have_snap;
       y.skip = &v.sc->done;
       y.value = v.Delta;
@@ -387,6 +389,7 @@ extern "C" rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D,
       x.m = nr;
       x.A = v.bprime;
       x.Badd = v.Delta;
+      x.u0 = prm.warm >= 1 ? v.alpha : nullptr;
       x.warm_gate = &v.sc->have_snap;
       x.skip = &v.sc->done;
       x.value = v.xval;
@@ -408,6 +411,7 @@ extern "C" rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D,
       fin[j] = make_fin(v);
       w.max_blocks = std::max(w.max_blocks, mzb[j]);
       w.max_T = std::max(w.max_T, (int)v.T);
+      w.max_n = std::max(w.max_n, nr);
     }
     CKN(cudaMemcpyAsync(d.items, items.data(), sizeof(NodeLapItem) * items.size(), cudaMemcpyHostToDevice, s));
     CKN(cudaMemcpyAsync(d.prefix, prefix.data(), sizeof(long long) * prefix.size(), cudaMemcpyHostToDevice, s));

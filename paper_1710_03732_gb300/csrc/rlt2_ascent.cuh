@@ -214,6 +214,14 @@ __device__ __forceinline__ void finalize_block(const FinArgs& a) {
   }
 }
 
+// Threads of a z-move block: the (n-1)(n-2) classes of one (triple, p) in
+// equal passes of at most 512 threads, rounded to whole warps.
+inline int move_z_threads(int n) {
+  const int c = (n - 1) * (n - 2);
+  const int passes = (c + 511) / 512;
+  return ((c + passes - 1) / passes + 31) / 32 * 32;
+}
+
 // Kernel arguments of one problem's z move and finalize step (host helpers).
 MoveZArgs make_move_z(const IterView& v);
 FinArgs make_fin(const IterView& v);

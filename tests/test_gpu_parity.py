@@ -384,3 +384,28 @@ def test_n30_full_size_sampled(R):
         assert abs(xi.sum() + psi.sum() - o.value) <= 1e-9 * scale * m
         assert (tile - xi[:, None] - psi[None, :]).min() >= -1e-9 * scale
         assert np.allclose(xi, o.u, atol=1e-9 * scale) and np.allclose(psi, o.v, atol=1e-9 * scale)
+
+
+@pytest.mark.parametrize("which", ["cfg1", "randB", "partial"])
+def test_warm_start_raw_bit_exact_and_canonical_equal(R, which):
+    """warm = 1 starts every Z, Y and X LAP from its previous row duals.  Raw
+    duals: the trajectory equals the oracle's warm run bit for bit.  Canonical
+    duals: the bounds equal those of the cold run (the start does not matter)."""
+    partial = None
+    if which == "cfg1":
+        inst, iters = I.config(1), 25
+    elif which == "randB":
+        inst, iters = I.random_instance(8, 12, with_b=True, asymmetric=True), 20
+    else:
+        inst, iters = I.random_instance(10, 13, with_b=True), 15
+        partial = -np.ones(10, dtype=np.int32)
+        partial[[0, 5]] = [3, 8]
+    with R.Context(inst.F, inst.D, inst.B, partial=partial, prm=_prm(R, 0, warm=1)) as ctx:
+        raw, _ = ctx.iterate(iters)
+    _, ref, _ = O.run(inst.F, inst.D, inst.B, iters=iters, dual_mode=0, partial=partial, warm=True, prm=_oprm())
+    assert np.array_equal(raw, np.array(ref))
+    out = {}
+    for warm in (0, 1):
+        with R.Context(inst.F, inst.D, inst.B, partial=partial, prm=_prm(R, 1, warm=warm)) as ctx:
+            out[warm], _ = ctx.iterate(iters)
+    assert np.max(np.abs(out[1] - out[0]) / np.maximum(1.0, np.abs(out[0]))) <= 1e-9
