@@ -223,16 +223,98 @@ def timed_device_run(R, torch, inst, warm: int, steps: int, warmup: int, barrier
 
 
 def run_profile_case(args):
-    """Minimal command for ncu: W + K iterations of the n=20 workload, warm start."""
+    """Minimal commands for ncu captures."""
     import torch
     from paper_1710_03732_gb300 import rlt2 as R
     R.lib()
+    if args.profile == "nodes":
+        inst = I.config(4)
+        lb, _, its, st = R.rlt2_bound_nodes(inst.F, inst.D, inst.partials[:16], args.warmup + args.steps,
+                                            prm=R.params(feas_tol=0.0, warm=1))
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "16 nodes of config 4", "iterations": int(its.sum()), "stats": st}))
+        return 0
     inst = I.config(CFG)
-    with R.Context(inst.F, inst.D, inst.B, prm=R.params(dual_mode=1, warm=1, feas_tol=0.0)) as ctx:
+    mlp = None
+    warm = 1
+    if args.profile == "learned":
+        mlp = R.Mlp(256)
+        mlp.load(os.path.join(ROOT, "paper_1710_03732_gb300", "weights", "warmstart_h256.npz"))
+        warm = 2
+    with R.Context(inst.F, inst.D, inst.B, prm=R.params(dual_mode=1, warm=warm, feas_tol=0.0)) as ctx:
+        if mlp is not None:
+            ctx.set_mlp(mlp)
         hist, got = ctx.iterate(args.warmup + args.steps)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": WORKLOAD, "iterations": got, "lb_last": float(hist[got - 1])}))
+    print(json.dumps({"profile_case": WORKLOAD, "warm": warm, "iterations": got, "lb_last": float(hist[got - 1])}))
     return 0
+
+
+def extra_workloads(R, torch):
+    """The other configurations, measured after the headline timed region:
+    config 4 (64 branch-and-bound nodes of a 2x11-grid QAP with n = 22, depths
+    4..8, bounded in one batched launch sequence), config 5 (n = 30, 5x6 grid)
+    and the learned warm start's augmenting searches on the n = 20 workload."""
+    out = {}
+    wpath = os.path.join(ROOT, "paper_1710_03732_gb300", "weights", "warmstart_h256.npz")
+    mlp = None
+    if os.path.exists(wpath):
+        mlp = R.Mlp(256)
+        mlp.load(wpath)
+    # config 4: batched node bounding, cold / previous duals / learned
+    inst = I.config(4)
+    iters = 30
+    c4 = {"workload": "n=22 2x11 grid, F 0..9 @0.6 (seed 3), 64 nodes at depths 4..8 (residual 14..18)",
+          "iterations_per_node": iters}
+    for warm in (0, 1, 2):
+        if warm == 2 and mlp is None:
+            continue
+        prm = R.params(feas_tol=0.0, warm=warm)
+        R.rlt2_bound_nodes(inst.F, inst.D, inst.partials[:4], 6, prm=prm, mlp=mlp)  # tuning + warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lb, _, its, st = R.rlt2_bound_nodes(inst.F, inst.D, inst.partials, iters, prm=prm, mlp=mlp)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        c4[["cold", "warm", "learned"][warm]] = {"node_iters_per_s": float(its.sum() / dt), "seconds": dt,
+                                                 "z_aug": int(st["z_aug"]), "lb_sum": float(lb.sum()),
+                                                 "z_lanes_per_lap": int(st["group"]), "z_warps_per_block": int(st["wpb"])}
+    out["config4_nodes"] = c4
+    # config 5: n = 30
+    inst = I.config(5)
+    c5 = {"workload": "n=30 5x6 grid, F 0..9 @0.5 (seed 4); 756,900 Z-LAPs of size 28, 4.75 GB z array"}
+    for warm in (0, 1, 2):
+        if warm == 2 and mlp is None:
+            continue
+        with R.Context(inst.F, inst.D, inst.B, prm=R.params(feas_tol=0.0, warm=warm)) as ctx:
+            if warm == 2:
+                ctx.set_mlp(mlp)
+            ctx.iterate(3)
+            s0 = ctx.stats()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lbs, _ = ctx.iterate(10)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            s1 = ctx.stats()
+            c5[["cold", "warm", "learned"][warm]] = {"iters_per_s": 10 / dt, "lb_after_13": float(lbs[-1]),
+                                                     "z_aug_per_lap": float((s1[1] - s0[1]) / (10 * ctx.T))}
+    out["config5_n30"] = c5
+    # learned start on the headline workload: augmenting searches, identical bounds
+    if mlp is not None:
+        inst = I.config(CFG)
+        lw = {"iterations": 20}
+        for warm in (0, 1, 2):
+            with R.Context(inst.F, inst.D, inst.B, prm=R.params(feas_tol=0.0, warm=warm)) as ctx:
+                if warm == 2:
+                    ctx.set_mlp(mlp)
+                lbs, _ = ctx.iterate(20)
+                lw[["cold", "warm", "learned"][warm]] = {"z_aug": int(ctx.stats()[1]), "lb_last": float(lbs[-1])}
+        lw["learned_saves_vs_cold"] = 1.0 - lw["learned"]["z_aug"] / lw["cold"]["z_aug"]
+        lw["warm_saves_vs_cold"] = 1.0 - lw["warm"]["z_aug"] / lw["cold"]["z_aug"]
+        out["learned_warm_start_n20"] = lw
+        mlp.close()
+    return out
 
 
 def main():
@@ -242,8 +324,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile", action="store_true",
-                    help="only run warmup+steps iterations (graph replay, warm start) for ncu captures")
+    ap.add_argument("--no-extra", action="store_true", help="skip the config 4 / config 5 / learned measurements")
+    ap.add_argument("--profile", nargs="?", const="n20", choices=["n20", "nodes", "learned"],
+                    help="only run a small case for ncu captures: n20 = warmup+steps iterations of the n=20 "
+                         "workload (graph replay, warm start); nodes = 16 nodes of the n=22 grid QAP; "
+                         "learned = n=20 with the learned warm start")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -379,6 +464,8 @@ def main():
         "gpu_kernel_ms_total": total_kernel_ms,
         "clocks": clk,
     }
+    if world == 1 and not args.no_extra:
+        line["extra"] = extra_workloads(R, torch)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
