@@ -73,6 +73,17 @@ def lib():
         L.or_feasibility.argtypes = [ctypes.c_int, _ip, _dp, _dp, _dp, _dp, ctypes.c_double]
         L.or_iterate.argtypes = ([ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
                                   _dp, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _lp, ctypes.c_int])
+        L.or_redistribute_z_v.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
+        L.or_redistribute_y_fast.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp]
+        L.or_move_x_fast.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp]
+        L.or_phase2_z.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, ctypes.c_int]
+        L.or_sa_schedule.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+        L.or_sa_term.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]
+        L.or_sa_term.restype = ctypes.c_int
+        L.or_iterate_v.argtypes = ([ctypes.c_int, _dp, _ip, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                    _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _ip, _lp,
+                                    ctypes.c_int])
         L.or_have_openmp.restype = ctypes.c_int
         _fp = ctypes.POINTER(ctypes.c_float)
         L.or_f32_trunc.argtypes = [ctypes.c_double]
@@ -280,18 +291,118 @@ def feasibility(n, xperm, piy, Dhat, xi, psi, tol=1e-9) -> bool:
                                      _d(_f64(Dhat)), _d(_f64(xi)), _d(_f64(psi)), float(tol)))
 
 
-def run(F, D, B=None, iters=10, prm=None, dual_mode=1, partial=None, threads=1, warm=False):
-    """Run the dual ascent; returns (state, list of per-iteration bounds incl. const, last IterOut)."""
+def run(F, D, B=None, iters=10, prm=None, dual_mode=1, partial=None, threads=1, warm=False, variant=0,
+        two_phase=False, sa=None, ub=None, sa_t0=0.04, sa_cool=0.99, sa_period=100, trace=None, p2tol=1e-9):
+    """Run the dual ascent; returns (state, list of per-iteration bounds incl. const, last IterOut).
+
+    variant 0 = S (slow), 1 = F (fast, incremental costs); two_phase adds the
+    second Z phase; sa = (kf[count, n], kl[count, n], neglog_u[count]) are the
+    Type 4 draws (annealing temperature sa_t0 * ub).  With warm, every LAP starts
+    from the previous iteration's row duals (and the second Z phase from the
+    first phase's).  trace (a list) receives per-iteration dicts (sa_on, stats).
+    Plain S1 runs take the original single-iteration path."""
     st = setup(F, D, B, partial)
     prm = params_array() if prm is None else prm
     lbs = []
     out = None
-    for _ in range(iters):
+    if variant == 0 and not two_phase and sa is None:
+        for _ in range(iters):
+            w = warm and out is not None
+            out = iterate(st, prm, dual_mode, u0z=out.xi.copy() if w else None, threads=threads,
+                          u0y=out.gamma.copy() if w else None, u0x=out.alpha.copy() if w else None)
+            lbs.append(st.const + out.lb)
+            if trace is not None:
+                trace.append({"sa_on": 0, "stats": out.stats.copy()})
+        return st, lbs, out
+    n = st.n
+    K = thr = None
+    if sa is not None:
+        kf, kl, ng = (_f64(a) for a in sa)
+        kf = kf.reshape(-1, n)
+        kl = kl.reshape(-1, n)
+        ng = ng.reshape(-1)
+        if ub is None or ub <= 0:
+            raise ValueError("the Type 4 rule needs a known upper bound (ub > 0)")
+        K, thr = sa_schedule(n, kf, kl, ng, ub, sa_t0, sa_cool, sa_period)
+    bx = st.bprime.copy()
+    base = st.const
+    for it in range(iters):
         w = warm and out is not None
-        out = iterate(st, prm, dual_mode, u0z=out.xi.copy() if w else None, threads=threads,
-                      u0y=out.gamma.copy() if w else None, u0x=out.alpha.copy() if w else None)
-        lbs.append(st.const + out.lb)
+        draw = None
+        if sa is not None and it < len(K):
+            draw = (K[it], thr[it], kf[it], kl[it])
+        out, lb, on = iterate_v(st, bx, prm, base, dual_mode=dual_mode, variant=variant, two_phase=two_phase,
+                                warm2=warm, u0z=out.xi.copy() if w else None,
+                                u0y=out.gamma.copy() if w else None, u0x=out.alpha.copy() if w else None,
+                                draw=draw, threads=threads, p2tol=p2tol)
+        lbs.append(lb)
+        if variant == 1:
+            base = lb
+        if trace is not None:
+            trace.append({"sa_on": on, "stats": out.stats.copy()})
     return st, lbs, out
+
+
+def iterate_v(st: State, bx: np.ndarray, prm, lb_base: float, dual_mode=1, variant=0, two_phase=False, warm2=False,
+              u0z=None, u0y=None, u0x=None, draw=None, threads=1, p2tol=1e-9):
+    """One iteration of a Section 3.4 variant in place on st.Chat, st.Dhat and bx.
+    Returns (IterOut, bound, Type 4 accepted)."""
+    n = st.n
+    T = num_tiles(n)
+    mz, my = n - 2, n - 1
+    o = IterOut(0.0, np.zeros(T), np.zeros(T * mz), np.zeros(T * mz), np.zeros(n * n), np.zeros(n * n * my),
+                np.zeros(n * n * my), np.zeros(n), np.zeros(n), np.zeros(n, dtype=np.int32), np.zeros(n * n),
+                np.zeros(T), np.zeros(6, dtype=np.int64))
+    opt = np.array([dual_mode, variant, int(bool(two_phase)), int(bool(warm2))], dtype=np.int32)
+    lb = ctypes.c_double()
+    on = ctypes.c_int()
+    dr = kf = kl = None
+    if draw is not None:
+        dr = np.array([draw[0], draw[1]], dtype=np.float64)
+        kf, kl = _f64(draw[2]), _f64(draw[3])
+    rc = lib().or_iterate_v(n, _d(_f64(prm)), _i(opt), float(p2tol), float(lb_base), _d(bx), _d(st.Chat), _d(st.Dhat),
+                            _d(None if u0z is None else _f64(u0z)), _d(None if u0y is None else _f64(u0y)),
+                            _d(None if u0x is None else _f64(u0x)), _d(dr), _d(kf), _d(kl), ctypes.byref(lb),
+                            _d(o.Theta), _d(o.xi), _d(o.psi), _d(o.Delta), _d(o.gamma), _d(o.delta), _d(o.alpha),
+                            _d(o.beta), _i(o.xperm), _d(o.pix), _d(o.piy), ctypes.byref(on),
+                            o.stats.ctypes.data_as(_lp), threads)
+    if rc != 0:
+        raise ValueError("or_iterate_v rejected the input")
+    o.lb = lb.value
+    return o, lb.value, int(on.value)
+
+
+def sa_schedule(n, kf, kl, neglog_u, ub, t0=0.04, cool=0.99, period=100):
+    """(K[d], thr[d]) of the Type 4 annealing schedule (Section 5)."""
+    kf = _f64(kf).reshape(-1, n)
+    kl = _f64(kl).reshape(-1, n)
+    ng = _f64(neglog_u).reshape(-1)
+    cnt = ng.shape[0]
+    K, thr = np.zeros(cnt), np.zeros(cnt)
+    lib().or_sa_schedule(n, cnt, float(ub), float(t0), float(cool), int(period), _d(kf), _d(kl), _d(ng), _d(K),
+                         _d(thr))
+    return K, thr
+
+
+def sa_term(n, nu, K, thr, kf, kl):
+    """Type 4 amounts per (i, p) of one draw, or None if the draw is rejected."""
+    out = np.zeros(n * n)
+    ok = lib().or_sa_term(n, float(nu), float(K), float(thr), _d(_f64(kf)), _d(_f64(kl)), _d(out))
+    return out if ok else None
+
+
+def redistribute_z_v(n, prm, Dhat, xi, psi, piy, pix, variant=0, sa=None, threads=1):
+    out = _f64(Dhat).copy()
+    lib().or_redistribute_z_v(n, _d(_f64(prm)), variant, _d(None if sa is None else _f64(sa)), _d(out),
+                              _d(_f64(xi)), _d(_f64(psi)), _d(_f64(piy)), _d(_f64(pix)), threads)
+    return out
+
+
+def phase2_z(n, Dhat, xi, psi, tol=1e-9, threads=1):
+    """Returns a new D^ after the second-phase move of the two-phase Z solve."""
+    out = _f64(Dhat).copy()
+    lib().or_phase2_z(n, float(tol), _d(out), _d(_f64(xi)), _d(_f64(psi)), threads)
+    return out
 
 
 # index helpers used by tests

@@ -41,6 +41,19 @@
  *     class's six s in member order;
  *   - an LAP optimum is summed as a pairwise tree;
  *   - y move (Eq. 2.21): C^'_ijpq = (C^_ijpq - phi_y*pi_y(ijpq)) + phi_y*pi_y(jiqp).
+ * Variants (Section 3.4):
+ *   - F: the LAPs run on the incremental costs of Psi_2 (Eq. 3.6): what is left
+ *     of each reduced cost after the step plus the inflow; the bound is the
+ *     previous bound plus the X-LAP value (Eq. 3.7).  With the y move of
+ *     Eq. 2.21 the new y cost is (1 - ky - phi_y) pi_y(ijpq) + phi_y pi_y(jiqp);
+ *   - two-phase Z solve: S_B = {pi_z <= tol (1 + |xi| + |psi|)} stands for
+ *     "zero slack" (the paper's pi(z) = 0 after rounding); the S_N slack sum is
+ *     shared as sum * (1/|S_B|);
+ *   - Type 4 rule (Section 2.3 rule 4, Section 5): the amounts per coefficient
+ *     are the printed ones (kappa_i nu / n per b, kappa_i nu / (n(n-1)(n-2)) per
+ *     z); acceptance compares kappa^lb * nu with -ln(u) * T (u <= exp(-kappa^lb
+ *     nu / T), the energy in the bound's units so that T = 4% of the upper
+ *     bound is commensurate); the random fractions and -ln(u) are inputs.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -479,8 +492,16 @@ static inline long long zidx(int n, int i, int j, int k, int p, int q, int r) {
  * Seen from the receiver a, the partners b1..b5 (same list) give it
  * phi_1, phi_2, phi_4, phi_3, phi_5 respectively (the two 3-cycles are each
  * other's inverse; the swaps are their own inverse). */
-void or_redistribute_z(int n, const double* prm, double* Dhat, const double* xi, const double* psi, const double* piy,
-                       const double* pix, int nthreads) {
+/* variant 0 (S): D^'(a) = (D^(a) - s(a)) + inflow.
+ * variant 1 (F, Section 3.4 and the constraint set Psi_2 of Eq. 3.6): the z
+ * cost is the incremental one, D^ holds the costs whose LAPs were just solved,
+ * and the new incremental cost is what remains of the slack plus the inflow:
+ * D^'(a) = fma(-kz, pi_z(a), pi_z(a)) [- sa(ip)] + inflow, i.e. (1-kz) pi_z
+ * + Omega of Eq. 3.5 (the y and x parts of the pool leave the y and x costs).
+ * sa (nullable, n*n): the Type 4 amount per (first facility, first location)
+ * (Section 2.3, rule 4), added to every pool and, in F, taken from the z cost. */
+void or_redistribute_z_v(int n, const double* prm, int variant, const double* sa, double* Dhat, const double* xi,
+                         const double* psi, const double* piy, const double* pix, int nthreads) {
   double kz = prm[0], cy = prm[1] / (double)(n - 2), cx = prm[2] / ((double)(n - 1) * (double)(n - 2));
   const double* phi = prm + 4;
   /* members of a class as position orders of the triple (i,j,k)/(p,q,r):
@@ -524,27 +545,34 @@ void or_redistribute_z(int n, const double* prm, double* Dhat, const double* xi,
         for (int r = 0; r < n; r++) {
           if (r == p || r == q) continue;
           int l3[3] = {p, q, r};
-          double s[6];
+          double s[6], base[6];
           long long idx[6];
           for (int a = 0; a < 6; a++) {
             int fi = f[M[a][0]], fj = f[M[a][1]], fk = f[M[a][2]];
             int li = l3[M[a][0]], lj = l3[M[a][1]], lk = l3[M[a][2]];
             double pz = piz_at(n, Dhat, xi, psi, fi, fj, fk, li, lj, lk);
             double ty = cy * piy[tile_of(n, fi, li, fj, lj)] + cx * pix[fi * n + li];
+            if (sa) ty = ty + sa[fi * n + li];
             s[a] = fma(kz, pz, ty);
             idx[a] = zidx(n, fi, fj, fk, li, lj, lk);
+            if (variant == 0) {
+              base[a] = Dhat[idx[a]] - s[a];
+            } else {
+              base[a] = fma(-kz, pz, pz);
+              if (sa) base[a] = base[a] - sa[fi * n + li];
+            }
           }
           double newv[6];
           if (uniform) {
             /* all phi equal: a receives phi * (sum of the other five s) */
             double S = s[0];
             for (int b = 1; b < 6; b++) S = S + s[b];
-            for (int a = 0; a < 6; a++) newv[a] = fma(phi[0], S - s[a], Dhat[idx[a]] - s[a]);
+            for (int a = 0; a < 6; a++) newv[a] = fma(phi[0], S - s[a], base[a]);
           } else {
             /* inflow from a's partners b1..b5 added in that order, one fused
-             * multiply-add each, onto D^ - s */
+             * multiply-add each, onto the member's own remainder */
             for (int a = 0; a < 6; a++) {
-              double acc = Dhat[idx[a]] - s[a];
+              double acc = base[a];
               for (int l = 0; l < 5; l++) {
                 int b = pmap[a][l];
                 acc = fma(gives[b][a], s[b], acc);
@@ -557,6 +585,11 @@ void or_redistribute_z(int n, const double* prm, double* Dhat, const double* xi,
       }
   }
   free(trip);
+}
+
+void or_redistribute_z(int n, const double* prm, double* Dhat, const double* xi, const double* psi, const double* piy,
+                       const double* pix, int nthreads) {
+  or_redistribute_z_v(n, prm, 0, NULL, Dhat, xi, psi, piy, pix, nthreads);
 }
 
 /* y redistribution (Type 1 rule for y, Eq. 2.21) in place on C^:
@@ -576,6 +609,124 @@ void or_redistribute_y(int n, double phi_y, double* Chat, const double* piy) {
     }
   memcpy(Chat, out, sizeof(double) * T);
   free(out);
+}
+
+/* F variant (Section 3.4, Psi_2 of Eq. 3.6): the new incremental y cost keeps
+ * (1 - ky - phi_y) of its own slack and receives phi_y of its mirror's:
+ * C^'_ijpq = keep*pi_y(ijpq) + phi_y*pi_y(jiqp), keep = (1 - ky) - phi_y. */
+void or_redistribute_y_fast(int n, double ky, double phi_y, double* Chat, const double* piy) {
+  long long T = or_num_tiles(n);
+  double keep = (1.0 - ky) - phi_y;
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < n; j++) {
+      if (j == i) continue;
+      for (int p = 0; p < n; p++)
+        for (int q = 0; q < n; q++) {
+          if (q == p) continue;
+          long long t = tile_of(n, i, p, j, q), tp = tile_of(n, j, q, i, p);
+          Chat[t] = keep * piy[t] + phi_y * piy[tp];
+        }
+    }
+  (void)T;
+}
+
+/* F variant: the new incremental x cost is (1 - kx) pi_x (Psi_2 of Eq. 3.6). */
+void or_move_x_fast(int n, double kx, double* bx, const double* pix) {
+  double keep = 1.0 - kx;
+  for (int e = 0; e < n * n; e++) bx[e] = keep * pix[e];
+}
+
+/* Second phase of the two-phase Z solve (Section 3.4): for every class
+ * (i<j<k, p,q,r distinct) the six members split by their slack into
+ * S_B = {pi_z <= tol (1 + |xi_k'| + |psi_r'|)} (zero slack up to the rounding of
+ * pi_z = (D^ - xi) - psi) and S_N = the others; every member of S_N drops to
+ * D^ - pi_z, and the sum of the S_N slacks (added in member order) times
+ * 1/|S_B| is added to every member of S_B.  A class with S_B or S_N empty is
+ * left as it is.  All slacks come from one snapshot. */
+void or_phase2_z(int n, double tol, double* Dhat, const double* xi, const double* psi, int nthreads) {
+  static const int M[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  static const double inv[7] = {0.0, 1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0, 1.0 / 5.0, 1.0 / 6.0};
+  int ntrip = n * (n - 1) * (n - 2) / 6;
+  int(*trip)[3] = (int(*)[3])malloc(sizeof(int[3]) * (size_t)(ntrip + 1));
+  int c = 0;
+  for (int i = 0; i < n; i++)
+    for (int j = i + 1; j < n; j++)
+      for (int k = j + 1; k < n; k++) {
+        trip[c][0] = i;
+        trip[c][1] = j;
+        trip[c][2] = k;
+        c++;
+      }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (int tr = 0; tr < ntrip; tr++) {
+    int f[3] = {trip[tr][0], trip[tr][1], trip[tr][2]};
+    for (int p = 0; p < n; p++)
+      for (int q = 0; q < n; q++) {
+        if (q == p) continue;
+        for (int r = 0; r < n; r++) {
+          if (r == p || r == q) continue;
+          int l3[3] = {p, q, r};
+          double pz[6];
+          long long idx[6];
+          int basic[6];
+          int nb = 0;
+          double sum = 0.0;
+          for (int a = 0; a < 6; a++) {
+            int fi = f[M[a][0]], fj = f[M[a][1]], fk = f[M[a][2]];
+            int li = l3[M[a][0]], lj = l3[M[a][1]], lk = l3[M[a][2]];
+            long long t = tile_of(n, fi, li, fj, lj);
+            int kk = cmp2(fk, fi, fj), rr = cmp2(lk, li, lj);
+            pz[a] = piz_at(n, Dhat, xi, psi, fi, fj, fk, li, lj, lk);
+            idx[a] = zidx(n, fi, fj, fk, li, lj, lk);
+            double lim = tol * ((1.0 + fabs(xi[t * (n - 2) + kk])) + fabs(psi[t * (n - 2) + rr]));
+            basic[a] = pz[a] <= lim;
+            if (basic[a]) nb++;
+            else sum = sum + pz[a];
+          }
+          if (nb == 0 || nb == 6) continue;
+          double share = sum * inv[nb];
+          for (int a = 0; a < 6; a++) {
+            if (basic[a]) Dhat[idx[a]] = Dhat[idx[a]] + share;
+            else Dhat[idx[a]] = Dhat[idx[a]] - pz[a];
+          }
+        }
+      }
+  }
+  free(trip);
+}
+
+/* Annealing schedule of the Type 4 rule (Section 5): temperature
+ * T_0 = t0 * ub, multiplied by `cool` before draws d = period, 2 period, ...;
+ * draw d redistributes kappa^lb = sum_i kf[d][i] + sum_p kl[d][p] (facilities
+ * first, in index order) of the bound nu when kappa^lb * nu <= e_d * T_d,
+ * e_d = -ln(u_d) for the draw's uniform u_d (i.e. u_d <= exp(-kappa^lb nu / T_d)).
+ * Outputs K[d] = kappa^lb and thr[d] = e_d * T_d. */
+void or_sa_schedule(int n, int count, double ub, double t0, double cool, int period, const double* kf,
+                    const double* kl, const double* neglog_u, double* K, double* thr) {
+  double T = t0 * ub;
+  for (int d = 0; d < count; d++) {
+    if (d > 0 && period > 0 && d % period == 0) T = T * cool;
+    double k = 0.0;
+    for (int i = 0; i < n; i++) k = k + kf[(long long)d * n + i];
+    for (int p = 0; p < n; p++) k = k + kl[(long long)d * n + p];
+    K[d] = k;
+    thr[d] = neglog_u[d] * T;
+  }
+}
+
+/* Type 4 amounts of one accepted draw (Section 2.3, rule 4): with
+ * g = nu / (n (n-1) (n-2)), every z with first facility i and first location p
+ * gives up kf[i] g + kl[p] g.  Returns 1 and fills out[n*n] when
+ * K * nu <= thr, else returns 0. */
+int or_sa_term(int n, double nu, double K, double thr, const double* kf, const double* kl, double* out) {
+  if (!(K * nu <= thr)) return 0;
+  double c4 = 1.0 / (((double)n * (double)(n - 1)) * (double)(n - 2));
+  double g = nu * c4;
+  for (int i = 0; i < n; i++)
+    for (int p = 0; p < n; p++) out[i * n + p] = kf[i] * g + kl[p] * g;
+  return 1;
 }
 
 /* Feasibility check (Section 2.3, after Algorithm 1): build y and z from the
@@ -609,6 +760,68 @@ int or_iterate(int n, const double* prm, int dual_mode, const double* bprime, do
   or_reduced_xy(n, bprime, Delta, alpha, beta, Chat, Theta, gamma, delta, pix, piy);
   or_redistribute_z(n, prm, Dhat, xi, psi, piy, pix, nthreads);
   or_redistribute_y(n, prm[3], Chat, piy);
+  if (stats) memcpy(stats, st, sizeof st);
+  return OR_OK;
+}
+
+/* One iteration of any variant of Section 3.4 (S or F; one or two phases;
+ * with or without the Type 4 rule), then its ascent step.
+ * opt = {dual_mode, variant (0 S, 1 F), two_phase, warm2}: warm2 = 1 starts the
+ * second Z solve from the first solve's row duals; p2tol is the second phase's
+ * zero-slack tolerance.
+ * lb_base: S passes the constant of the fixed facilities; F passes the
+ * previous bound (the constant before the first iteration); *lb = lb_base + the
+ * X-LAP value (for F the previous bound plus the increment, Eq. 3.7).
+ * bx: x costs (b' in S; the incremental x cost in F, updated in place).
+ * sa_draw (nullable): {K, thr} of this iteration's draw with kf, kl (n each);
+ * *sa_on reports whether the draw was accepted at the new bound. */
+int or_iterate_v(int n, const double* prm, const int* opt, double p2tol, double lb_base, double* bx, double* Chat, double* Dhat,
+                 const double* u0z, const double* u0y, const double* u0x, const double* sa_draw, const double* kf,
+                 const double* kl, double* lb, double* Theta, double* xi, double* psi, double* Delta, double* gamma,
+                 double* delta, double* alpha, double* beta, int* xperm, double* pix, double* piy, int* sa_on,
+                 long long* stats, int nthreads) {
+  if (n < 3) return OR_EINVAL;
+  int dual_mode = opt[0], variant = opt[1], two_phase = opt[2], warm2 = opt[3];
+  long long st[6] = {0, 0, 0, 0, 0, 0};
+  long long T = or_num_tiles(n);
+  int m = n - 2;
+  or_stage_z(n, dual_mode, Dhat, u0z, Theta, xi, psi, &st[0], &st[1], nthreads);
+  if (two_phase) {
+    long long a2 = 0, r2 = 0;
+    double* u1 = NULL;
+    or_phase2_z(n, p2tol, Dhat, xi, psi, nthreads);
+    if (warm2) {
+      u1 = (double*)malloc(sizeof(double) * (size_t)(T * m));
+      memcpy(u1, xi, sizeof(double) * (size_t)(T * m));
+    }
+    or_stage_z(n, dual_mode, Dhat, u1, Theta, xi, psi, &a2, &r2, nthreads);
+    free(u1);
+    st[0] += a2;
+    st[1] += r2;
+  }
+  double xv = 0.0;
+  or_stage_y(n, dual_mode, Chat, Theta, u0y, Delta, gamma, delta, &st[2], &st[3]);
+  or_stage_x(n, dual_mode, bx, Delta, u0x, &xv, alpha, beta, xperm, &st[4], &st[5]);
+  *lb = lb_base + xv;
+  or_reduced_xy(n, bx, Delta, alpha, beta, Chat, Theta, gamma, delta, pix, piy);
+  double* sa = NULL;
+  *sa_on = 0;
+  if (sa_draw) {
+    sa = (double*)malloc(sizeof(double) * n * n);
+    *sa_on = or_sa_term(n, *lb, sa_draw[0], sa_draw[1], kf, kl, sa);
+    if (!*sa_on) {
+      free(sa);
+      sa = NULL;
+    }
+  }
+  or_redistribute_z_v(n, prm, variant, sa, Dhat, xi, psi, piy, pix, nthreads);
+  if (variant == 0) {
+    or_redistribute_y(n, prm[3], Chat, piy);
+  } else {
+    or_redistribute_y_fast(n, prm[1], prm[3], Chat, piy);
+    or_move_x_fast(n, prm[2], bx, pix);
+  }
+  free(sa);
   if (stats) memcpy(stats, st, sizeof st);
   return OR_OK;
 }

@@ -155,3 +155,29 @@ def random_instance(n: int, seed: int, hi: int = 9, density: float = 0.7,
             for p in range(n):
                 B[i, p] = float(rng.below(hi + 1))
     return Instance(f"rand_n{n}_s{seed}", n, F, D, B, 10)
+
+
+def sa_draws(n: int, count: int, seed: int, kappa_max: float = 0.25):
+    """Random draws of the Type 4 (annealing) rule, passed to both sides as inputs.
+
+    Per draw d (SplitMix64, in this order): a total ``k = kappa_max * U``, then
+    2n weights ``w = U`` (facilities first, then locations), then ``u`` in
+    (0, 1] as ``((next() >> 11) + 1) * 2**-53``.  The fractions are
+    ``kf[d] = k * w[:n] / sum(w)``, ``kl[d] = k * w[n:] / sum(w)`` (their sum is
+    at most kappa_max, as Section 5 draws them) and ``neglog_u[d] = -ln(u)``.
+    Returns (kf[count, n], kl[count, n], neglog_u[count]) as float64."""
+    import math
+    rng = SplitMix64(seed)
+    kf = np.zeros((count, n))
+    kl = np.zeros((count, n))
+    ng = np.zeros(count)
+    for d in range(count):
+        k = kappa_max * rng.uniform()
+        w = np.array([rng.uniform() for _ in range(2 * n)])
+        u = ((rng.next() >> 11) + 1) * (1.0 / (1 << 53))
+        tot = float(w.sum())
+        frac = (k / tot) * w if tot > 0 else np.zeros(2 * n)
+        kf[d] = frac[:n]
+        kl[d] = frac[n:]
+        ng[d] = -math.log(u)
+    return kf, kl, ng
