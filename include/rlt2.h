@@ -72,7 +72,24 @@ typedef enum {
  *  stall_window, stall_tol : early termination of the branch-and-bound
  *               experiments (Section 5): stop once the best bound improved by
  *               less than stall_tol * |UB| over the last stall_window
- *               iterations (stall_window <= 0 disables it; at most 64) */
+ *               iterations (stall_window <= 0 disables it; at most 64)
+ *  variant    : 0 = S (slow) RLT2-DA: the LAPs are solved on the full
+ *               multiplier-adjusted costs b', C^, D^ (Section 3.4);
+ *               1 = F (fast): the LAPs are solved on the incremental costs of
+ *               the constraint set Psi_2 of Eq. 3.6 -- what remains of each
+ *               reduced cost after the ascent step, (1-kz) pi_z + inflow for
+ *               z, (1-ky-phi_y) pi_y(ijpq) + phi_y pi_y(jiqp) for y,
+ *               (1-kx) pi_x for x -- and the bound is the previous bound
+ *               plus the X-LAP value (Eq. 3.7)
+ *  two_phase  : 1 = after the Z-LAPs, move every class's z slack from its
+ *               members with pi_z > 0 (S_N) evenly onto its members with zero
+ *               slack (S_B) and solve the Z-LAPs again (Section 3.4)
+ *  phase2_tol : a z belongs to S_B when pi_z <= phase2_tol (1 + |xi| + |psi|)
+ *               (its row and column duals)
+ *  sa_t0, sa_cool, sa_period : annealing schedule of the Type 4 rule
+ *               (Section 2.3, rule 4; Section 5): temperature sa_t0 * ub,
+ *               multiplied by sa_cool every sa_period iterations; the draws
+ *               are given with rlt2_set_sa (needs ub > 0) */
 typedef struct rlt2_params {
   double kz, ky, kx, phi_y;
   double phi_z[5];
@@ -83,13 +100,20 @@ typedef struct rlt2_params {
   double feas_tol;
   int stall_window;
   double stall_tol;
+  int variant;
+  int two_phase;
+  double phase2_tol;
+  double sa_t0;
+  double sa_cool;
+  int sa_period;
 } rlt2_params;
 
 typedef struct rlt2_ctx rlt2_ctx;
 
 /* Default parameters: kz = kx = 1, ky = 1/2, phi_y = 1/2, phi_z = 1/5 each,
  * canonical duals, cold start, min_gap = 0, ub unknown, feas_tol = 1e-9,
- * no stall stop (stall_window = 0, stall_tol = 0.0002). */
+ * no stall stop (stall_window = 0, stall_tol = 0.0002), S variant, one phase,
+ * phase2_tol = 1e-9, sa_t0 = 0.04, sa_cool = 0.99, sa_period = 100 (Section 5). */
 void rlt2_params_default(rlt2_params* p);
 
 /* Create a dual-ascent context for one QAP node (Eq. 1.1; a branch-and-bound
@@ -107,7 +131,8 @@ void rlt2_params_default(rlt2_params* p);
 rlt2_status rlt2_create(int n, const double* F, const double* D, const double* B, const int* partial,
                         const rlt2_params* p, void* stream, rlt2_ctx** out);
 
-/* Run up to `iters` iterations of S1 RLT2-DA (Algorithm 1 / 2): the ascent
+/* Run up to `iters` iterations of RLT2-DA (Algorithm 1 / 2; S or F, one or two
+ * phases, as the parameters select): the ascent
  * step from the previous iteration's reduced costs (if any), then the Z, Y and
  * X LAP stages.  After return, the bound, duals, reduced costs and state all
  * belong to the same multipliers (the last solved ones).
@@ -152,6 +177,35 @@ rlt2_status rlt2_reduced_costs(rlt2_ctx* ctx, double* pi_x, double* pi_y, double
 rlt2_status rlt2_export_state(rlt2_ctx* ctx, double* Dhat, double* Chat, int on_device);
 rlt2_status rlt2_import_state(rlt2_ctx* ctx, const double* Dhat, const double* Chat, int on_device);
 
+/* The rest of an F-variant checkpoint: the incremental x costs bx (host, n*n)
+ * and the bound the next solve adds its X-LAP value to (*lb_base).  Export
+ * after an iteration returns the base of that iteration's solve, so importing
+ * D^, C^, bx and lb_base and iterating repeats that solve and continues as the
+ * uninterrupted run would.  S variant: bx is b' and lb_base the constant.
+ * Errors: EINVAL (NULL context or, on import, NULL bx / non-finite values). */
+rlt2_status rlt2_export_xstate(rlt2_ctx* ctx, double* bx, double* lb_base);
+rlt2_status rlt2_import_xstate(rlt2_ctx* ctx, const double* bx, double lb_base);
+
+/* Draws of the Type 4 rule with simulated annealing (Section 2.3, rule 4;
+ * Section 5).  Draw d belongs to the ascent step after the d-th solve
+ * (d = 0, 1, ...):
+ *  kappa_fac : host, count*n doubles (residual n), kappa^lb_i of draw d at [d*n+i]
+ *  kappa_loc : host, count*n doubles, kappa^lb_p of draw d at [d*n+p]
+ *  neglog_u  : host, count doubles, -ln(u_d) of the draw's uniform u_d in (0, 1]
+ * With kappa^lb = sum_i kappa_fac + sum_p kappa_loc (facilities first, in index
+ * order), temperature T_d = sa_t0 * ub * sa_cool^floor(d / sa_period)
+ * (one multiplication per period) and nu the bound of the d-th solve, the
+ * draw is accepted when kappa^lb * nu <= neglog_u[d] * T_d (u_d <=
+ * exp(-kappa^lb nu / T_d)); then every z with first facility i and first
+ * location p adds kappa_fac[i] g + kappa_loc[p] g, g = nu / (n (n-1) (n-2)),
+ * to the amount it gives to its symmetric partners (and, in F, takes it from
+ * its own cost).  count = 0 switches the rule off.  Copied; rebuilds the CUDA
+ * graph.  Errors: EINVAL (ub <= 0, sa_t0 <= 0, sa_cool not in (0, 1],
+ * sa_period < 1, a kappa outside [0, 1], a sum above 1, a negative or
+ * non-finite neglog_u), ENOMEM, ECUDA. */
+rlt2_status rlt2_set_sa(rlt2_ctx* ctx, int count, const double* kappa_fac, const double* kappa_loc,
+                        const double* neglog_u);
+
 /* Counters since creation, out[8] = {iterations, Z augmentations, Z relaxations,
  * Y augmentations, Y relaxations, X augmentations, X relaxations, stopped}. */
 rlt2_status rlt2_stats(rlt2_ctx* ctx, long long* out);
@@ -163,7 +217,8 @@ rlt2_status rlt2_sizes(rlt2_ctx* ctx, int* n_res, long long* T, long long* E, do
 /* Per-kernel timing with CUDA events on the context's stream (disables CUDA
  * graph replay while on).  rlt2_kernel_times fills ms[k] (total milliseconds)
  * and count[k] (launches) for k = 0..nk-1 in the order
- * {move_y, move_z, lap_z, lap_y, lap_x, finalize}; synchronises. */
+ * {move_y, move_z, lap_z, lap_y, lap_x, finalize, phase2_move, lap_z2}
+ * (the last two are empty intervals without two_phase); synchronises. */
 rlt2_status rlt2_set_timing(rlt2_ctx* ctx, int on);
 rlt2_status rlt2_kernel_times(rlt2_ctx* ctx, double* ms, long long* count, int nk);
 

@@ -34,7 +34,7 @@ rlt2_status cuda_fail(cudaError_t e, const char* what) {
   return RLT2_ECUDA;
 }
 
-constexpr int kKinds = 6;
+constexpr int kKinds = 8;
 
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
@@ -90,17 +90,21 @@ __global__ void k_setup_c(int nr, long long T, const double* Fr, const double* D
 // ------------------------------------------------------------------ moves ----
 static const int h_widx[5] = {0, 1, 3, 2, 4};
 
-__global__ void k_move_y(int n, long long T, double cy, double cx, double phi_y, const double* __restrict__ piy,
-                         const double* __restrict__ pix, double* __restrict__ Chat, double* __restrict__ tterm,
-                         const DevScalars* sc) {
-  if (!sc->have_snap || sc->done) return;
-  move_y_range(n, T, cy, cx, phi_y, piy, pix, Chat, tterm, blockIdx.x * (long long)blockDim.x + threadIdx.x,
-               (long long)gridDim.x * blockDim.x);
+__global__ void k_move_y(MoveYArgs a) {
+  if (!a.sc->have_snap || a.sc->done) return;
+  move_y_range(a, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
 __global__ void __launch_bounds__(512) k_move_z(MoveZArgs a) {
   if (!a.sc->have_snap || a.sc->done) return;
   move_z_block(a, blockIdx.x);
+}
+
+// Second phase of the two-phase Z solve; runs on every iteration (the first
+// phase's duals are always fresh).
+__global__ void __launch_bounds__(512) k_phase2(Phase2Args a) {
+  if (a.sc->done) return;
+  phase2_block(a, blockIdx.x);
 }
 
 // pi_z = (D^ - xi_k') - psi_r' for every z entry (reduced costs on demand).
@@ -153,14 +157,18 @@ struct rlt2_ctx {
   double *Theta = nullptr, *xi = nullptr, *psi = nullptr, *Delta = nullptr, *gamma = nullptr, *delta = nullptr;
   double *alpha = nullptr, *beta = nullptr, *pix = nullptr, *piy = nullptr, *tterm = nullptr, *xval = nullptr;
   double* ring = nullptr;
+  double* xcost = nullptr;   // F variant: own buffer; S variant: aliases bprime
+  double* saterm = nullptr;
+  double* sa_buf = nullptr;  // Type 4 draws: kf[count*n] | kl[count*n] | K[count] | thr[count]
+  int sa_count = 0;
   int *xperm = nullptr, *ubperm = nullptr, *trips = nullptr;
   int ntrip = 0;
   DevScalars* sc = nullptr;
   cudaGraphExec_t graph = nullptr;
   bool timing = false;
   std::vector<cudaEvent_t> ev;  // timing mode: 2 events per kernel launch
-  double kms[kKinds] = {0, 0, 0, 0, 0, 0};
-  long long kcount[kKinds] = {0, 0, 0, 0, 0, 0};
+  double kms[kKinds] = {};
+  long long kcount[kKinds] = {};
   int iter_host = 0;
   double cst_host = 0.0;
   rlt2_mlp* mlp = nullptr;
@@ -176,6 +184,9 @@ static void ctx_free(rlt2_ctx* c) {
                   c->tterm, c->xval,  c->ring, c->xperm,  c->ubperm, c->trips, c->sc};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (c->xcost && c->xcost != c->bprime) cudaFree(c->xcost);
+  if (c->saterm) cudaFree(c->saterm);
+  if (c->sa_buf) cudaFree(c->sa_buf);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->u0buf) cudaFree(c->u0buf);
   delete c;
@@ -214,6 +225,16 @@ static IterView view_of(const rlt2_ctx* c) {
   v.ubperm = c->ubperm;
   v.trips = c->trips;
   v.sc = c->sc;
+  v.xcost = c->xcost;
+  v.saterm = c->saterm;
+  v.sa_count = c->sa_count;
+  if (c->sa_count > 0) {
+    const long long cn = (long long)c->sa_count * c->n;
+    v.sa_kf = c->sa_buf;
+    v.sa_kl = c->sa_buf + cn;
+    v.sa_K = c->sa_buf + 2 * cn;
+    v.sa_thr = c->sa_buf + 2 * cn + c->sa_count;
+  }
   return v;
 }
 
@@ -237,6 +258,12 @@ extern "C" void rlt2_params_default(rlt2_params* p) {
   p->feas_tol = 1e-9;
   p->stall_window = 0;
   p->stall_tol = 0.0002;
+  p->variant = 0;
+  p->two_phase = 0;
+  p->phase2_tol = 1e-9;
+  p->sa_t0 = 0.04;
+  p->sa_cool = 0.99;
+  p->sa_period = 100;
 }
 
 bool rlt2::params_valid(const rlt2_params& p) {
@@ -253,6 +280,10 @@ bool rlt2::params_valid(const rlt2_params& p) {
   if (p.warm < 0 || p.warm > 2) return false;
   if (!std::isfinite(p.min_gap) || !std::isfinite(p.ub) || !std::isfinite(p.feas_tol)) return false;
   if (p.stall_window < 0 || p.stall_window >= kStallRing || !std::isfinite(p.stall_tol)) return false;
+  if (p.variant != 0 && p.variant != 1) return false;
+  if (p.two_phase != 0 && p.two_phase != 1) return false;
+  if (!std::isfinite(p.phase2_tol) || p.phase2_tol < 0.0) return false;
+  if (!std::isfinite(p.sa_t0) || !std::isfinite(p.sa_cool) || p.sa_period < 1) return false;
   return true;
 }
 
@@ -377,7 +408,10 @@ extern "C" rlt2_status rlt2_create(int n, const double* F, const double* D, cons
   AL(c->ubperm, nr);
   AL(c->trips, c->ntrip);
   AL(c->sc, 1);
+  AL(c->saterm, n2);
+  if (prm.variant == 1) AL(c->xcost, n2);
 #undef AL
+  if (!c->xcost) c->xcost = c->bprime;  // S variant: the X-LAP reads b' itself
   if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return fail(e, "cudaStreamCreate");
 
@@ -429,6 +463,10 @@ extern "C" rlt2_status rlt2_create(int n, const double* F, const double* D, cons
   const int* dfixl = dint + 2 * nr + nfix;
   e = enqueue_setup(view_of(c), n, dF, dD, dB, dfac, dloc, dfixf, dfixl, nfix, s);
   if (e == cudaSuccess) e = cudaGetLastError();
+  // F variant: the first solve runs on b' and its bound starts from the constant
+  if (e == cudaSuccess && c->xcost != c->bprime)
+    e = cudaMemcpyAsync(c->xcost, c->bprime, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&c->sc->lb_base, c->d_cst, sizeof(double), cudaMemcpyDeviceToDevice, s);
   cudaError_t e3 = cudaStreamSynchronize(s);
   cleanup_tmp();
   if (e != cudaSuccess) return fail(e, "setup kernels");
@@ -438,6 +476,47 @@ extern "C" rlt2_status rlt2_create(int n, const double* F, const double* D, cons
     if ((e = prepare_lap(mm2)) != cudaSuccess) return fail(e, "prepare_lap");
   *out = c;
   return RLT2_OK;
+}
+
+MoveYArgs rlt2::make_move_y(const IterView& v) {
+  const rlt2_params& p = v.prm;
+  const int n = v.n;
+  MoveYArgs a{};
+  a.n = n;
+  a.T = v.T;
+  a.cy = p.ky / (double)(n - 2);
+  a.cx = p.kx / ((double)(n - 1) * (double)(n - 2));
+  a.phi_y = p.phi_y;
+  a.fast = p.variant == 1;
+  a.keep_y = (1.0 - p.ky) - p.phi_y;
+  a.keep_x = 1.0 - p.kx;
+  a.piy = v.piy;
+  a.pix = v.pix;
+  a.Chat = v.Chat;
+  a.tterm = v.tterm;
+  a.xcost = v.xcost;
+  a.saterm = v.saterm;
+  a.sa_kf = v.sa_kf;
+  a.sa_kl = v.sa_kl;
+  a.sa_K = v.sa_K;
+  a.sa_thr = v.sa_thr;
+  a.sa_count = v.sa_count;
+  a.c4 = 1.0 / (((double)n * (double)(n - 1)) * (double)(n - 2));
+  a.sc = v.sc;
+  return a;
+}
+
+Phase2Args rlt2::make_phase2(const IterView& v) {
+  Phase2Args a{};
+  a.n = v.n;
+  a.m = v.m;
+  a.tol = v.prm.phase2_tol;
+  a.Dhat = v.Dhat;
+  a.xi = v.xi;
+  a.psi = v.psi;
+  a.trips = v.trips;
+  a.sc = v.sc;
+  return a;
 }
 
 MoveZArgs rlt2::make_move_z(const IterView& v) {
@@ -450,6 +529,8 @@ MoveZArgs rlt2::make_move_z(const IterView& v) {
   mz.kz_one = (p.kz == 1.0);
   mz.uniform = (p.phi_z[0] == p.phi_z[1] && p.phi_z[0] == p.phi_z[2] && p.phi_z[0] == p.phi_z[3] &&
                 p.phi_z[0] == p.phi_z[4]);
+  mz.fast = p.variant == 1;
+  mz.saterm = v.saterm;
   mz.Dhat = v.Dhat;
   mz.xi = v.xi;
   mz.psi = v.psi;
@@ -481,6 +562,7 @@ FinArgs rlt2::make_fin(const IterView& v) {
   f.feas_tol = p.feas_tol;
   f.stall_window = p.stall_window;
   f.stall_tol = p.stall_tol;
+  f.fast = p.variant == 1;
   f.sc = v.sc;
   return f;
 }
@@ -497,14 +579,11 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
     if (!ev) return cudaSuccess;
     return cudaEventRecord(ev[2 * k + which], s);
   };
-  // 1) y move + tile terms
-  const double cy = p.ky / (double)(n - 2);
-  const double cx = p.kx / ((double)(n - 1) * (double)(n - 2));
+  // 1) y move (and F's x move) + tile terms
   if ((e = rec(0, 0)) != cudaSuccess) return e;
   {
     const long long blocks = (T + 255) / 256;
-    k_move_y<<<(int)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(n, T, cy, cx, p.phi_y, v.piy, v.pix, v.Chat,
-                                                                    v.tterm, v.sc);
+    k_move_y<<<(int)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(make_move_y(v));
   }
   if ((e = cudaGetLastError()) != cudaSuccess || (e = rec(0, 1)) != cudaSuccess) return e;
   // 2) z move
@@ -535,6 +614,20 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   if ((e = rec(2, 0)) != cudaSuccess) return e;
   if ((e = launch_lap(z, s)) != cudaSuccess) return e;
   if ((e = rec(2, 1)) != cudaSuccess) return e;
+  // 3b) two-phase Z solve: move slack onto the zero-slack members, solve again
+  if ((e = rec(6, 0)) != cudaSuccess) return e;
+  if (p.two_phase) {
+    k_phase2<<<v.ntrip * n, move_z_threads(n), 0, s>>>(make_phase2(v));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if ((e = rec(6, 1)) != cudaSuccess || (e = rec(7, 0)) != cudaSuccess) return e;
+  if (p.two_phase) {
+    LapArgs z2 = z;
+    z2.u0 = p.warm >= 1 ? v.xi : nullptr;  // from the first phase's row duals
+    z2.warm_gate = nullptr;
+    if ((e = launch_lap(z2, s)) != cudaSuccess) return e;
+  }
+  if ((e = rec(7, 1)) != cudaSuccess) return e;
   // 4) Y stage on C^ + Theta, writes pi_y
   LapArgs y{};
   y.batch = (long long)n * n;
@@ -557,7 +650,7 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   LapArgs x{};
   x.batch = 1;
   x.m = n;
-  x.A = v.bprime;
+  x.A = v.xcost;
   x.Badd = v.Delta;
   x.value = v.xval;
   x.u = v.alpha;
@@ -619,7 +712,8 @@ static rlt2_status enqueue_many(rlt2_ctx* c, int iters) {
         cudaError_t e = enqueue_iteration_ctx(c, c->stream, it * kKinds * 2);
         if (e != cudaSuccess) return cuda_fail(e, "enqueue_iteration");
       }
-      CK(cudaEventSynchronize(c->ev[(cnt - 1) * kKinds * 2 + 2 * (kKinds - 1) + 1]));
+      // finalize (kind 5) is the last interval recorded in an iteration
+      CK(cudaEventSynchronize(c->ev[(cnt - 1) * kKinds * 2 + 2 * 5 + 1]));
       for (int it = 0; it < cnt; ++it)
         for (int k = 0; k < kKinds; ++k) {
           float ms = 0.f;
@@ -774,6 +868,108 @@ extern "C" rlt2_status rlt2_import_state(rlt2_ctx* c, const double* Dhat, const 
   CK(cudaMemcpyAsync(&c->sc->have_snap, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(&c->sc->done, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_export_xstate(rlt2_ctx* c, double* bx, double* lb_base) {
+  if (!c) return RLT2_EINVAL;
+  const size_t n2 = (size_t)c->n * c->n;
+  if (bx) CK(cudaMemcpyAsync(bx, c->xcost, sizeof(double) * n2, cudaMemcpyDeviceToHost, c->stream));
+  DevScalars h;
+  CK(cudaMemcpyAsync(&h, c->sc, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (lb_base) *lb_base = (c->prm.variant == 1) ? h.lb_base : c->cst_host;
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_import_xstate(rlt2_ctx* c, const double* bx, double lb_base) {
+  if (!c || !bx || !std::isfinite(lb_base)) {
+    set_error("rlt2_import_xstate: invalid argument");
+    return RLT2_EINVAL;
+  }
+  const size_t n2 = (size_t)c->n * c->n;
+  if (!finite_all(bx, n2)) {
+    set_error("rlt2_import_xstate: non-finite x costs");
+    return RLT2_EINVAL;
+  }
+  if (c->prm.variant != 1) return RLT2_OK;  // S: b' and the constant never change
+  CK(cudaMemcpyAsync(c->xcost, bx, sizeof(double) * n2, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(&c->sc->lb_base, &lb_base, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  const int zero = 0;
+  CK(cudaMemcpyAsync(&c->sc->have_snap, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_set_sa(rlt2_ctx* c, int count, const double* kf, const double* kl,
+                                   const double* neglog_u) {
+  if (!c || count < 0) {
+    set_error("rlt2_set_sa: invalid argument");
+    return RLT2_EINVAL;
+  }
+  const int n = c->n;
+  const rlt2_params& p = c->prm;
+  if (count > 0) {
+    if (!kf || !kl || !neglog_u) {
+      set_error("rlt2_set_sa: NULL draws");
+      return RLT2_EINVAL;
+    }
+    if (!(p.ub > 0.0) || !(p.sa_t0 > 0.0) || !(p.sa_cool > 0.0 && p.sa_cool <= 1.0) || p.sa_period < 1) {
+      set_error("rlt2_set_sa: needs ub > 0, sa_t0 > 0, 0 < sa_cool <= 1, sa_period >= 1");
+      return RLT2_EINVAL;
+    }
+  }
+  // host side of the schedule: K[d] (facilities first, index order) and
+  // thr[d] = neglog_u[d] * T_d, T_0 = sa_t0 * ub, times sa_cool every sa_period draws
+  const long long cn = (long long)count * n;
+  std::vector<double> buf((size_t)(2 * cn + 2 * (long long)count));
+  double temp = p.sa_t0 * p.ub;
+  for (int d = 0; d < count; ++d) {
+    if (d > 0 && d % p.sa_period == 0) temp = temp * p.sa_cool;
+    double k = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double x = kf[(long long)d * n + i];
+      if (!std::isfinite(x) || x < 0.0 || x > 1.0) {
+        set_error("rlt2_set_sa: kappa outside [0, 1]");
+        return RLT2_EINVAL;
+      }
+      buf[(size_t)((long long)d * n + i)] = x;
+      k = k + x;
+    }
+    for (int q = 0; q < n; ++q) {
+      const double x = kl[(long long)d * n + q];
+      if (!std::isfinite(x) || x < 0.0 || x > 1.0) {
+        set_error("rlt2_set_sa: kappa outside [0, 1]");
+        return RLT2_EINVAL;
+      }
+      buf[(size_t)(cn + (long long)d * n + q)] = x;
+      k = k + x;
+    }
+    if (k > 1.0 || !std::isfinite(neglog_u[d]) || neglog_u[d] < 0.0) {
+      set_error("rlt2_set_sa: kappa sum above 1 or bad -ln(u)");
+      return RLT2_EINVAL;
+    }
+    buf[(size_t)(2 * cn + d)] = k;
+    buf[(size_t)(2 * cn + count + d)] = neglog_u[d] * temp;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->sa_buf) {
+    cudaFree(c->sa_buf);
+    c->sa_buf = nullptr;
+  }
+  c->sa_count = 0;
+  if (count > 0) {
+    cudaError_t e = cudaMalloc((void**)&c->sa_buf, sizeof(double) * buf.size());
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? (cuda_fail(e, "cudaMalloc"), RLT2_ENOMEM)
+                                                                 : cuda_fail(e, "cudaMalloc");
+    CK(cudaMemcpy(c->sa_buf, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice));
+    c->sa_count = count;
+  }
+  // the graph holds the old arguments
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
   return RLT2_OK;
 }
 

@@ -80,6 +80,8 @@ __global__ void k_noalloc_init(int n, int* fac, int* loc, int* trips, int ntrip,
     sc->done = 0;
     sc->have_snap = 0;
     sc->reason = 0;
+    sc->sa_on = 0;
+    sc->lb_base = 0.0;  // set to the constant after setup
     for (int k = 0; k < 6; ++k) sc->stats[k] = 0;
   }
 }
@@ -149,6 +151,8 @@ extern "C" rlt2_status rlt2_iterate_noalloc(int n, const double* F, const double
   v.Fr = cv.take<double>(n2);
   v.Dr = cv.take<double>(n2);
   v.bprime = cv.take<double>(n2);
+  v.xcost = cv.take<double>(n2);
+  v.saterm = cv.take<double>(n2);
   v.Delta = cv.take<double>(n2);
   v.pix = cv.take<double>(n2);
   v.gamma = cv.take<double>(n2 * (n - 1));
@@ -177,6 +181,9 @@ extern "C" rlt2_status rlt2_iterate_noalloc(int n, const double* F, const double
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "rlt2_iterate_noalloc: init");
   if ((e = enqueue_setup(v, n, F, D, B, fac, loc, nullptr, nullptr, 0, s)) != cudaSuccess)
     return cuda_fail(e, "rlt2_iterate_noalloc: setup");
+  if ((e = cudaMemcpyAsync(v.xcost, v.bprime, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&v.sc->lb_base, v.d_cst, sizeof(double), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return cuda_fail(e, "rlt2_iterate_noalloc: x costs");
   for (int mm : {n - 2, n - 1, n})
     if ((e = prepare_lap(mm)) != cudaSuccess) return cuda_fail(e, "rlt2_iterate_noalloc: prepare");
   for (int it = 0; it < iters; ++it)

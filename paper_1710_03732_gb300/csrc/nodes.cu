@@ -27,22 +27,10 @@
 namespace rlt2 {
 namespace {
 
-struct MoveYNode {
-  int n;
-  long long T;
-  double cy, cx, phi_y;
-  const double* piy;
-  const double* pix;
-  double* Chat;
-  double* tterm;
-  const DevScalars* sc;
-};
-
-__global__ void k_move_y_nodes(const MoveYNode* nodes) {
-  const MoveYNode a = nodes[blockIdx.y];
+__global__ void k_move_y_nodes(const MoveYArgs* nodes) {
+  const MoveYArgs a = nodes[blockIdx.y];
   if (!a.sc->have_snap || a.sc->done) return;
-  move_y_range(a.n, a.T, a.cy, a.cx, a.phi_y, a.piy, a.pix, a.Chat, a.tterm,
-               blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+  move_y_range(a, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
 __global__ void __launch_bounds__(512) k_move_z_nodes(const MoveZArgs* nodes, const int* nblocks) {
@@ -50,6 +38,13 @@ __global__ void __launch_bounds__(512) k_move_z_nodes(const MoveZArgs* nodes, co
   const MoveZArgs a = nodes[blockIdx.y];
   if (!a.sc->have_snap || a.sc->done) return;
   move_z_block(a, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(512) k_phase2_nodes(const Phase2Args* nodes, const int* nblocks) {
+  if ((int)blockIdx.x >= nblocks[blockIdx.y]) return;
+  const Phase2Args a = nodes[blockIdx.y];
+  if (a.sc->done) return;
+  phase2_block(a, blockIdx.x);
 }
 
 __global__ void __launch_bounds__(256) k_finalize_nodes(const FinArgs* nodes) {
@@ -101,6 +96,7 @@ void carve(NodeHost& h, char* base, const rlt2_params& prm) {
   v.Fr = ar.take<double>(n2);
   v.Dr = ar.take<double>(n2);
   v.bprime = ar.take<double>(n2);
+  v.xcost = ar.take<double>(n2);
   v.Delta = ar.take<double>(n2);
   v.pix = ar.take<double>(n2);
   v.gamma = ar.take<double>(n2 * (n - 1));
@@ -126,14 +122,18 @@ std::mutex g_tune_mu;
 std::map<int, Tuned> g_tuned;  // largest Z-LAP size of a wave -> Z-stage launch shape
 
 // Device-side descriptors of one wave.
+// LAP stages of a wave: Z, Y, X and the second Z phase.
+constexpr int kStages = 4;
+
 struct WaveDev {
-  NodeLapItem* items = nullptr;  // [3][kMaxWaveNodes]
-  long long* prefix = nullptr;   // [3][kMaxWaveNodes + 1]
-  MoveYNode* my = nullptr;
+  NodeLapItem* items = nullptr;  // [kStages][kMaxWaveNodes]
+  long long* prefix = nullptr;   // [kStages][kMaxWaveNodes + 1]
+  MoveYArgs* my = nullptr;
   MoveZArgs* mz = nullptr;
+  Phase2Args* p2 = nullptr;
   int* mz_blocks = nullptr;
   FinArgs* fin = nullptr;
-  unsigned long long* heads = nullptr;  // [3]
+  unsigned long long* heads = nullptr;  // [kStages]
   unsigned long long* stats = nullptr;  // [6]
 };
 
@@ -149,8 +149,9 @@ struct Wave {
   rlt2_mlp* mlp = nullptr;
   std::vector<LearnedStart> learned;  // one per node when warm == 2
   int nn = 0;
-  long long total[3] = {0, 0, 0};
-  int max_m[3] = {0, 0, 0};
+  int two_phase = 0;
+  long long total[kStages] = {0, 0, 0, 0};
+  int max_m[kStages] = {0, 0, 0, 0};
   int max_blocks = 0;
   int max_T = 0;
   int max_n = 0;
@@ -168,8 +169,16 @@ cudaError_t enqueue_wave_iteration(const Wave& w, const WaveDev& d, int dual_mod
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   for (const LearnedStart& ls : w.learned)
     if ((e = mlp_predict_enqueue(w.mlp, ls.T, ls.m, ls.Dhat, ls.xi, ls.u0, s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(d.heads, 0, 3 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
-  for (int stage = 0; stage < 3; ++stage) {
+  if ((e = cudaMemsetAsync(d.heads, 0, kStages * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+  // Z, [second phase move, Z again], Y, X
+  const int order[kStages] = {0, 3, 1, 2};
+  for (int oi = 0; oi < kStages; ++oi) {
+    const int stage = order[oi];
+    if (stage == 3) {
+      if (!w.two_phase) continue;
+      k_phase2_nodes<<<dim3(w.max_blocks, w.nn), move_z_threads(w.max_n), 0, s>>>(d.p2, d.mz_blocks);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     NodeLapArgs a{};
     a.nnodes = w.nn;
     a.items = d.items + stage * kMaxWaveNodes;
@@ -178,10 +187,10 @@ cudaError_t enqueue_wave_iteration(const Wave& w, const WaveDev& d, int dual_mod
     a.max_m = w.max_m[stage];
     a.dual_mode = dual_mode;
     a.head = d.heads + stage;
-    a.stats = d.stats + 2 * stage;
-    a.group = stage == 0 ? zgroup : 0;
-    a.warps_per_block = stage == 0 ? zwpb : 0;
-    a.pre = stage == 0;  // the Z stage writes no reduced costs
+    a.stats = d.stats + 2 * (stage == 3 ? 0 : stage);
+    a.group = (stage == 0 || stage == 3) ? zgroup : 0;
+    a.warps_per_block = (stage == 0 || stage == 3) ? zwpb : 0;
+    a.pre = stage == 0 || stage == 3;  // the Z stages write no reduced costs
     if (stage == 0 && zev0 && (e = cudaEventRecord(zev0, s)) != cudaSuccess) return e;
     if ((e = launch_lap_nodes(a, s)) != cudaSuccess) return e;
     if (stage == 0 && zev1 && (e = cudaEventRecord(zev1, s)) != cudaSuccess) return e;
@@ -309,13 +318,14 @@ extern "C" rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D,
   CKN(cudaMalloc((void**)&dF, nn2 * 8));
   CKN(cudaMalloc((void**)&dD, nn2 * 8));
   if (B) CKN(cudaMalloc((void**)&dB, nn2 * 8));
-  CKN(cudaMalloc((void**)&d.items, sizeof(NodeLapItem) * 3 * kMaxWaveNodes));
-  CKN(cudaMalloc((void**)&d.prefix, sizeof(long long) * 3 * (kMaxWaveNodes + 1)));
-  CKN(cudaMalloc((void**)&d.my, sizeof(MoveYNode) * kMaxWaveNodes));
+  CKN(cudaMalloc((void**)&d.items, sizeof(NodeLapItem) * kStages * kMaxWaveNodes));
+  CKN(cudaMalloc((void**)&d.prefix, sizeof(long long) * kStages * (kMaxWaveNodes + 1)));
+  CKN(cudaMalloc((void**)&d.my, sizeof(MoveYArgs) * kMaxWaveNodes));
   CKN(cudaMalloc((void**)&d.mz, sizeof(MoveZArgs) * kMaxWaveNodes));
+  CKN(cudaMalloc((void**)&d.p2, sizeof(Phase2Args) * kMaxWaveNodes));
   CKN(cudaMalloc((void**)&d.mz_blocks, sizeof(int) * kMaxWaveNodes));
   CKN(cudaMalloc((void**)&d.fin, sizeof(FinArgs) * kMaxWaveNodes));
-  CKN(cudaMalloc((void**)&d.heads, sizeof(unsigned long long) * 3));
+  CKN(cudaMalloc((void**)&d.heads, sizeof(unsigned long long) * kStages));
   CKN(cudaMalloc((void**)&d.stats, sizeof(unsigned long long) * 6));
   CKN(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   CKN(cudaEventCreate(&zev0));
@@ -331,10 +341,12 @@ extern "C" rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D,
     w.mlp = prm.warm == 2 ? mlp : nullptr;
     // carve the arenas and upload each node's index lists
     char* cur = pool;
-    std::vector<NodeLapItem> items(3 * kMaxWaveNodes);
-    std::vector<long long> prefix(3 * (kMaxWaveNodes + 1), 0);
-    std::vector<MoveYNode> my(w.nn);
+    w.two_phase = prm.two_phase;
+    std::vector<NodeLapItem> items(kStages * kMaxWaveNodes);
+    std::vector<long long> prefix(kStages * (kMaxWaveNodes + 1), 0);
+    std::vector<MoveYArgs> my(w.nn);
     std::vector<MoveZArgs> mz(w.nn);
+    std::vector<Phase2Args> p2(w.nn);
     std::vector<int> mzb(w.nn);
     std::vector<FinArgs> fin(w.nn);
     std::vector<DevScalars> init(1);
@@ -361,9 +373,12 @@ extern "C" rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D,
       const int nfix = (int)h.fixf.size();
       CKN(enqueue_setup(v, n, dF, dD, dB, h.dfac, h.dfac + h.nr, h.dfac + 2 * h.nr, h.dfac + 2 * h.nr + nfix, nfix,
                         s));
+      // X-LAP costs start as b' (the F variant then updates them); F's bound starts at the constant
+      CKN(cudaMemcpyAsync(v.xcost, v.bprime, sizeof(double) * h.nr * h.nr, cudaMemcpyDeviceToDevice, s));
+      CKN(cudaMemcpyAsync(&v.sc->lb_base, v.d_cst, sizeof(double), cudaMemcpyDeviceToDevice, s));
       // stage descriptors
       const int nr = h.nr;
-      NodeLapItem z{}, y{}, x{};
+      NodeLapItem z{}, y{}, x{}, z2{};
       z.count = v.T;
       z.m = nr - 2;
       z.A = v.Dhat;
@@ -387,7 +402,7 @@ extern "C" rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D,
       y.pi = v.piy;
       x.count = 1;
       x.m = nr;
-      x.A = v.bprime;
+      x.A = v.xcost;
       x.Badd = v.Delta;
       x.u0 = prm.warm >= 1 ? v.alpha : nullptr;
       x.warm_gate = &v.sc->have_snap;
@@ -397,16 +412,19 @@ extern "C" rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D,
       x.v = v.beta;
       x.r2c = v.xperm;
       x.pi = v.pix;
-      const NodeLapItem st3[3] = {z, y, x};
-      for (int sg = 0; sg < 3; ++sg) {
+      z2 = z;
+      z2.u0 = prm.warm >= 1 ? v.xi : nullptr;  // second phase: from the first phase's row duals
+      z2.warm_gate = nullptr;
+      const NodeLapItem st3[kStages] = {z, y, x, z2};
+      for (int sg = 0; sg < kStages; ++sg) {
         items[sg * kMaxWaveNodes + j] = st3[sg];
         prefix[sg * (kMaxWaveNodes + 1) + j + 1] = prefix[sg * (kMaxWaveNodes + 1) + j] + st3[sg].count;
         w.total[sg] += st3[sg].count;
         w.max_m[sg] = std::max(w.max_m[sg], st3[sg].m);
       }
-      my[j] = MoveYNode{nr, v.T, prm.ky / (double)(nr - 2), prm.kx / ((double)(nr - 1) * (double)(nr - 2)),
-                        prm.phi_y, v.piy, v.pix, v.Chat, v.tterm, v.sc};
+      my[j] = make_move_y(v);
       mz[j] = make_move_z(v);
+      p2[j] = make_phase2(v);
       mzb[j] = v.ntrip * nr;
       fin[j] = make_fin(v);
       w.max_blocks = std::max(w.max_blocks, mzb[j]);
@@ -415,8 +433,9 @@ extern "C" rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D,
     }
     CKN(cudaMemcpyAsync(d.items, items.data(), sizeof(NodeLapItem) * items.size(), cudaMemcpyHostToDevice, s));
     CKN(cudaMemcpyAsync(d.prefix, prefix.data(), sizeof(long long) * prefix.size(), cudaMemcpyHostToDevice, s));
-    CKN(cudaMemcpyAsync(d.my, my.data(), sizeof(MoveYNode) * w.nn, cudaMemcpyHostToDevice, s));
+    CKN(cudaMemcpyAsync(d.my, my.data(), sizeof(MoveYArgs) * w.nn, cudaMemcpyHostToDevice, s));
     CKN(cudaMemcpyAsync(d.mz, mz.data(), sizeof(MoveZArgs) * w.nn, cudaMemcpyHostToDevice, s));
+    CKN(cudaMemcpyAsync(d.p2, p2.data(), sizeof(Phase2Args) * w.nn, cudaMemcpyHostToDevice, s));
     CKN(cudaMemcpyAsync(d.mz_blocks, mzb.data(), sizeof(int) * w.nn, cudaMemcpyHostToDevice, s));
     CKN(cudaMemcpyAsync(d.fin, fin.data(), sizeof(FinArgs) * w.nn, cudaMemcpyHostToDevice, s));
     CKN(cudaStreamSynchronize(s));  // host vectors above must outlive the copies
@@ -522,7 +541,7 @@ done:
   if (zev1) cudaEventDestroy(zev1);
   if (cap) cudaStreamDestroy(cap);
   cudaStreamSynchronize(s);
-  void* frees[] = {pool, dF, dD, dB, d.items, d.prefix, d.my, d.mz, d.mz_blocks, d.fin, d.heads, d.stats};
+  void* frees[] = {pool, dF, dD, dB, d.items, d.prefix, d.my, d.mz, d.p2, d.mz_blocks, d.fin, d.heads, d.stats};
   for (void* q : frees)
     if (q) cudaFree(q);
   return st;

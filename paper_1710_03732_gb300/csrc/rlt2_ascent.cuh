@@ -13,24 +13,80 @@ __device__ __forceinline__ double dadd_(double a, double b) { return __dadd_rn(a
 __device__ __forceinline__ double dsub_(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double dmul_(double a, double b) { return __dmul_rn(a, b); }
 
+// 64-bit key that orders like the double (non-NaN; -0 == +0), for compares off the FP64 pipe.
+__device__ __forceinline__ unsigned long long okey_(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  b = (b == 0x8000000000000000ull) ? 0ull : b;
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
 // ------------------------------------------------------------------ moves ----
-// Per tile (i,p,j,q): the pending y move of Eq. 2.21 on C^ and the term
-// cy*pi_y(ijpq) + cx*pi_x(ip) that rules 2 and 3 add to each z of the tile.
-__device__ __forceinline__ void move_y_range(int n, long long T, double cy, double cx, double phi_y,
-                                             const double* __restrict__ piy, const double* __restrict__ pix,
-                                             double* __restrict__ Chat, double* __restrict__ tterm, long long start,
-                                             long long stride) {
-  const int n1 = n - 1;
-  for (long long t = start; t < T; t += stride) {
+struct MoveYArgs {
+  int n;
+  long long T;
+  double cy, cx, phi_y;
+  int fast;              // F variant: new incremental y and x costs from the slacks
+  double keep_y, keep_x;  // (1 - ky) - phi_y and 1 - kx (F variant)
+  const double* piy;
+  const double* pix;
+  double* Chat;
+  double* tterm;
+  double* xcost;   // F: written with keep_x * pi_x
+  double* saterm;  // n*n Type 4 amounts of an accepted draw
+  const double *sa_kf, *sa_kl, *sa_K, *sa_thr;
+  int sa_count;
+  double c4;  // 1 / (n (n-1) (n-2))
+  DevScalars* sc;
+};
+
+// Per tile (i,p,j,q): the pending y move on C^ (S: Eq. 2.21 on the full cost;
+// F: keep_y pi_y(ijpq) + phi_y pi_y(jiqp)), the term cy*pi_y(ijpq) + cx*pi_x(ip)
+// that rules 2 and 3 add to each z pool of the tile, plus the Type 4 amount
+// kf_i g + kl_p g of an accepted draw (rule 4, Section 5: accepted when
+// kappa^lb * nu <= -ln(u) T).  Thread 0 records the draw's acceptance and, in
+// F, makes the last bound the base of the next one (Eq. 3.7).
+__device__ __forceinline__ void move_y_range(const MoveYArgs& a, long long start, long long stride) {
+  const int n = a.n, n1 = n - 1;
+  bool on = false;
+  double g = 0.0;
+  const double* kf = nullptr;
+  const double* kl = nullptr;
+  if (a.sa_count > 0) {
+    const int d = a.sc->iter - 1;
+    if (d >= 0 && d < a.sa_count) {
+      const double nu = a.sc->lb;
+      if (dmul_(a.sa_K[d], nu) <= a.sa_thr[d]) {
+        on = true;
+        g = dmul_(nu, a.c4);
+        kf = a.sa_kf + (long long)d * n;
+        kl = a.sa_kl + (long long)d * n;
+      }
+    }
+  }
+  for (long long t = start; t < a.T; t += stride) {
     const int ip = (int)(t / (n1 * n1));
     const int rem = (int)(t - (long long)ip * n1 * n1);
     const int jj = rem / n1, qq = rem - jj * n1;
     const int i = ip / n, p = ip - i * n;
     const int j = jj + (jj >= i), q = qq + (qq >= p);
     const long long tp = ((long long)(j * n + q) * n1 + (i - (i > j))) * n1 + (p - (p > q));
-    const double py = piy[t];
-    tterm[t] = dadd_(dmul_(cy, py), dmul_(cx, pix[ip]));
-    Chat[t] = dadd_(dsub_(Chat[t], dmul_(phi_y, py)), dmul_(phi_y, piy[tp]));
+    const double py = a.piy[t];
+    double ty = dadd_(dmul_(a.cy, py), dmul_(a.cx, a.pix[ip]));
+    if (on) ty = dadd_(ty, dadd_(dmul_(kf[i], g), dmul_(kl[p], g)));
+    a.tterm[t] = ty;
+    if (a.fast)
+      a.Chat[t] = dadd_(dmul_(a.keep_y, py), dmul_(a.phi_y, a.piy[tp]));
+    else
+      a.Chat[t] = dadd_(dsub_(a.Chat[t], dmul_(a.phi_y, py)), dmul_(a.phi_y, a.piy[tp]));
+    if (t < (long long)n * n) {
+      const int xi_ = (int)t / n, xp = (int)t - xi_ * n;
+      if (a.fast) a.xcost[t] = dmul_(a.keep_x, a.pix[t]);
+      if (on) a.saterm[t] = dadd_(dmul_(kf[xi_], g), dmul_(kl[xp], g));
+    }
+  }
+  if (start == 0) {
+    a.sc->sa_on = on ? 1 : 0;
+    if (a.fast) a.sc->lb_base = a.sc->lb;
   }
 }
 
@@ -52,7 +108,9 @@ struct MoveZArgs {
   double kz;
   double w[5];  // weight received from partner l (phi permuted by h_widx)
   int kz_one;   // kz == 1: kz*x == x exactly, skip the product
-  int uniform;  // all phi equal: member b gets phi * (class sum - s_b)
+  int uniform;  // all phi equal: member b gets phi * (S - s_b)
+  int fast;     // F variant: the member keeps fma(-kz, pi_z, pi_z) (minus a Type 4 amount)
+  const double* saterm;  // n*n Type 4 amounts (F variant, when sc->sa_on)
   double* Dhat;
   const double* xi;
   const double* psi;
@@ -74,6 +132,7 @@ __device__ __forceinline__ void move_z_block(const MoveZArgs& a, int blk) {
   const int F3[3] = {packed & 255, (packed >> 8) & 255, packed >> 16};
   const int npairs = n1 * m;
   const long long mm = (long long)m * m;
+  const bool sa = a.fast && a.sc->sa_on;
   for (int c = threadIdx.x; c < npairs; c += blockDim.x) {
     const int qq = c / m, rr = c - qq * m;
     const int q = qq + (qq >= p);
@@ -82,7 +141,7 @@ __device__ __forceinline__ void move_z_block(const MoveZArgs& a, int blk) {
     r += (r >= lo);
     r += (r >= hi);
     const int L3[3] = {p, q, r};
-    double s[6], Dv[6];
+    double s[6], base[6];
     long long idx[6];
 #pragma unroll
     for (int b = 0; b < 6; ++b) {
@@ -91,10 +150,17 @@ __device__ __forceinline__ void move_z_block(const MoveZArgs& a, int blk) {
       const long long t = ((long long)(f0 * n + l0) * n1 + (f1 - (f1 > f0))) * n1 + (l1 - (l1 > l0));
       const int kr = f2 - (f2 > f0) - (f2 > f1), cc = l2 - (l2 > l0) - (l2 > l1);
       idx[b] = t * mm + kr * m + cc;
-      Dv[b] = a.Dhat[idx[b]];
-      const double pz = dsub_(dsub_(Dv[b], __ldg(a.xi + t * m + kr)), __ldg(a.psi + t * m + cc));
+      const double Dv = a.Dhat[idx[b]];
+      const double pz = dsub_(dsub_(Dv, __ldg(a.xi + t * m + kr)), __ldg(a.psi + t * m + cc));
       // s = kz*pi_z + tile term in one rounding (kz = 1: an exact fma(1, x, y) is x + y)
       s[b] = a.kz_one ? dadd_(pz, __ldg(a.tterm + t)) : __fma_rn(a.kz, pz, __ldg(a.tterm + t));
+      if (!a.fast) {
+        base[b] = dsub_(Dv, s[b]);
+      } else {
+        // (1 - kz) pi_z in one rounding; fma(-1, x, x) is +0 exactly
+        base[b] = a.kz_one ? 0.0 : __fma_rn(-a.kz, pz, pz);
+        if (sa) base[b] = dsub_(base[b], __ldg(a.saterm + f0 * n + l0));
+      }
     }
     if (a.uniform) {
       // all phi equal: member b receives phi * (S - s_b), S the class sum in member order
@@ -102,17 +168,81 @@ __device__ __forceinline__ void move_z_block(const MoveZArgs& a, int blk) {
 #pragma unroll
       for (int b = 1; b < 6; ++b) S = dadd_(S, s[b]);
 #pragma unroll
-      for (int b = 0; b < 6; ++b) a.Dhat[idx[b]] = __fma_rn(a.w[0], dsub_(S, s[b]), dsub_(Dv[b], s[b]));
+      for (int b = 0; b < 6; ++b) a.Dhat[idx[b]] = __fma_rn(a.w[0], dsub_(S, s[b]), base[b]);
     } else {
       // partner inflows one fused multiply-add at a time, partners in Eq. 2.20 order
 #pragma unroll
       for (int b = 0; b < 6; ++b) {
-        double acc = dsub_(Dv[b], s[b]);
+        double acc = base[b];
 #pragma unroll
         for (int l = 0; l < 5; ++l) acc = __fma_rn(a.w[l], s[kPart[b][l]], acc);
         a.Dhat[idx[b]] = acc;
       }
     }
+  }
+}
+
+// Second phase of the two-phase Z solve (Section 3.4), class-owned like the z
+// move: members with pi_z above tol (1 + |xi| + |psi|) (S_N) drop to D^ - pi_z,
+// and the sum of their slacks (member order) times 1/|S_B| goes to each
+// member with zero slack (S_B); classes with S_B or S_N empty stay as they are.
+struct Phase2Args {
+  int n, m;
+  double tol;
+  double* Dhat;
+  const double* xi;
+  const double* psi;
+  const int* trips;
+  const DevScalars* sc;
+};
+
+__device__ __forceinline__ void phase2_block(const Phase2Args& a, int blk) {
+  RLT2_CLASS_TABLES
+  (void)kPart;
+  const int n = a.n, m = a.m, n1 = n - 1;
+  const int tr = blk / n, p = blk - tr * n;
+  const int packed = a.trips[tr];
+  const int F3[3] = {packed & 255, (packed >> 8) & 255, packed >> 16};
+  const int npairs = n1 * m;
+  const long long mm = (long long)m * m;
+  for (int c = threadIdx.x; c < npairs; c += blockDim.x) {
+    const int qq = c / m, rr = c - qq * m;
+    const int q = qq + (qq >= p);
+    const int lo = p < q ? p : q, hi = p < q ? q : p;
+    int r = rr;
+    r += (r >= lo);
+    r += (r >= hi);
+    const int L3[3] = {p, q, r};
+    double pz[6], Dv[6];
+    long long idx[6];
+    int nb = 0;
+    unsigned basic = 0;
+    double sum = 0.0;
+#pragma unroll
+    for (int b = 0; b < 6; ++b) {
+      const int f0 = F3[kOrd[b][0]], f1 = F3[kOrd[b][1]], f2 = F3[kOrd[b][2]];
+      const int l0 = L3[kOrd[b][0]], l1 = L3[kOrd[b][1]], l2 = L3[kOrd[b][2]];
+      const long long t = ((long long)(f0 * n + l0) * n1 + (f1 - (f1 > f0))) * n1 + (l1 - (l1 > l0));
+      const int kr = f2 - (f2 > f0) - (f2 > f1), cc = l2 - (l2 > l0) - (l2 > l1);
+      idx[b] = t * mm + kr * m + cc;
+      Dv[b] = a.Dhat[idx[b]];
+      const double xv = __ldg(a.xi + t * m + kr), pv = __ldg(a.psi + t * m + cc);
+      pz[b] = dsub_(dsub_(Dv[b], xv), pv);
+      const double lim = dmul_(a.tol, dadd_(dadd_(1.0, fabs(xv)), fabs(pv)));
+      if (okey_(pz[b]) <= okey_(lim)) {
+        basic |= 1u << b;
+        ++nb;
+      } else {
+        sum = dadd_(sum, pz[b]);
+      }
+    }
+    if (nb == 0 || nb == 6) continue;
+    // 1/|S_B| as a correctly rounded constant, as in 1.0 / k
+    const double inv = nb == 1 ? 1.0 : nb == 2 ? 0.5 : nb == 3 ? 1.0 / 3.0 : nb == 4 ? 0.25 : 0.2;
+    const double share = dmul_(sum, inv);
+#pragma unroll
+    for (int b = 0; b < 6; ++b)
+      a.Dhat[idx[b]] = ((basic >> b) & 1u) ? dadd_(Dv[b], share) : dsub_(Dv[b], pz[b]);
   }
 }
 
@@ -133,6 +263,7 @@ struct FinArgs {
   double* ring;
   double min_gap, ub_known, feas_tol, stall_tol;
   int stall_window;
+  int fast;  // F variant: bound = previous bound + X-LAP value (Eq. 3.7)
   DevScalars* sc;
 };
 
@@ -141,7 +272,7 @@ __device__ __forceinline__ void finalize_block(const FinArgs& a) {
   __shared__ double red[256];
   __shared__ int bad, improve;
   const int n = a.n, m = a.m, n1 = n - 1, tid = threadIdx.x;
-  const double lb = dadd_(*a.cst, a.xval[0]);
+  const double lb = dadd_(a.fast ? a.sc->lb_base : *a.cst, a.xval[0]);
   if (tid == 0) bad = (a.feas_tol > 0.0) ? 0 : 1;
   // residual QAP value of the X-LAP primal (an upper bound)
   double part = 0.0;
@@ -222,8 +353,10 @@ inline int move_z_threads(int n) {
   return ((c + passes - 1) / passes + 31) / 32 * 32;
 }
 
-// Kernel arguments of one problem's z move and finalize step (host helpers).
+// Kernel arguments of one problem's moves and finalize step (host helpers).
+MoveYArgs make_move_y(const IterView& v);
 MoveZArgs make_move_z(const IterView& v);
+Phase2Args make_phase2(const IterView& v);
 FinArgs make_fin(const IterView& v);
 
 }  // namespace rlt2

@@ -79,7 +79,9 @@ constexpr int kRing = 1 << 16;  // bound-history ring (entries)
 constexpr int kStallRing = 64;  // best-bound history for the stall rule
 struct DevScalars {
   double lb, best_lb, ub, gap;
+  double lb_base;  // F variant: the bound the next X-LAP value is added to
   int iter, done, have_snap, reason;
+  int sa_on;       // the pending ascent step applies a Type 4 draw
   unsigned long long stats[6];  // Z aug, Z relax, Y aug, Y relax, X aug, X relax
   double best_hist[kStallRing];  // best bound after iteration it, at it % kStallRing
 };
@@ -94,6 +96,10 @@ struct IterView {
   rlt2_params prm;
   double *d_cst, *Fr, *Dr, *bprime, *Chat, *Dhat, *Theta, *xi, *psi, *Delta, *gamma, *delta;
   double *alpha, *beta, *pix, *piy, *tterm, *xval, *ring;
+  double* xcost;   // X-LAP costs: b' (S variant, may alias bprime) or the incremental x costs (F)
+  double* saterm;  // n*n Type 4 amount per (first facility, first location) of the pending step
+  const double *sa_kf, *sa_kl, *sa_K, *sa_thr;  // Type 4 draws (count*n, count*n, count, count)
+  int sa_count;
   int *xperm, *ubperm, *trips;
   DevScalars* sc;
 };

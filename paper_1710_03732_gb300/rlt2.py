@@ -24,7 +24,9 @@ class rlt2_params(ctypes.Structure):
     _fields_ = [("kz", ctypes.c_double), ("ky", ctypes.c_double), ("kx", ctypes.c_double),
                 ("phi_y", ctypes.c_double), ("phi_z", ctypes.c_double * 5), ("dual_mode", ctypes.c_int),
                 ("warm", ctypes.c_int), ("min_gap", ctypes.c_double), ("ub", ctypes.c_double),
-                ("feas_tol", ctypes.c_double), ("stall_window", ctypes.c_int), ("stall_tol", ctypes.c_double)]
+                ("feas_tol", ctypes.c_double), ("stall_window", ctypes.c_int), ("stall_tol", ctypes.c_double),
+                ("variant", ctypes.c_int), ("two_phase", ctypes.c_int), ("phase2_tol", ctypes.c_double),
+                ("sa_t0", ctypes.c_double), ("sa_cool", ctypes.c_double), ("sa_period", ctypes.c_int)]
 
 
 class Rlt2Error(RuntimeError):
@@ -44,7 +46,7 @@ EXPORTS = ["rlt2_params_default", "rlt2_create", "rlt2_iterate", "rlt2_iterate_a
            "rlt2_iterate_noalloc", "rlt2_mlp_create", "rlt2_mlp_destroy", "rlt2_mlp_get_weights",
            "rlt2_mlp_set_weights", "rlt2_mlp_add_samples", "rlt2_mlp_samples", "rlt2_mlp_clear_samples",
            "rlt2_mlp_grad", "rlt2_mlp_fit", "rlt2_mlp_set_gate", "rlt2_mlp_predict", "rlt2_set_mlp",
-           "rlt2_strerror", "rlt2_last_error"]
+           "rlt2_export_xstate", "rlt2_import_xstate", "rlt2_set_sa", "rlt2_strerror", "rlt2_last_error"]
 
 
 def lib():
@@ -66,6 +68,9 @@ def lib():
     L.rlt2_reduced_costs.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int]
     L.rlt2_export_state.argtypes = [_vp, _vp, _vp, ctypes.c_int]
     L.rlt2_import_state.argtypes = [_vp, _vp, _vp, ctypes.c_int]
+    L.rlt2_export_xstate.argtypes = [_vp, _dp, _dp]
+    L.rlt2_import_xstate.argtypes = [_vp, _dp, ctypes.c_double]
+    L.rlt2_set_sa.argtypes = [_vp, ctypes.c_int, _dp, _dp, _dp]
     L.rlt2_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
     L.rlt2_sizes.argtypes = [_vp, _ip, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), _dp]
     L.rlt2_set_timing.argtypes = [_vp, ctypes.c_int]
@@ -132,7 +137,9 @@ def _stream(stream) -> Optional[int]:
 
 
 def params(kz=1.0, ky=0.5, kx=1.0, phi_y=0.5, phi_z=(0.2,) * 5, dual_mode=1, warm=0, min_gap=0.0, ub=0.0,
-           feas_tol=1e-9, stall_window=0, stall_tol=0.0002) -> rlt2_params:
+           feas_tol=1e-9, stall_window=0, stall_tol=0.0002, variant=0, two_phase=0, phase2_tol=1e-9, sa_t0=0.04,
+           sa_cool=0.99, sa_period=100) -> rlt2_params:
+    """Parameters (variant 0 = S, 1 = F; two_phase; annealing schedule of the Type 4 rule)."""
     p = rlt2_params()
     lib().rlt2_params_default(ctypes.byref(p))
     p.kz, p.ky, p.kx, p.phi_y = kz, ky, kx, phi_y
@@ -140,6 +147,8 @@ def params(kz=1.0, ky=0.5, kx=1.0, phi_y=0.5, phi_z=(0.2,) * 5, dual_mode=1, war
         p.phi_z[i] = x
     p.dual_mode, p.warm, p.min_gap, p.ub, p.feas_tol = dual_mode, warm, min_gap, ub, feas_tol
     p.stall_window, p.stall_tol = stall_window, stall_tol
+    p.variant, p.two_phase, p.phase2_tol = int(variant), int(two_phase), phase2_tol
+    p.sa_t0, p.sa_cool, p.sa_period = sa_t0, sa_cool, int(sa_period)
     return p
 
 
@@ -213,14 +222,36 @@ def rlt2_set_timing(ctx: int, on: bool):
     _check(lib().rlt2_set_timing(ctx, int(bool(on))), "rlt2_set_timing")
 
 
-KERNEL_KINDS = ["move_y", "move_z", "lap_z", "lap_y", "lap_x", "finalize"]
+KERNEL_KINDS = ["move_y", "move_z", "lap_z", "lap_y", "lap_x", "finalize", "phase2_move", "lap_z2"]
 
 
 def rlt2_kernel_times(ctx: int):
-    ms = (ctypes.c_double * 6)()
-    cnt = (ctypes.c_longlong * 6)()
-    _check(lib().rlt2_kernel_times(ctx, ms, cnt, 6), "rlt2_kernel_times")
+    k = len(KERNEL_KINDS)
+    ms = (ctypes.c_double * k)()
+    cnt = (ctypes.c_longlong * k)()
+    _check(lib().rlt2_kernel_times(ctx, ms, cnt, k), "rlt2_kernel_times")
     return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def rlt2_export_xstate(ctx: int, n: int):
+    bx = np.empty(n * n)
+    base = ctypes.c_double()
+    _check(lib().rlt2_export_xstate(ctx, _host_d(bx), ctypes.byref(base)), "rlt2_export_xstate")
+    return bx, base.value
+
+
+def rlt2_import_xstate(ctx: int, bx, lb_base: float):
+    bx = np.ascontiguousarray(bx, dtype=np.float64)
+    _check(lib().rlt2_import_xstate(ctx, _host_d(bx), float(lb_base)), "rlt2_import_xstate")
+
+
+def rlt2_set_sa(ctx: int, kappa_fac, kappa_loc, neglog_u):
+    kf = np.ascontiguousarray(kappa_fac, dtype=np.float64).reshape(-1)
+    kl = np.ascontiguousarray(kappa_loc, dtype=np.float64).reshape(-1)
+    ng = np.ascontiguousarray(neglog_u, dtype=np.float64).reshape(-1)
+    count = int(ng.shape[0])
+    _check(lib().rlt2_set_sa(ctx, count, _host_d(kf) if count else None, _host_d(kl) if count else None,
+                             _host_d(ng) if count else None), "rlt2_set_sa")
 
 
 def rlt2_destroy(ctx: int):
@@ -396,6 +427,17 @@ class Context:
     def import_state(self, Dhat, Chat):
         rlt2_import_state(self.ctx, np.ascontiguousarray(Dhat, dtype=np.float64),
                           np.ascontiguousarray(Chat, dtype=np.float64))
+
+    def export_xstate(self):
+        """(incremental x costs, bound base) of an F-variant checkpoint."""
+        return rlt2_export_xstate(self.ctx, self.n)
+
+    def import_xstate(self, bx, lb_base):
+        rlt2_import_xstate(self.ctx, bx, lb_base)
+
+    def set_sa(self, kappa_fac, kappa_loc, neglog_u):
+        """Type 4 draws (count x n, count x n, count); count = 0 switches the rule off."""
+        rlt2_set_sa(self.ctx, kappa_fac, kappa_loc, neglog_u)
 
     def stats(self):
         return rlt2_stats(self.ctx)
