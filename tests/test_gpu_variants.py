@@ -178,7 +178,7 @@ def test_type4_needs_upper_bound(R):
             ctx.set_sa(kf, kl, ng)
     with R.Context(inst.F, inst.D, inst.B, prm=R.params(ub=100.0)) as ctx:
         with pytest.raises(R.Rlt2Error):
-            ctx.set_sa(kf * 10, kl, ng)  # a fraction above 1
+            ctx.set_sa(kf + 1.5, kl, ng)  # fractions above 1
         ctx.set_sa(kf, kl, ng)
         ctx.iterate(3)
         ctx.set_sa(np.zeros((0, inst.n)), np.zeros((0, inst.n)), np.zeros(0))  # off again
