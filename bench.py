@@ -250,6 +250,38 @@ def run_profile_case(args):
     return 0
 
 
+def variant_runs(R, torch, iters: int = 300):
+    """S1 / F1 / S2 / F2, each with and without the Type 4 rule (annealing at
+    4 % of the best upper bound the S1 run found, cooled by 0.99 every 100
+    iterations, draws from instances.sa_draws seed 5): iterations per second over
+    the whole run from the first solve, best and last bound, Z augmenting
+    searches per iteration (canonical duals, previous-iteration warm starts; the
+    time includes the one-time CUDA-graph capture)."""
+    inst = I.config(CFG)
+    res = {"workload": WORKLOAD, "iterations": iters}
+    kf, kl, ng = I.sa_draws(inst.n, iters, 5)
+    ub = None
+    for name, variant, two_phase, sa in [("S1", 0, 0, False), ("F1", 1, 0, False), ("S2", 0, 1, False),
+                                         ("F2", 1, 1, False), ("S1+SA", 0, 0, True), ("F1+SA", 1, 0, True),
+                                         ("S2+SA", 0, 1, True), ("F2+SA", 1, 1, True)]:
+        prm = R.params(feas_tol=0.0, warm=1, variant=variant, two_phase=two_phase, ub=ub if sa else 0.0)
+        with R.Context(inst.F, inst.D, inst.B, prm=prm) as ctx:
+            if sa:
+                ctx.set_sa(kf, kl, ng)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            lbs, done = ctx.iterate(iters)
+            dt = time.perf_counter() - t0
+            _, best, ubf, _, _, _ = ctx.bound()
+            st = ctx.stats()
+        if name == "S1":
+            ub = float(ubf)
+            res["ub_for_annealing"] = ub
+        res[name] = {"iters_per_s": done / dt, "best_lb": float(best), "lb_last": float(lbs[done - 1]),
+                     "z_aug_per_iter": float(st[1]) / done, "drops": int(np.sum(np.diff(lbs[:done]) < 0))}
+    return res
+
+
 def extra_workloads(R, torch):
     """The other configurations, measured after the headline timed region:
     config 4 (64 branch-and-bound nodes of a 2x11-grid QAP with n = 22, depths
@@ -300,6 +332,8 @@ def extra_workloads(R, torch):
             c5[["cold", "warm", "learned"][warm]] = {"iters_per_s": 10 / dt, "lb_after_13": float(lbs[-1]),
                                                      "z_aug_per_lap": float((s1[1] - s0[1]) / (10 * ctx.T))}
     out["config5_n30"] = c5
+    # Section 3.4 variants on the headline workload: speed and bound reached
+    out["variants_n20"] = variant_runs(R, torch)
     # learned start on the headline workload: augmenting searches, identical bounds
     if mlp is not None:
         inst = I.config(CFG)
