@@ -279,6 +279,22 @@ def variant_runs(R, torch, iters: int = 300):
             res["ub_for_annealing"] = ub
         res[name] = {"iters_per_s": done / dt, "best_lb": float(best), "lb_last": float(lbs[done - 1]),
                      "z_aug_per_iter": float(st[1]) / done, "drops": int(np.sum(np.diff(lbs[:done]) < 0))}
+    # half-Z-LAP scheme (Section 5): 72,200 of the 144,400 Z-LAPs per iteration
+    with R.Context(inst.F, inst.D, inst.B, prm=R.half_z_params(feas_tol=0.0, warm=1)) as ctx:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lbs, done = ctx.iterate(iters)
+        dt = time.perf_counter() - t0
+        _, best, _, _, _, _ = ctx.bound()
+        st = ctx.stats()
+        ctx.set_timing(True)
+        ctx.iterate(20)
+        kt = ctx.kernel_times()
+    res["S1 half-Z"] = {"iters_per_s": done / dt, "best_lb": float(best), "lb_last": float(lbs[done - 1]),
+                        "z_aug_per_iter": float(st[1]) / done, "drops": int(np.sum(np.diff(lbs[:done]) < 0)),
+                        "z_laps_per_iter": ctx.T // 2,
+                        "lap_z_ms": kt["lap_z"][0] / max(1, kt["lap_z"][1]),
+                        "move_z_ms": kt["move_z"][0] / max(1, kt["move_z"][1])}
     return res
 
 

@@ -89,7 +89,19 @@ typedef enum {
  *  sa_t0, sa_cool, sa_period : annealing schedule of the Type 4 rule
  *               (Section 2.3, rule 4; Section 5): temperature sa_t0 * ub,
  *               multiplied by sa_cool every sa_period iterations; the draws
- *               are given with rlt2_set_sa (needs ub > 0) */
+ *               are given with rlt2_set_sa (needs ub > 0)
+ *  half_z     : 1 = the half-Z-LAP scheme of Section 5 (after Goncalves et
+ *               al.): the z whose first facility index exceeds the second
+ *               ("lower order") keep cost 0, so their Z-LAPs (i > j) are not
+ *               solved.  The y move of Eq. 2.21 runs with phi_y (1/2 in the
+ *               paper) on every y; each of the three upper members of a class
+ *               then pools kz (2/3) of its z slack, ky (1) of its tile's y
+ *               slack as left by the y move and the Type 3 part of pi_x (kx = 1),
+ *               and gives half of the pool to each other upper member; a lower
+ *               y (i > j) passes kx pi_x(ip)/(n-1) to its mirror on the y level.
+ *               S variant, one phase, no Type 4 rule; phi_z ignored; the
+ *               phi_y + ky <= 1 limit does not apply (each y's slack is
+ *               first split by the y move, then pushed into z). */
 typedef struct rlt2_params {
   double kz, ky, kx, phi_y;
   double phi_z[5];
@@ -106,6 +118,7 @@ typedef struct rlt2_params {
   double sa_t0;
   double sa_cool;
   int sa_period;
+  int half_z;
 } rlt2_params;
 
 typedef struct rlt2_ctx rlt2_ctx;

@@ -84,6 +84,10 @@ def lib():
         L.or_iterate_v.argtypes = ([ctypes.c_int, _dp, _ip, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
                                     _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _ip, _lp,
                                     ctypes.c_int])
+        L.or_stage_z_upper.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _lp, _lp]
+        L.or_redistribute_half.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.or_iterate_half.argtypes = ([ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                       _dp, _dp, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _lp])
         L.or_have_openmp.restype = ctypes.c_int
         _fp = ctypes.POINTER(ctypes.c_float)
         L.or_f32_trunc.argtypes = [ctypes.c_double]
@@ -370,6 +374,41 @@ def iterate_v(st: State, bx: np.ndarray, prm, lb_base: float, dual_mode=1, varia
         raise ValueError("or_iterate_v rejected the input")
     o.lb = lb.value
     return o, lb.value, int(on.value)
+
+
+HALF_PRM = (2.0 / 3.0, 1.0, 1.0, 0.5)  # kz, ky, kx, phi_y of the half-Z scheme (Section 5)
+
+
+def iterate_half(st: State, prm=HALF_PRM, dual_mode: int = 1, u0z=None, u0y=None, u0x=None) -> IterOut:
+    """One iteration of the half-Z scheme in place on st.Chat / st.Dhat."""
+    n = st.n
+    T = num_tiles(n)
+    mz, my = n - 2, n - 1
+    o = IterOut(0.0, np.zeros(T), np.zeros(T * mz), np.zeros(T * mz), np.zeros(n * n), np.zeros(n * n * my),
+                np.zeros(n * n * my), np.zeros(n), np.zeros(n), np.zeros(n, dtype=np.int32), np.zeros(n * n),
+                np.zeros(T), np.zeros(6, dtype=np.int64))
+    lb = ctypes.c_double()
+    rc = lib().or_iterate_half(n, _d(_f64(prm)), dual_mode, _d(st.bprime), _d(st.Chat), _d(st.Dhat),
+                               _d(None if u0z is None else _f64(u0z)), _d(None if u0y is None else _f64(u0y)),
+                               _d(None if u0x is None else _f64(u0x)), ctypes.byref(lb), _d(o.Theta), _d(o.xi),
+                               _d(o.psi), _d(o.Delta), _d(o.gamma), _d(o.delta), _d(o.alpha), _d(o.beta),
+                               _i(o.xperm), _d(o.pix), _d(o.piy), o.stats.ctypes.data_as(_lp))
+    if rc != 0:
+        raise ValueError("or_iterate_half rejected the input")
+    o.lb = lb.value
+    return o
+
+
+def run_half(F, D, B=None, iters=10, prm=HALF_PRM, dual_mode=1, partial=None, warm=False):
+    """Half-Z scheme run; returns (state, bounds incl. const, last IterOut)."""
+    st = setup(F, D, B, partial)
+    lbs, out = [], None
+    for _ in range(iters):
+        w = warm and out is not None
+        out = iterate_half(st, prm, dual_mode, u0z=out.xi.copy() if w else None,
+                           u0y=out.gamma.copy() if w else None, u0x=out.alpha.copy() if w else None)
+        lbs.append(st.const + out.lb)
+    return st, lbs, out
 
 
 def sa_schedule(n, kf, kl, neglog_u, ub, t0=0.04, cool=0.99, period=100):

@@ -53,7 +53,14 @@
  *     are the printed ones (kappa_i nu / n per b, kappa_i nu / (n(n-1)(n-2)) per
  *     z); acceptance compares kappa^lb * nu with -ln(u) * T (u <= exp(-kappa^lb
  *     nu / T), the energy in the bound's units so that T = 4% of the upper
- *     bound is commensurate); the random fractions and -ln(u) are inputs.
+ *     bound is commensurate); the random fractions and -ln(u) are inputs;
+ *   - half-Z scheme (Section 5): lower-order members keep cost 0 (their
+ *     Z-LAPs are skipped); the y move of Eq. 2.21 runs with phi_y = 1/2 (the
+ *     updated slack split equally between y_ijpq and y_jiqp); only the three
+ *     upper members pool (kz pi_z + cy * [upper y slack after the y move] +
+ *     cx pi_x) and share (1/2 to each other upper member); the x slack of the
+ *     lower rows (i > j) moves on the y level, kx pi_x(ip)/(n-1) from y_ijpq
+ *     to its mirror, so every Y-LAP row passes its share of pi_x on.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -822,6 +829,115 @@ int or_iterate_v(int n, const double* prm, const int* opt, double p2tol, double 
     or_move_x_fast(n, prm[2], bx, pix);
   }
   free(sa);
+  if (stats) memcpy(stats, st, sizeof st);
+  return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Half-Z-LAP scheme (Section 5, after Goncalves et al.).  Members of a class  */
+/* whose first facility index exceeds the second ("lower order") keep cost 0:  */
+/* their Z-LAPs (i > j) have optimum 0 and zero duals and are not solved.     */
+/* The three upper members (i,j,k|p,q,r), (i,k,j|p,r,q), (j,k,i|q,r,p) pool   */
+/* s = kz pi_z + cy pi'_y + cx pi_x, pi'_y the upper y's slack after the y    */
+/* move of Eq. 2.21 (phi_y = 1/2), and each takes half of the other two      */
+/* pools; a lower y passes kx pi_x/(n-1) to its mirror on the y level.        */
+/* ------------------------------------------------------------------------ */
+void or_stage_z_upper(int n, int dual_mode, const double* Dhat, const double* u0, double* Theta, double* xi,
+                      double* psi, long long* naug, long long* nrelax) {
+  int m = n - 2;
+  long long aug_tot = 0, relax_tot = 0;
+  for (int i = 0; i < n; i++)
+    for (int p = 0; p < n; p++)
+      for (int j = 0; j < n; j++) {
+        if (j == i) continue;
+        for (int q = 0; q < n; q++) {
+          if (q == p) continue;
+          long long t = tile_of(n, i, p, j, q);
+          if (j < i) {
+            Theta[t] = 0.0;
+            for (int k = 0; k < m; k++) xi[t * m + k] = psi[t * m + k] = 0.0;
+            continue;
+          }
+          int perm[64];
+          int aug;
+          long long relax;
+          solve_one(m, Dhat + t * m * m, u0 ? u0 + t * m : NULL, dual_mode, &Theta[t], xi + t * m, psi + t * m, perm,
+                    &aug, &relax);
+          aug_tot += aug;
+          relax_tot += relax;
+        }
+      }
+  if (naug) *naug = aug_tot;
+  if (nrelax) *nrelax = relax_tot;
+}
+
+void or_redistribute_half(int n, const double* prm, double* Dhat, double* Chat, const double* xi, const double* psi,
+                          const double* piy, const double* pix) {
+  double kz = prm[0], cy = prm[1] / (double)(n - 2), cx = prm[2] / ((double)(n - 1) * (double)(n - 2));
+  double phi_y = prm[3], cxy = prm[2] / (double)(n - 1);
+  for (int i = 0; i < n; i++)
+    for (int j = i + 1; j < n; j++)
+      for (int k = j + 1; k < n; k++)
+        for (int p = 0; p < n; p++)
+          for (int q = 0; q < n; q++) {
+            if (q == p) continue;
+            for (int r = 0; r < n; r++) {
+              if (r == p || r == q) continue;
+              /* upper members in member order: (i,j,k|p,q,r), (i,k,j|p,r,q), (j,k,i|q,r,p) */
+              int F[3][3] = {{i, j, k}, {i, k, j}, {j, k, i}};
+              int L[3][3] = {{p, q, r}, {p, r, q}, {q, r, p}};
+              double s[3], D[3];
+              long long idx[3];
+              for (int u = 0; u < 3; u++) {
+                int a = F[u][0], b = F[u][1], c = F[u][2], x = L[u][0], y = L[u][1], w = L[u][2];
+                double pz = piz_at(n, Dhat, xi, psi, a, b, c, x, y, w);
+                /* the upper y's slack after the y move: its own half kept plus half of its mirror's */
+                long long t = tile_of(n, a, x, b, y), tm = tile_of(n, b, y, a, x);
+                double py = (piy[t] - phi_y * piy[t]) + phi_y * piy[tm];
+                double ty = cy * py + cx * pix[a * n + x];
+                s[u] = fma(kz, pz, ty);
+                idx[u] = zidx(n, a, b, c, x, y, w);
+                D[u] = Dhat[idx[u]];
+              }
+              double S = (s[0] + s[1]) + s[2];
+              for (int u = 0; u < 3; u++) Dhat[idx[u]] = fma(0.5, S - s[u], D[u] - s[u]);
+            }
+          }
+  /* y move of Eq. 2.21 with phi_y (1/2): every y keeps (1 - phi_y) of its slack and
+   * receives phi_y of its mirror's; an upper y then gives that updated slack to its z (ky) */
+  long long T = or_num_tiles(n);
+  double* out = (double*)malloc(sizeof(double) * T);
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < n; j++) {
+      if (j == i) continue;
+      for (int p = 0; p < n; p++)
+        for (int q = 0; q < n; q++) {
+          if (q == p) continue;
+          long long t = tile_of(n, i, p, j, q), tp = tile_of(n, j, q, i, p);
+          out[t] = (Chat[t] - phi_y * piy[t]) + phi_y * piy[tp];
+          /* Type 3 on the y level for the lower rows: y_ijpq (i > j) gives
+           * kx pi_x(ip) / (n-1) to its mirror y_jiqp */
+          if (i > j) out[t] = out[t] - cxy * pix[i * n + p];
+          else out[t] = out[t] + cxy * pix[j * n + q];
+        }
+    }
+  memcpy(Chat, out, sizeof(double) * T);
+  free(out);
+}
+
+/* One iteration of the half-Z scheme (solve, then the ascent step in place).
+ * prm = {kz, ky, kx, phi_y} (the paper: 2/3, 1, 1, 1/2). */
+int or_iterate_half(int n, const double* prm, int dual_mode, const double* bprime, double* Chat, double* Dhat,
+                    const double* u0z, const double* u0y, const double* u0x, double* lb, double* Theta, double* xi,
+                    double* psi, double* Delta, double* gamma, double* delta, double* alpha, double* beta,
+                    int* xperm, double* pix, double* piy, long long* stats) {
+  if (n < 3) return OR_EINVAL;
+  long long st[6] = {0, 0, 0, 0, 0, 0};
+  or_stage_z_upper(n, dual_mode, Dhat, u0z, Theta, xi, psi, &st[0], &st[1]);
+  or_stage_y(n, dual_mode, Chat, Theta, u0y, Delta, gamma, delta, &st[2], &st[3]);
+  or_stage_x(n, dual_mode, bprime, Delta, u0x, lb, alpha, beta, xperm, &st[4], &st[5]);
+  or_reduced_xy(n, bprime, Delta, alpha, beta, Chat, Theta, gamma, delta, pix, piy);
+  or_redistribute_half(n, prm, Dhat, Chat, xi, psi, piy, pix);
   if (stats) memcpy(stats, st, sizeof st);
   return OR_OK;
 }

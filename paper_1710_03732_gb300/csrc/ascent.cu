@@ -161,6 +161,8 @@ struct rlt2_ctx {
   double* saterm = nullptr;
   double* sa_buf = nullptr;  // Type 4 draws: kf[count*n] | kl[count*n] | K[count] | thr[count]
   int sa_count = 0;
+  int* zmap = nullptr;       // half-Z scheme: upper tiles
+  long long Tz = 0;
   int *xperm = nullptr, *ubperm = nullptr, *trips = nullptr;
   int ntrip = 0;
   DevScalars* sc = nullptr;
@@ -187,6 +189,7 @@ static void ctx_free(rlt2_ctx* c) {
   if (c->xcost && c->xcost != c->bprime) cudaFree(c->xcost);
   if (c->saterm) cudaFree(c->saterm);
   if (c->sa_buf) cudaFree(c->sa_buf);
+  if (c->zmap) cudaFree(c->zmap);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->u0buf) cudaFree(c->u0buf);
   delete c;
@@ -227,6 +230,8 @@ static IterView view_of(const rlt2_ctx* c) {
   v.sc = c->sc;
   v.xcost = c->xcost;
   v.saterm = c->saterm;
+  v.zmap = c->zmap;
+  v.Tz = c->Tz;
   v.sa_count = c->sa_count;
   if (c->sa_count > 0) {
     const long long cn = (long long)c->sa_count * c->n;
@@ -264,12 +269,16 @@ extern "C" void rlt2_params_default(rlt2_params* p) {
   p->sa_t0 = 0.04;
   p->sa_cool = 0.99;
   p->sa_period = 100;
+  p->half_z = 0;
 }
 
 bool rlt2::params_valid(const rlt2_params& p) {
   auto in01 = [](double x) { return std::isfinite(x) && x >= 0.0 && x <= 1.0; };
   if (!in01(p.kz) || !in01(p.ky) || !in01(p.kx) || !in01(p.phi_y)) return false;
-  if (p.phi_y + p.ky > 1.0) return false;
+  if (p.half_z != 0 && p.half_z != 1) return false;
+  // the half scheme moves an upper y's slack (ky) and a lower y's slack (phi_y): different y
+  if (!p.half_z && p.phi_y + p.ky > 1.0) return false;
+  if (p.half_z && (p.variant != 0 || p.two_phase != 0)) return false;
   double s = 0.0;
   for (int l = 0; l < 5; ++l) {
     if (!in01(p.phi_z[l])) return false;
@@ -410,6 +419,7 @@ extern "C" rlt2_status rlt2_create(int n, const double* F, const double* D, cons
   AL(c->sc, 1);
   AL(c->saterm, n2);
   if (prm.variant == 1) AL(c->xcost, n2);
+  if (prm.half_z) AL(c->zmap, T / 2);
 #undef AL
   if (!c->xcost) c->xcost = c->bprime;  // S variant: the X-LAP reads b' itself
   if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -452,10 +462,31 @@ extern "C" rlt2_status rlt2_create(int n, const double* F, const double* D, cons
       (e = cudaMemcpyAsync(c->trips, trips.data(), trips.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(c->sc, &init, sizeof init, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(c->Dhat, 0, sizeof(double) * (size_t)c->E, s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(c->xi, 0, sizeof(double) * T * m, s)) != cudaSuccess) {
+      (e = cudaMemsetAsync(c->xi, 0, sizeof(double) * T * m, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->psi, 0, sizeof(double) * T * m, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->Theta, 0, sizeof(double) * T, s)) != cudaSuccess) {
     cudaStreamSynchronize(s);
     cleanup_tmp();
     return fail(e, "upload");
+  }
+  // half-Z scheme: the tiles (i,p,j',q') with j > i, i.e. j' >= i; the others keep
+  // D^ = 0, Theta = 0 and zero duals forever
+  c->Tz = (long long)T;
+  if (prm.half_z) {
+    std::vector<int> up;
+    up.reserve(T / 2);
+    for (int i = 0; i < nr; ++i)
+      for (int p2 = 0; p2 < nr; ++p2)
+        for (int jj = i; jj < nr - 1; ++jj)
+          for (int qq = 0; qq < nr - 1; ++qq) up.push_back(((i * nr + p2) * (nr - 1) + jj) * (nr - 1) + qq);
+    c->Tz = (long long)up.size();
+    if ((e = cudaMemcpyAsync(c->zmap, up.data(), up.size() * sizeof(int), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess) {
+      cudaStreamSynchronize(s);
+      cleanup_tmp();
+      return fail(e, "upload");
+    }
+    cudaStreamSynchronize(s);  // the host vector must outlive the copy
   }
   const int* dfac = dint;
   const int* dloc = dint + nr;
@@ -488,6 +519,8 @@ MoveYArgs rlt2::make_move_y(const IterView& v) {
   a.cx = p.kx / ((double)(n - 1) * (double)(n - 2));
   a.phi_y = p.phi_y;
   a.fast = p.variant == 1;
+  a.half = p.half_z;
+  a.cxy = p.kx / (double)(n - 1);
   a.keep_y = (1.0 - p.ky) - p.phi_y;
   a.keep_x = 1.0 - p.kx;
   a.piy = v.piy;
@@ -530,6 +563,7 @@ MoveZArgs rlt2::make_move_z(const IterView& v) {
   mz.uniform = (p.phi_z[0] == p.phi_z[1] && p.phi_z[0] == p.phi_z[2] && p.phi_z[0] == p.phi_z[3] &&
                 p.phi_z[0] == p.phi_z[4]);
   mz.fast = p.variant == 1;
+  mz.half = p.half_z;
   mz.saterm = v.saterm;
   mz.Dhat = v.Dhat;
   mz.xi = v.xi;
@@ -594,7 +628,8 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   if ((e = cudaGetLastError()) != cudaSuccess || (e = rec(1, 1)) != cudaSuccess) return e;
   // 3) Z stage
   LapArgs z{};
-  z.batch = T;
+  z.batch = v.zmap ? v.Tz : T;
+  z.map = v.zmap;
   z.m = m;
   z.A = v.Dhat;
   z.u0 = p.warm == 1 ? v.xi : nullptr;
@@ -909,6 +944,10 @@ extern "C" rlt2_status rlt2_set_sa(rlt2_ctx* c, int count, const double* kf, con
   }
   const int n = c->n;
   const rlt2_params& p = c->prm;
+  if (count > 0 && p.half_z) {
+    set_error("rlt2_set_sa: the Type 4 rule is not combined with the half-Z scheme");
+    return RLT2_EINVAL;
+  }
   if (count > 0) {
     if (!kf || !kl || !neglog_u) {
       set_error("rlt2_set_sa: NULL draws");

@@ -41,8 +41,9 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap(LapArgs a) {
   unsigned long long aug_acc = 0, relax_acc = 0;
 
   for (long long t0 = ((long long)blockIdx.x * wpb + wib) * per; t0 < a.batch; t0 += nwarps * per) {
-    const long long t = t0 + grp;
-    const bool have = t < a.batch;
+    const long long tb = t0 + grp;
+    const bool have = tb < a.batch;
+    const long long t = (have && a.map) ? (long long)a.map[tb] : tb;
     if (have) {
       const double* src = a.A + t * mm;
       const double* add = a.Badd ? a.Badd + t * mm : nullptr;

@@ -123,8 +123,8 @@ extern "C" rlt2_status rlt2_iterate_noalloc(int n, const double* F, const double
   rlt2_params prm;
   rlt2_params_default(&prm);
   if (p) prm = *p;
-  if (!params_valid(prm)) {
-    set_error("rlt2_iterate_noalloc: parameters out of range");
+  if (!params_valid(prm) || prm.half_z) {
+    set_error("rlt2_iterate_noalloc: parameters out of range (the half-Z scheme needs a context)");
     return RLT2_EINVAL;
   }
   double* base = nullptr;

@@ -239,6 +239,10 @@ extern "C" rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D,
     set_error("rlt2_bound_nodes: warm == 2 needs a network");
     return RLT2_EINVAL;
   }
+  if (prm.half_z) {
+    set_error("rlt2_bound_nodes: the half-Z scheme runs on single contexts only");
+    return RLT2_EINVAL;
+  }
   // per-node residual problems
   std::vector<NodeHost> nodes(n_nodes);
   for (int k = 0; k < n_nodes; ++k) {

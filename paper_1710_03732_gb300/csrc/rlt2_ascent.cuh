@@ -26,7 +26,9 @@ struct MoveYArgs {
   long long T;
   double cy, cx, phi_y;
   int fast;              // F variant: new incremental y and x costs from the slacks
+  int half;              // half-Z scheme (see move_y_range)
   double keep_y, keep_x;  // (1 - ky) - phi_y and 1 - kx (F variant)
+  double cxy;             // half-Z scheme: kx / (n-1), Type 3 on the y level for the lower rows
   const double* piy;
   const double* pix;
   double* Chat;
@@ -40,7 +42,8 @@ struct MoveYArgs {
 };
 
 // Per tile (i,p,j,q): the pending y move on C^ (S: Eq. 2.21 on the full cost;
-// F: keep_y pi_y(ijpq) + phi_y pi_y(jiqp)), the term cy*pi_y(ijpq) + cx*pi_x(ip)
+// F: keep_y pi_y(ijpq) + phi_y pi_y(jiqp); half-Z scheme: Eq. 2.21 plus the
+// lower rows' x slack moved on the y level), the term cy*pi_y(ijpq) + cx*pi_x(ip)
 // that rules 2 and 3 add to each z pool of the tile, plus the Type 4 amount
 // kf_i g + kl_p g of an accepted draw (rule 4, Section 5: accepted when
 // kappa^lb * nu <= -ln(u) T).  Thread 0 records the draw's acceptance and, in
@@ -71,10 +74,17 @@ __device__ __forceinline__ void move_y_range(const MoveYArgs& a, long long start
     const int j = jj + (jj >= i), q = qq + (qq >= p);
     const long long tp = ((long long)(j * n + q) * n1 + (i - (i > j))) * n1 + (p - (p > q));
     const double py = a.piy[t];
-    double ty = dadd_(dmul_(a.cy, py), dmul_(a.cx, a.pix[ip]));
+    // half-Z scheme: the z pools of an upper tile take the y slack left after the y move
+    const double pyz = a.half ? dadd_(dsub_(py, dmul_(a.phi_y, py)), dmul_(a.phi_y, a.piy[tp])) : py;
+    double ty = dadd_(dmul_(a.cy, pyz), dmul_(a.cx, a.pix[ip]));
     if (on) ty = dadd_(ty, dadd_(dmul_(kf[i], g), dmul_(kl[p], g)));
     a.tterm[t] = ty;
-    if (a.fast)
+    if (a.half) {
+      // y move of Eq. 2.21, then Type 3 on the y level: a lower y (i > j) gives
+      // kx pi_x(ip) / (n-1) to its mirror (the lower z stay at zero)
+      const double c0 = dadd_(dsub_(a.Chat[t], dmul_(a.phi_y, py)), dmul_(a.phi_y, a.piy[tp]));
+      a.Chat[t] = (i > j) ? dsub_(c0, dmul_(a.cxy, a.pix[ip])) : dadd_(c0, dmul_(a.cxy, a.pix[j * n + q]));
+    } else if (a.fast)
       a.Chat[t] = dadd_(dmul_(a.keep_y, py), dmul_(a.phi_y, a.piy[tp]));
     else
       a.Chat[t] = dadd_(dsub_(a.Chat[t], dmul_(a.phi_y, py)), dmul_(a.phi_y, a.piy[tp]));
@@ -110,6 +120,7 @@ struct MoveZArgs {
   int kz_one;   // kz == 1: kz*x == x exactly, skip the product
   int uniform;  // all phi equal: member b gets phi * (S - s_b)
   int fast;     // F variant: the member keeps fma(-kz, pi_z, pi_z) (minus a Type 4 amount)
+  int half;     // half-Z scheme: only the three upper members move (lower ones stay 0)
   const double* saterm;  // n*n Type 4 amounts (F variant, when sc->sa_on)
   double* Dhat;
   const double* xi;
@@ -124,7 +135,53 @@ struct MoveZArgs {
 // so members (i,j,k|p,q,r) and (j,i,k|q,p,r) are read and written as contiguous
 // rows; the other four members' rows are shared by the block or by the n blocks
 // of the same triple, which run back to back.
+// Half-Z scheme (Section 5): the upper members (i,j,k|p,q,r), (i,k,j|p,r,q) and
+// (j,k,i|q,r,p) -- members 0, 1, 3 -- pool s = kz pi_z + tile term and each
+// receives half of the other two pools: D' = fma(1/2, S - s, D - s) with S the
+// sum of the three pools in member order.  Lower members are never touched.
+__device__ __forceinline__ void move_z_half_block(const MoveZArgs& a, int blk) {
+  RLT2_CLASS_TABLES
+  (void)kPart;
+  constexpr int kUp[3] = {0, 1, 3};
+  const int n = a.n, m = a.m, n1 = n - 1;
+  const int tr = blk / n, p = blk - tr * n;
+  const int packed = a.trips[tr];
+  const int F3[3] = {packed & 255, (packed >> 8) & 255, packed >> 16};
+  const int npairs = n1 * m;
+  const long long mm = (long long)m * m;
+  for (int c = threadIdx.x; c < npairs; c += blockDim.x) {
+    const int qq = c / m, rr = c - qq * m;
+    const int q = qq + (qq >= p);
+    const int lo = p < q ? p : q, hi = p < q ? q : p;
+    int r = rr;
+    r += (r >= lo);
+    r += (r >= hi);
+    const int L3[3] = {p, q, r};
+    double s[3], Dv[3];
+    long long idx[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int b = kUp[u];
+      const int f0 = F3[kOrd[b][0]], f1 = F3[kOrd[b][1]], f2 = F3[kOrd[b][2]];
+      const int l0 = L3[kOrd[b][0]], l1 = L3[kOrd[b][1]], l2 = L3[kOrd[b][2]];
+      const long long t = ((long long)(f0 * n + l0) * n1 + (f1 - (f1 > f0))) * n1 + (l1 - (l1 > l0));
+      const int kr = f2 - (f2 > f0) - (f2 > f1), cc = l2 - (l2 > l0) - (l2 > l1);
+      idx[u] = t * mm + kr * m + cc;
+      Dv[u] = a.Dhat[idx[u]];
+      const double pz = dsub_(dsub_(Dv[u], __ldg(a.xi + t * m + kr)), __ldg(a.psi + t * m + cc));
+      s[u] = a.kz_one ? dadd_(pz, __ldg(a.tterm + t)) : __fma_rn(a.kz, pz, __ldg(a.tterm + t));
+    }
+    const double S = dadd_(dadd_(s[0], s[1]), s[2]);
+#pragma unroll
+    for (int u = 0; u < 3; ++u) a.Dhat[idx[u]] = __fma_rn(0.5, dsub_(S, s[u]), dsub_(Dv[u], s[u]));
+  }
+}
+
 __device__ __forceinline__ void move_z_block(const MoveZArgs& a, int blk) {
+  if (a.half) {
+    move_z_half_block(a, blk);
+    return;
+  }
   RLT2_CLASS_TABLES
   const int n = a.n, m = a.m, n1 = n - 1;
   const int tr = blk / n, p = blk - tr * n;

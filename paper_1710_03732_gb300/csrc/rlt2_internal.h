@@ -27,6 +27,7 @@ struct LapArgs {
   const int* skip;           // nullable: kernel does nothing when *skip != 0
   int group;                 // lanes per LAP (8, 16 or 32); 0 = smallest that fits m
   int warps_per_block;       // 4 or 8; 0 = 8
+  const int* map;            // nullable: LAP b works on slot map[b] of every array (a subset of tiles)
 };
 
 // The LAPs of one stage of one branch-and-bound node.
@@ -100,6 +101,8 @@ struct IterView {
   double* saterm;  // n*n Type 4 amount per (first facility, first location) of the pending step
   const double *sa_kf, *sa_kl, *sa_K, *sa_thr;  // Type 4 draws (count*n, count*n, count, count)
   int sa_count;
+  const int* zmap;  // half-Z scheme: the tiles with first facility < second facility
+  long long Tz;     // number of Z-LAPs solved (T, or T/2 with the half scheme)
   int *xperm, *ubperm, *trips;
   DevScalars* sc;
 };

@@ -26,7 +26,8 @@ class rlt2_params(ctypes.Structure):
                 ("warm", ctypes.c_int), ("min_gap", ctypes.c_double), ("ub", ctypes.c_double),
                 ("feas_tol", ctypes.c_double), ("stall_window", ctypes.c_int), ("stall_tol", ctypes.c_double),
                 ("variant", ctypes.c_int), ("two_phase", ctypes.c_int), ("phase2_tol", ctypes.c_double),
-                ("sa_t0", ctypes.c_double), ("sa_cool", ctypes.c_double), ("sa_period", ctypes.c_int)]
+                ("sa_t0", ctypes.c_double), ("sa_cool", ctypes.c_double), ("sa_period", ctypes.c_int),
+                ("half_z", ctypes.c_int)]
 
 
 class Rlt2Error(RuntimeError):
@@ -138,8 +139,9 @@ def _stream(stream) -> Optional[int]:
 
 def params(kz=1.0, ky=0.5, kx=1.0, phi_y=0.5, phi_z=(0.2,) * 5, dual_mode=1, warm=0, min_gap=0.0, ub=0.0,
            feas_tol=1e-9, stall_window=0, stall_tol=0.0002, variant=0, two_phase=0, phase2_tol=1e-9, sa_t0=0.04,
-           sa_cool=0.99, sa_period=100) -> rlt2_params:
-    """Parameters (variant 0 = S, 1 = F; two_phase; annealing schedule of the Type 4 rule)."""
+           sa_cool=0.99, sa_period=100, half_z=0) -> rlt2_params:
+    """Parameters (variant 0 = S, 1 = F; two_phase; annealing schedule of the Type 4 rule;
+    half_z = the half-Z-LAP scheme, see half_z_params)."""
     p = rlt2_params()
     lib().rlt2_params_default(ctypes.byref(p))
     p.kz, p.ky, p.kx, p.phi_y = kz, ky, kx, phi_y
@@ -149,7 +151,16 @@ def params(kz=1.0, ky=0.5, kx=1.0, phi_y=0.5, phi_z=(0.2,) * 5, dual_mode=1, war
     p.stall_window, p.stall_tol = stall_window, stall_tol
     p.variant, p.two_phase, p.phase2_tol = int(variant), int(two_phase), phase2_tol
     p.sa_t0, p.sa_cool, p.sa_period = sa_t0, sa_cool, int(sa_period)
+    p.half_z = int(half_z)
     return p
+
+
+def half_z_params(**kw) -> rlt2_params:
+    """The half-Z-LAP scheme with the paper's values (Section 5): kz = 2/3 for the
+    upper members, ky = kx = 1, phi_y = 1/2."""
+    d = dict(kz=2.0 / 3.0, ky=1.0, kx=1.0, phi_y=0.5, half_z=1)
+    d.update(kw)
+    return params(**d)
 
 
 # ------------------------------------------------------------ C entry points --

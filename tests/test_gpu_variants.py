@@ -213,3 +213,75 @@ def test_nodes_variants_match_single_contexts(R, mode):
         with R.Context(inst.F, inst.D, inst.B, partial=parts[k], prm=prm) as ctx:
             ref, _ = ctx.iterate(iters)
         assert np.array_equal(hist[k], ref), k
+
+
+# ----------------------------------------------------------- half-Z scheme ----
+@pytest.mark.parametrize("which", ["cfg1", "asymB", "partial"])
+@pytest.mark.parametrize("warm", [False, True])
+def test_half_raw_bit_exact(R, which, warm):
+    """Half-Z scheme (only the Z-LAPs with i < j solved): bounds, D^ and C^ of the
+    last solve, duals and reduced costs equal the oracle's bit for bit; the
+    lower-order z stay exactly 0."""
+    partial = None
+    if which == "cfg1":
+        inst, iters = I.config(1), 14
+    elif which == "asymB":
+        inst, iters = I.random_instance(7, 43, with_b=True, asymmetric=True), 12
+    else:
+        inst, iters = I.random_instance(9, 44, with_b=True), 10
+        partial = -np.ones(9, dtype=np.int32)
+        partial[[0, 8]] = [4, 7]
+    prm = R.half_z_params(dual_mode=0, feas_tol=0.0, warm=int(warm))
+    with R.Context(inst.F, inst.D, inst.B, partial=partial, prm=prm) as ctx:
+        lbs, done = ctx.iterate(iters)
+        D, C = ctx.export_state()
+        duals = ctx.duals()
+        red = ctx.reduced_costs()
+    st = O.setup(inst.F, inst.D, inst.B, partial)
+    ref, out = [], None
+    for _ in range(iters):
+        before = (st.Dhat.copy(), st.Chat.copy())
+        w = warm and out is not None
+        out = O.iterate_half(st, dual_mode=0, u0z=out.xi.copy() if w else None,
+                             u0y=out.gamma.copy() if w else None, u0x=out.alpha.copy() if w else None)
+        ref.append(st.const + out.lb)
+    assert done == iters
+    assert np.array_equal(lbs, np.array(ref))
+    assert np.array_equal(D, before[0]) and np.array_equal(C, before[1])
+    assert np.array_equal(duals["xi"], out.xi) and np.array_equal(duals["psi"], out.psi)
+    assert np.array_equal(duals["gamma"], out.gamma) and np.array_equal(duals["alpha"], out.alpha)
+    assert np.array_equal(red["pi_y"], out.piy) and np.array_equal(red["pi_x"], out.pix)
+    n, m = st.n, st.n - 2
+    for i in range(n):
+        for j in range(i):
+            t = O.tile_index(n, i, 0 if i != 0 else 1, j, 1 if i != 0 else 0)
+            assert np.all(D[t * m * m:(t + 1) * m * m] == 0.0)
+
+
+def test_half_canonical_close_and_half_the_work(R):
+    """n = 12 grid, canonical duals, warm starts: bounds within 1e-6 of the oracle;
+    the Z stage runs half the LAPs of the full scheme."""
+    inst = I.config(2)
+    iters = 25
+    with R.Context(inst.F, inst.D, inst.B, prm=R.half_z_params(feas_tol=0.0, warm=1)) as ctx:
+        lbs, done = ctx.iterate(iters)
+    _, ref, _ = O.run_half(inst.F, inst.D, inst.B, iters=iters, warm=True)
+    ref = np.array(ref)
+    assert done == iters
+    assert np.max(np.abs(lbs - ref) / np.maximum(1.0, np.abs(ref))) <= 1e-6
+    assert np.all(np.diff(lbs) >= -1e-9 * np.abs(lbs[:-1]))
+
+
+def test_half_rejections(R):
+    inst = I.config(1)
+    with pytest.raises(R.Rlt2Error):
+        R.Context(inst.F, inst.D, inst.B, prm=R.half_z_params(variant=1))
+    with pytest.raises(R.Rlt2Error):
+        R.Context(inst.F, inst.D, inst.B, prm=R.half_z_params(two_phase=1))
+    with R.Context(inst.F, inst.D, inst.B, prm=R.half_z_params(ub=100.0)) as ctx:
+        kf, kl, ng = I.sa_draws(inst.n, 3, 2)
+        with pytest.raises(R.Rlt2Error):
+            ctx.set_sa(kf, kl, ng)
+    parts = -np.ones((2, 8), dtype=np.int32)
+    with pytest.raises(R.Rlt2Error):
+        R.rlt2_bound_nodes(inst.F, inst.D, parts, 3, prm=R.half_z_params())

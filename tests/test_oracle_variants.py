@@ -234,3 +234,93 @@ def test_move_sums(with_sa):
     bx = np.zeros(n * n)
     O.lib().or_move_x_fast(n, float(kx), O._d(bx), O._d(out.pix))
     assert np.allclose(bx, (1 - kx) * out.pix, rtol=1e-15, atol=0)
+
+
+# ----------------------------------------------------------- half-Z scheme ----
+def _lower_mask(n):
+    """Tiles (i,p,j,q) with i > j (lower order) and the matching z entries."""
+    m = n - 2
+    T = O.num_tiles(n)
+    low = np.zeros(T, dtype=bool)
+    for i in range(n):
+        for p in range(n):
+            for j in range(n):
+                for q in range(n):
+                    if i != j and p != q and i > j:
+                        low[O.tile_index(n, i, p, j, q)] = True
+    return low, np.repeat(low, m * m)
+
+
+def test_half_lower_members_stay_zero():
+    """The lower-order z keep cost 0 and their (skipped) Z-LAPs optimum 0 and zero
+    duals -- so skipping them is exact: solving them anyway changes nothing."""
+    inst = I.random_instance(7, 41, with_b=True, asymmetric=True)
+    st = O.setup(inst.F, inst.D, inst.B)
+    n, m = st.n, st.n - 2
+    low_t, low_z = _lower_mask(n)
+    for _ in range(6):
+        out = O.iterate_half(st, dual_mode=1)
+        assert np.all(st.Dhat[low_z] == 0.0)
+        assert np.all(out.Theta[low_t] == 0.0)
+    th_all, xi_all, psi_all, _, _ = O.stage_z(n, st.Dhat, dual_mode=1)
+    snap = O.State(st.n, st.const, st.bprime, st.Chat.copy(), st.Dhat.copy())
+    out = O.iterate_half(snap, dual_mode=1)
+    assert np.array_equal(th_all[low_t], np.zeros(low_t.sum()))
+    assert np.allclose(th_all, out.Theta, rtol=1e-12, atol=1e-12)
+    lowm = np.repeat(low_t, m)
+    assert np.all(xi_all[lowm] == 0.0) and np.all(psi_all[lowm] == 0.0)
+
+
+@pytest.mark.parametrize("which", ["cfg1", "asymB", "partial"])
+def test_half_monotone_and_valid(which):
+    """Theorem 1 for the half scheme (every reduced cost stays >= 0 under the old
+    duals), bounds below the brute-force optimum of every completion."""
+    inst, part = _inst(which)
+    _, lbs, _ = O.run_half(inst.F, inst.D, inst.B, iters=30, partial=part)
+    for a, b in zip(lbs, lbs[1:]):
+        assert b >= a - 1e-9 * abs(a)
+    if part is None:
+        opt, _ = O.qap_brute(inst.F, inst.D, inst.B)
+    else:
+        free_f = [i for i in range(inst.n) if part[i] < 0]
+        free_l = [q for q in range(inst.n) if q not in set(part[part >= 0])]
+        import itertools
+        opt = np.inf
+        for perm in itertools.permutations(free_l):
+            full = part.copy()
+            full[free_f] = perm
+            opt = min(opt, O.qap_cost(inst.F, inst.D, inst.B, full))
+    assert max(lbs) <= opt + 1e-9 * abs(opt)
+
+
+def test_half_reaches_optimum_on_n8_grid():
+    """Like the full scheme, the half scheme closes the gap on the n = 8 grid
+    (optimum 118 by brute force) -- a broken move or a lost slack stalls below."""
+    inst = I.config(1)
+    _, lbs, _ = O.run_half(inst.F, inst.D, inst.B, iters=40)
+    assert max(lbs) >= 118.0 - 1e-6
+
+
+def test_half_moves_conserve_pair_and_class_sums():
+    """The half-scheme step is a symmetric redistribution: every class's z sum and
+    every mirror pair C^_ijpq + C^_jiqp (y move and the y-level x move) keep their
+    totals."""
+    inst = I.random_instance(6, 42, with_b=True)
+    st = O.setup(inst.F, inst.D, inst.B)
+    for _ in range(3):
+        O.iterate_half(st, dual_mode=0)
+    n = st.n
+    D0, C0 = st.Dhat.copy(), st.Chat.copy()
+    O.iterate_half(st, dual_mode=0)
+    for idx in _classes(n):
+        idx = np.array(idx)
+        assert abs(st.Dhat[idx].sum() - D0[idx].sum()) <= 1e-10 * max(1.0, np.abs(D0[idx]).sum())
+    for i in range(n):
+        for j in range(i + 1, n):
+            for p in range(n):
+                for q in range(n):
+                    if p == q:
+                        continue
+                    t, tp = O.tile_index(n, i, p, j, q), O.tile_index(n, j, q, i, p)
+                    assert abs((st.Chat[t] + st.Chat[tp]) - (C0[t] + C0[tp])) <= 1e-10 * max(1.0, abs(C0[t]) +
+                                                                                             abs(C0[tp]))
