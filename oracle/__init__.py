@@ -88,6 +88,10 @@ def lib():
         L.or_redistribute_half.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
         L.or_iterate_half.argtypes = ([ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
                                        _dp, _dp, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _lp])
+        L.or_child_state.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, _dp,
+                                     _dp, _dp, _dp]
+        L.or_lagrangian_objective.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, _ip]
+        L.or_lagrangian_objective.restype = ctypes.c_double
         L.or_have_openmp.restype = ctypes.c_int
         _fp = ctypes.POINTER(ctypes.c_float)
         L.or_f32_trunc.argtypes = [ctypes.c_double]
@@ -512,3 +516,26 @@ def mlp_grads(X, W1, b1, W2, b2, w3, b3, t, bf16_acts=True):
     loss = lib().or_mlp_backward(N, H, _f(X), _f(W2c), _f(w3c), int(bf16_acts), _d(out), _d(h1), _d(h2),
                                  _d(_f64(t)), *(_d(a) for a in g), ctypes.byref(gb3))
     return loss, g[0], g[1], g[2], g[3], g[4], gb3.value
+
+
+# --------------------------------------------------------------------------
+# branch and bound: parent -> child multiplier warm start (Section 4)
+# --------------------------------------------------------------------------
+def child_state(st: State, f: int, l: int) -> State:
+    """Child of `st` (residual indices) with facility f fixed at location l,
+    keeping the parent's multiplier-adjusted costs."""
+    n = st.n
+    nc = n - 1
+    bc = np.zeros(nc * nc)
+    Cc = np.zeros(max(num_tiles(nc), 1))
+    Dc = np.zeros(max(num_z(nc), 1)) if nc >= 3 else np.zeros(1)
+    cst = ctypes.c_double()
+    lib().or_child_state(n, f, l, _d(st.bprime), _d(st.Chat), _d(st.Dhat), float(st.const), _d(bc), _d(Cc), _d(Dc),
+                         ctypes.byref(cst))
+    return State(nc, cst.value, bc, Cc, Dc)
+
+
+def lagrangian_objective(st: State, perm) -> float:
+    s = np.ascontiguousarray(perm, dtype=np.int32)
+    return float(lib().or_lagrangian_objective(st.n, _d(st.bprime), _d(st.Chat), _d(st.Dhat), float(st.const),
+                                               _i(s)))

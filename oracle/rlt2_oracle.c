@@ -942,6 +942,78 @@ int or_iterate_half(int n, const double* prm, int dual_mode, const double* bprim
   return OR_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Parent -> child warm start of the branch-and-bound (Section 4, step 3):   */
+/* fixing facility f at location l (residual indices of the parent) in the  */
+/* parent's Lagrangian LRLT2(v) turns y_{i f p l}, y_{f i l p} into x_ip and  */
+/* z with (f,l) in any position into the y of the other two, so the child's */
+/* multiplier-adjusted costs are                                             */
+/*   D^_c(i,j,k|p,q,r) = D^_p(same facilities and locations)                 */
+/*   C^_c(i,j|p,q) = ((C^_p(i,j|p,q) + D^_p(i,j,f|p,q,l)) + D^_p(i,f,j|p,l,q)) */
+/*                   + D^_p(f,i,j|l,p,q)                                     */
+/*   b'_c(i|p)     = (b'_p(i|p) + C^_p(i,f|p,l)) + C^_p(f,i|l,p)              */
+/*   const_c       = const_p + b'_p(f|l)                                     */
+/* (child residual index a <-> parent a + (a >= f), locations likewise).      */
+/* ------------------------------------------------------------------------ */
+void or_child_state(int np, int f, int l, const double* bp, const double* Cp, const double* Dp, double cst_p,
+                    double* bc, double* Cc, double* Dc, double* cst_c) {
+  int nc = np - 1;
+#define PF(a) ((a) + ((a) >= f))
+#define PL(a) ((a) + ((a) >= l))
+  *cst_c = cst_p + bp[f * np + l];
+  for (int i = 0; i < nc; i++)
+    for (int p = 0; p < nc; p++) {
+      int I = PF(i), P = PL(p);
+      bc[i * nc + p] = (bp[I * np + P] + Cp[tile_of(np, I, P, f, l)]) + Cp[tile_of(np, f, l, I, P)];
+    }
+  for (int i = 0; i < nc; i++)
+    for (int j = 0; j < nc; j++) {
+      if (j == i) continue;
+      for (int p = 0; p < nc; p++)
+        for (int q = 0; q < nc; q++) {
+          if (q == p) continue;
+          int I = PF(i), J = PF(j), P = PL(p), Q = PL(q);
+          double c = Cp[tile_of(np, I, P, J, Q)];
+          if (nc >= 2 && np >= 3) {
+            c = c + Dp[zidx(np, I, J, f, P, Q, l)];
+            c = c + Dp[zidx(np, I, f, J, P, l, Q)];
+            c = c + Dp[zidx(np, f, I, J, l, P, Q)];
+          }
+          Cc[tile_of(nc, i, p, j, q)] = c;
+          if (nc < 3) continue;
+          for (int k = 0; k < nc; k++) {
+            if (k == i || k == j) continue;
+            for (int r = 0; r < nc; r++) {
+              if (r == p || r == q) continue;
+              Dc[zidx(nc, i, j, k, p, q, r)] = Dp[zidx(np, I, J, PF(k), P, Q, PL(r))];
+            }
+          }
+        }
+    }
+#undef PF
+#undef PL
+}
+
+/* Lagrangian objective of one full assignment (perm over the residual
+ * problem): const + sum_i b'(i|s_i) + sum_{i!=j} C^(i,j|s_i,s_j)
+ * + sum_{i,j,k distinct} D^(i,j,k|s_i,s_j,s_k).  For a permutation every RLT2
+ * constraint holds, so this equals the QAP cost for any multipliers. */
+double or_lagrangian_objective(int n, const double* b, const double* C, const double* D, double cst, const int* s) {
+  double v = cst;
+  for (int i = 0; i < n; i++) v += b[i * n + s[i]];
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < n; j++) {
+      if (j == i) continue;
+      v += C[tile_of(n, i, s[i], j, s[j])];
+      if (n < 3) continue;
+      for (int k = 0; k < n; k++) {
+        if (k == i || k == j) continue;
+        v += D[zidx(n, i, j, k, s[i], s[j], s[k])];
+      }
+    }
+  return v;
+}
+
 int or_have_openmp(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
