@@ -144,6 +144,23 @@ void rlt2_params_default(rlt2_params* p);
 rlt2_status rlt2_create(int n, const double* F, const double* D, const double* B, const int* partial,
                         const rlt2_params* p, void* stream, rlt2_ctx** out);
 
+/* Child context of a branch-and-bound node (Section 4, step 3): the parent's
+ * problem with facility `facility` fixed at location `location` (original
+ * indices, both free in the parent), starting from the parent's multipliers --
+ * its multiplier-adjusted costs of the last solve (the pending ascent step is
+ * not applied): in LRLT2(v), y_{i f p l} and y_{f i l p} become x_ip and each
+ * z with (f,l) in one position becomes the y of the other two, so
+ *   D^_c(i,j,k|p,q,r) = D^_p(i,j,k|p,q,r),
+ *   C^_c(i,j|p,q) = ((C^_p(i,j|p,q) + D^_p(i,j,f|p,q,l)) + D^_p(i,f,j|p,l,q)) + D^_p(f,i,j|l,p,q),
+ *   b'_c(i|p) = (b'_p(i|p) + C^_p(i,f|p,l)) + C^_p(f,i|l,p),  const_c = const_p + b'_p(f|l);
+ * the child's upper bounds use the plain QAP reduction of b.  Built on the
+ * parent's stream, on the device; the parent is not changed and may be
+ * destroyed afterwards.  p: the child's parameters (NULL = the parent's).
+ * Errors: EINVAL (NULL, not free, residual below 3, parent or p not the S
+ * variant), ENOMEM, ECUDA. */
+rlt2_status rlt2_create_child(rlt2_ctx* parent, int facility, int location, const rlt2_params* p,
+                              rlt2_ctx** out);
+
 /* Run up to `iters` iterations of RLT2-DA (Algorithm 1 / 2; S or F, one or two
  * phases, as the parameters select): the ascent
  * step from the previous iteration's reduced costs (if any), then the Z, Y and
@@ -279,6 +296,45 @@ typedef struct rlt2_mlp rlt2_mlp;
 rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D, const double* B, int n_nodes,
                              const int* partials, const rlt2_params* p, rlt2_mlp* mlp, int iters, size_t mem_budget,
                              double* lb_out, double* lb_hist, int* iters_out, long long* stats_out, void* stream);
+
+/* Branch and bound to optimality (Section 4) on one GPU, every node bounded by
+ * RLT2-DA.  Facilities are placed in a fixed order (order_rule 1: index order;
+ * 2: largest total interaction first, then largest interaction with those
+ * already placed; 3: the same with smallest -- the paper's best); a node at
+ * depth d fixes the first d facilities of the order and branches the next one
+ * over every free location (polytomic).  Open nodes wait in a best-first heap
+ * (deeper first among equal bounds); a node is fathomed when its bound reaches
+ * the incumbent minus abs_tol.  Children of a parent at depth <= warm_depth
+ * start from the parent's multipliers (rlt2_create_child) while at most
+ * max_states parent contexts are kept; other children start from zero.  Each
+ * node's ascent stops at iters_node iterations (iters_root at the root), when
+ * it is fathomed (min-gap against the incumbent) or by the stall rule of p.
+ * Nodes with at most two free facilities are enumerated.  Every bounded node's
+ * X-LAP primal is an incumbent candidate. */
+typedef struct rlt2_bnb_options {
+  int order_rule;       /* 1, 2 or 3; default 3 */
+  int iters_root;       /* default 200 */
+  int iters_node;       /* default 100 */
+  int warm_depth;       /* default 64 (all); -1: every node starts from zero multipliers */
+  int max_states;       /* parent contexts kept for warm starts at once; default 64 */
+  long long max_nodes;  /* stop after this many bounded nodes (0: no limit) */
+  double time_limit_s;  /* stop after this many seconds (0: no limit) */
+  double ub0;           /* known incumbent value (<= 0: none) */
+  double abs_tol;       /* fathom when LB >= UB - abs_tol; < 0 (default): 1 - 1e-6 when F, D, B are
+                           integral (the optimum is then an integer), else 1e-9 max(1, |UB|) */
+} rlt2_bnb_options;
+void rlt2_bnb_options_default(rlt2_bnb_options* o);
+
+/* n, F, D, B as in rlt2_create (root node); p: node parameters (S variant;
+ * NULL = defaults).  Outputs (host): *best = the best value found, perm (n
+ * ints) its permutation, *root_lb (nullable) the root bound, stats (nullable,
+ * 8) = {nodes bounded, nodes branched, completions enumerated, ascent
+ * iterations, deepest level, proven optimal (0/1), warm-started children,
+ * cold-started children}.  Not proven when max_nodes or time_limit_s stopped
+ * the search.  Errors: EINVAL, ENOMEM, ECUDA (from the node contexts). */
+rlt2_status rlt2_bnb_solve(int n, const double* F, const double* D, const double* B, const rlt2_params* p,
+                           const rlt2_bnb_options* o, double* best, int* perm, double* root_lb, long long* stats,
+                           void* stream);
 
 /* Dual ascent of a small QAP that allocates no device memory.  The paper has no
  * counterpart; this entry point exists for callers that cannot call cudaMalloc:

@@ -139,6 +139,81 @@ cudaError_t enqueue_setup(const IterView& v, int n_full, const double* dF, const
   return cudaGetLastError();
 }
 
+// ------------------------------------------------ parent -> child warm start --
+// A branch-and-bound child fixes residual facility f at location l of its
+// parent (Section 4).  In the parent's Lagrangian LRLT2(v), y_{i f p l} and
+// y_{f i l p} become x_ip and every z with (f,l) in one position becomes the y
+// of the other two, so the child starts from the parent's multipliers:
+//   D^_c(i,j,k|p,q,r) = D^_p(I,J,K|P,Q,R)        (I = i + (i >= f), P = p + (p >= l))
+//   C^_c(i,j|p,q) = ((C^_p(I,J|P,Q) + D^_p(I,J,f|P,Q,l)) + D^_p(I,f,J|P,l,Q)) + D^_p(f,I,J|l,P,Q)
+//   b'_c(i|p) = (b'_p(I|P) + C^_p(I,f|P,l)) + C^_p(f,I|l,P),  const_c = const_p + b'_p(f|l)
+// and, for upper bounds, the QAP's own reduction of b and the constant.
+__device__ __forceinline__ long long ptile(int n, int i, int p, int j, int q) {
+  return ((long long)(i * n + p) * (n - 1) + (j - (j > i))) * (n - 1) + (q - (q > p));
+}
+__device__ __forceinline__ long long pz(int n, int i, int j, int k, int p, int q, int r) {
+  const int m = n - 2;
+  return ptile(n, i, p, j, q) * m * m + (long long)(k - (k > i) - (k > j)) * m + (r - (r > p) - (r > q));
+}
+
+__global__ void k_child_z(int np, int f, int l, const double* __restrict__ Dp, double* __restrict__ Dc, long long Ec) {
+  const int nc = np - 1, n1 = nc - 1, mc = nc - 2;
+  const long long mm = (long long)mc * mc;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < Ec; e += (long long)gridDim.x * blockDim.x) {
+    const long long t = e / mm;
+    const int w = (int)(e - t * mm);
+    const int kk = w / mc, rr = w - kk * mc;
+    const int ip = (int)(t / (n1 * n1));
+    const int rem = (int)(t - (long long)ip * n1 * n1);
+    const int jj = rem / n1, qq = rem - jj * n1;
+    const int i = ip / nc, p = ip - i * nc;
+    const int j = jj + (jj >= i), q = qq + (qq >= p);
+    int k = kk;
+    k += (k >= (i < j ? i : j));
+    k += (k >= (i < j ? j : i));
+    int r = rr;
+    r += (r >= (p < q ? p : q));
+    r += (r >= (p < q ? q : p));
+    Dc[e] = Dp[pz(np, i + (i >= f), j + (j >= f), k + (k >= f), p + (p >= l), q + (q >= l), r + (r >= l))];
+  }
+}
+
+__global__ void k_child_yx(int np, int f, int l, const double* __restrict__ Dp, const double* __restrict__ Cp,
+                           const double* __restrict__ bp, const double* __restrict__ bqp, const double* __restrict__ Frp,
+                           const double* __restrict__ Drp, const double* cst_p, const double* cstq_p,
+                           double* __restrict__ Cc, double* __restrict__ bc, double* __restrict__ bqc,
+                           double* __restrict__ Frc, double* __restrict__ Drc, double* cst_c, double* cstq_c,
+                           long long Tc) {
+  const int nc = np - 1, n1 = nc - 1;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (long long t = t0; t < Tc; t += stride) {
+    const int ip = (int)(t / (n1 * n1));
+    const int rem = (int)(t - (long long)ip * n1 * n1);
+    const int jj = rem / n1, qq = rem - jj * n1;
+    const int i = ip / nc, p = ip - i * nc;
+    const int j = jj + (jj >= i), q = qq + (qq >= p);
+    const int I = i + (i >= f), J = j + (j >= f), P = p + (p >= l), Q = q + (q >= l);
+    double c = Cp[ptile(np, I, P, J, Q)];
+    c = dadd(c, Dp[pz(np, I, J, f, P, Q, l)]);
+    c = dadd(c, Dp[pz(np, I, f, J, P, l, Q)]);
+    c = dadd(c, Dp[pz(np, f, I, J, l, P, Q)]);
+    Cc[t] = c;
+  }
+  for (long long e = t0; e < (long long)nc * nc; e += stride) {
+    const int i = (int)e / nc, p = (int)e - i * nc;
+    const int I = i + (i >= f), P = p + (p >= l);
+    bc[e] = dadd(dadd(bp[I * np + P], Cp[ptile(np, I, P, f, l)]), Cp[ptile(np, f, l, I, P)]);
+    bqc[e] = dadd(dadd(bqp[I * np + P], dmul(Frp[I * np + f], Drp[P * np + l])), dmul(Frp[f * np + I], Drp[l * np + P]));
+    Frc[e] = Frp[I * np + (p + (p >= f))];
+    Drc[e] = Drp[(i + (i >= l)) * np + P];
+  }
+  if (t0 == 0) {
+    *cst_c = dadd(*cst_p, bp[f * np + l]);
+    *cstq_c = dadd(*cstq_p, bqp[f * np + l]);
+  }
+}
+
 }  // namespace rlt2
 
 using namespace rlt2;
@@ -163,6 +238,8 @@ struct rlt2_ctx {
   int sa_count = 0;
   int* zmap = nullptr;       // half-Z scheme: upper tiles
   long long Tz = 0;
+  double* bqap = nullptr;    // QAP linear costs of the residual problem (upper bounds); aliases bprime
+  double* d_cst_qap = nullptr;  // QAP constant of the fixed facilities; aliases d_cst
   int *xperm = nullptr, *ubperm = nullptr, *trips = nullptr;
   int ntrip = 0;
   DevScalars* sc = nullptr;
@@ -190,6 +267,8 @@ static void ctx_free(rlt2_ctx* c) {
   if (c->saterm) cudaFree(c->saterm);
   if (c->sa_buf) cudaFree(c->sa_buf);
   if (c->zmap) cudaFree(c->zmap);
+  if (c->bqap && c->bqap != c->bprime) cudaFree(c->bqap);
+  if (c->d_cst_qap && c->d_cst_qap != c->d_cst) cudaFree(c->d_cst_qap);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->u0buf) cudaFree(c->u0buf);
   delete c;
@@ -232,6 +311,8 @@ static IterView view_of(const rlt2_ctx* c) {
   v.saterm = c->saterm;
   v.zmap = c->zmap;
   v.Tz = c->Tz;
+  v.bqap = c->bqap;
+  v.cst_qap = c->d_cst_qap;
   v.sa_count = c->sa_count;
   if (c->sa_count > 0) {
     const long long cn = (long long)c->sa_count * c->n;
@@ -307,6 +388,115 @@ static cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
 }
 
+// Device buffers of a context whose sizes (n, m, T, E, ntrip) and parameters
+// are set: memory admission, allocation, the capture stream, cleared D^, duals
+// and Theta, fresh scalars, the facility triples and (half-Z scheme) the tile
+// map.  own_qap: the QAP linear costs and constant used for upper bounds get
+// their own buffers (child contexts, whose b' carries multipliers); otherwise
+// they are b' and the constant.  Frees c and returns the status on failure.
+static rlt2_status ctx_alloc(rlt2_ctx* c, bool own_qap) {
+  const int nr = c->n;
+  const rlt2_params& prm = c->prm;
+  size_t need = sizeof(double) * ((size_t)c->E + 6 * (size_t)c->T + 2 * (size_t)c->T * c->m + 10 * (size_t)nr * nr +
+                                  2 * (size_t)nr * nr * nr + kRing) +
+                sizeof(int) * (size_t)(c->ntrip + nr + (prm.half_z ? c->T / 2 : 0)) + (64u << 20);
+  size_t fr = 0, tot = 0;
+  cudaError_t e = cudaMemGetInfo(&fr, &tot);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaMemGetInfo");
+  }
+  if (need > fr) {
+    delete c;
+    set_error("rlt2_create: not enough free device memory");
+    return RLT2_ENOMEM;
+  }
+  rlt2_status st = RLT2_OK;
+  auto fail = [&](cudaError_t err, const char* what) {
+    st = (err == cudaErrorMemoryAllocation) ? RLT2_ENOMEM : RLT2_ECUDA;
+    cuda_fail(err, what);
+    ctx_free(c);
+    return st;
+  };
+#define AL(ptr, cnt)                                      \
+  do {                                                    \
+    cudaError_t e2 = dalloc(&(ptr), (cnt));               \
+    if (e2 != cudaSuccess) return fail(e2, "cudaMalloc"); \
+  } while (0)
+  const size_t T = c->T, m = c->m, n2 = (size_t)nr * nr;
+  AL(c->d_cst, 1);
+  AL(c->Fr, n2);
+  AL(c->Dr, n2);
+  AL(c->bprime, n2);
+  AL(c->Chat, T);
+  AL(c->Dhat, (size_t)c->E);
+  AL(c->Theta, T);
+  AL(c->xi, T * m);
+  AL(c->psi, T * m);
+  AL(c->Delta, n2);
+  AL(c->gamma, n2 * (nr - 1));
+  AL(c->delta, n2 * (nr - 1));
+  AL(c->alpha, nr);
+  AL(c->beta, nr);
+  AL(c->pix, n2);
+  AL(c->piy, T);
+  AL(c->tterm, T);
+  AL(c->xval, 1);
+  AL(c->ring, kRing);
+  AL(c->xperm, nr);
+  AL(c->ubperm, nr);
+  AL(c->trips, c->ntrip);
+  AL(c->sc, 1);
+  AL(c->saterm, n2);
+  if (prm.variant == 1) AL(c->xcost, n2);
+  if (prm.half_z) AL(c->zmap, T / 2);
+  if (own_qap) {
+    AL(c->bqap, n2);
+    AL(c->d_cst_qap, 1);
+  }
+#undef AL
+  if (!c->xcost) c->xcost = c->bprime;  // S variant: the X-LAP reads b' itself
+  if (!c->bqap) c->bqap = c->bprime;
+  if (!c->d_cst_qap) c->d_cst_qap = c->d_cst;
+  if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return fail(e, "cudaStreamCreate");
+  std::vector<int> trips;
+  trips.reserve(c->ntrip);
+  for (int i = 0; i < nr; ++i)
+    for (int j = i + 1; j < nr; ++j)
+      for (int k = j + 1; k < nr; ++k) trips.push_back(i | (j << 8) | (k << 16));
+  // half-Z scheme: the tiles (i,p,j',q') with j > i, i.e. j' >= i; the others keep
+  // D^ = 0, Theta = 0 and zero duals forever
+  std::vector<int> up;
+  c->Tz = (long long)T;
+  if (prm.half_z) {
+    up.reserve(T / 2);
+    for (int i = 0; i < nr; ++i)
+      for (int p2 = 0; p2 < nr; ++p2)
+        for (int jj = i; jj < nr - 1; ++jj)
+          for (int qq = 0; qq < nr - 1; ++qq) up.push_back(((i * nr + p2) * (nr - 1) + jj) * (nr - 1) + qq);
+    c->Tz = (long long)up.size();
+  }
+  DevScalars init{};
+  init.ub = INFINITY;
+  init.best_lb = -INFINITY;
+  init.lb = -INFINITY;
+  cudaStream_t s = c->stream;
+  if ((e = cudaMemcpyAsync(c->trips, trips.data(), trips.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(c->sc, &init, sizeof init, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->Dhat, 0, sizeof(double) * (size_t)c->E, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->xi, 0, sizeof(double) * T * m, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->psi, 0, sizeof(double) * T * m, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->Theta, 0, sizeof(double) * T, s)) != cudaSuccess ||
+      (prm.half_z &&
+       (e = cudaMemcpyAsync(c->zmap, up.data(), up.size() * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess)) {
+    cudaStreamSynchronize(s);
+    return fail(e, "upload");
+  }
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e, "upload sync");  // host vectors outlive the copies
+  return RLT2_OK;
+}
+
 extern "C" rlt2_status rlt2_create(int n, const double* F, const double* D, const double* B, const int* partial,
                                    const rlt2_params* p, void* stream, rlt2_ctx** out) {
   if (!out) {
@@ -366,71 +556,17 @@ extern "C" rlt2_status rlt2_create(int n, const double* F, const double* D, cons
   c->T = (long long)nr * nr * (nr - 1) * (nr - 1);
   c->E = c->T * c->m * c->m;
   c->ntrip = nr * (nr - 1) * (nr - 2) / 6;
-  // memory admission
-  size_t need = sizeof(double) * ((size_t)c->E + 6 * (size_t)c->T + 2 * (size_t)c->T * c->m + 8 * (size_t)nr * nr +
-                                  2 * (size_t)nr * nr * nr + kRing) +
-                sizeof(int) * (size_t)(c->ntrip + nr) + (64u << 20);
-  size_t fr = 0, tot = 0;
-  cudaError_t e = cudaMemGetInfo(&fr, &tot);
-  if (e != cudaSuccess) {
-    delete c;
-    return cuda_fail(e, "cudaMemGetInfo");
-  }
-  if (need > fr) {
-    delete c;
-    set_error("rlt2_create: not enough free device memory");
-    return RLT2_ENOMEM;
-  }
-  rlt2_status st = RLT2_OK;
+  rlt2_status st = ctx_alloc(c, false);
+  if (st != RLT2_OK) return st;
   auto fail = [&](cudaError_t err, const char* what) {
     st = (err == cudaErrorMemoryAllocation) ? RLT2_ENOMEM : RLT2_ECUDA;
     cuda_fail(err, what);
     ctx_free(c);
     return st;
   };
-#define AL(ptr, cnt)                                   \
-  do {                                                 \
-    cudaError_t e2 = dalloc(&(ptr), (cnt));            \
-    if (e2 != cudaSuccess) return fail(e2, "cudaMalloc"); \
-  } while (0)
-  const size_t T = c->T, m = c->m, n2 = (size_t)nr * nr;
-  AL(c->d_cst, 1);
-  AL(c->Fr, n2);
-  AL(c->Dr, n2);
-  AL(c->bprime, n2);
-  AL(c->Chat, T);
-  AL(c->Dhat, (size_t)c->E);
-  AL(c->Theta, T);
-  AL(c->xi, T * m);
-  AL(c->psi, T * m);
-  AL(c->Delta, n2);
-  AL(c->gamma, n2 * (nr - 1));
-  AL(c->delta, n2 * (nr - 1));
-  AL(c->alpha, nr);
-  AL(c->beta, nr);
-  AL(c->pix, n2);
-  AL(c->piy, T);
-  AL(c->tterm, T);
-  AL(c->xval, 1);
-  AL(c->ring, kRing);
-  AL(c->xperm, nr);
-  AL(c->ubperm, nr);
-  AL(c->trips, c->ntrip);
-  AL(c->sc, 1);
-  AL(c->saterm, n2);
-  if (prm.variant == 1) AL(c->xcost, n2);
-  if (prm.half_z) AL(c->zmap, T / 2);
-#undef AL
-  if (!c->xcost) c->xcost = c->bprime;  // S variant: the X-LAP reads b' itself
-  if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
-    return fail(e, "cudaStreamCreate");
-
   // inputs to the device, then the setup kernels (step A0) on the stream
-  std::vector<int> trips;
-  trips.reserve(c->ntrip);
-  for (int i = 0; i < nr; ++i)
-    for (int j = i + 1; j < nr; ++j)
-      for (int k = j + 1; k < nr; ++k) trips.push_back(i | (j << 8) | (k << 16));
+  cudaError_t e = cudaSuccess;
+  const size_t n2 = (size_t)nr * nr;
   double *dF = nullptr, *dD = nullptr, *dB = nullptr;
   int* dint = nullptr;
   const int nfix = (int)c->fixf.size();
@@ -451,42 +587,13 @@ extern "C" rlt2_status rlt2_create(int n, const double* F, const double* D, cons
     cleanup_tmp();
     return fail(e, "cudaMalloc");
   }
-  DevScalars init{};
-  init.ub = INFINITY;
-  init.best_lb = -INFINITY;
-  init.lb = -INFINITY;
   if ((e = cudaMemcpyAsync(dF, F, nn * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (e = cudaMemcpyAsync(dD, D, nn * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
       (B && (e = cudaMemcpyAsync(dB, B, nn * 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) ||
-      (e = cudaMemcpyAsync(dint, ints.data(), ints.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(c->trips, trips.data(), trips.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(c->sc, &init, sizeof init, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(c->Dhat, 0, sizeof(double) * (size_t)c->E, s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(c->xi, 0, sizeof(double) * T * m, s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(c->psi, 0, sizeof(double) * T * m, s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(c->Theta, 0, sizeof(double) * T, s)) != cudaSuccess) {
+      (e = cudaMemcpyAsync(dint, ints.data(), ints.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
     cudaStreamSynchronize(s);
     cleanup_tmp();
     return fail(e, "upload");
-  }
-  // half-Z scheme: the tiles (i,p,j',q') with j > i, i.e. j' >= i; the others keep
-  // D^ = 0, Theta = 0 and zero duals forever
-  c->Tz = (long long)T;
-  if (prm.half_z) {
-    std::vector<int> up;
-    up.reserve(T / 2);
-    for (int i = 0; i < nr; ++i)
-      for (int p2 = 0; p2 < nr; ++p2)
-        for (int jj = i; jj < nr - 1; ++jj)
-          for (int qq = 0; qq < nr - 1; ++qq) up.push_back(((i * nr + p2) * (nr - 1) + jj) * (nr - 1) + qq);
-    c->Tz = (long long)up.size();
-    if ((e = cudaMemcpyAsync(c->zmap, up.data(), up.size() * sizeof(int), cudaMemcpyHostToDevice, s)) !=
-        cudaSuccess) {
-      cudaStreamSynchronize(s);
-      cleanup_tmp();
-      return fail(e, "upload");
-    }
-    cudaStreamSynchronize(s);  // the host vector must outlive the copy
   }
   const int* dfac = dint;
   const int* dloc = dint + nr;
@@ -505,6 +612,85 @@ extern "C" rlt2_status rlt2_create(int n, const double* F, const double* D, cons
   if ((e = cudaMemcpy(&c->cst_host, c->d_cst, 8, cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e, "cst");
   for (int mm2 : {nr - 2, nr - 1, nr})
     if ((e = prepare_lap(mm2)) != cudaSuccess) return fail(e, "prepare_lap");
+  *out = c;
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_create_child(rlt2_ctx* parent, int facility, int location, const rlt2_params* p,
+                                         rlt2_ctx** out) {
+  if (!out) {
+    set_error("rlt2_create_child: out is NULL");
+    return RLT2_EINVAL;
+  }
+  *out = nullptr;
+  if (!parent) {
+    set_error("rlt2_create_child: parent is NULL");
+    return RLT2_EINVAL;
+  }
+  if (parent->prm.variant != 0) {
+    set_error("rlt2_create_child: the parent must run the S variant (its costs carry the multipliers)");
+    return RLT2_EINVAL;
+  }
+  int f = -1, l = -1;
+  for (int a = 0; a < parent->n; ++a) {
+    if (parent->fac[a] == facility) f = a;
+    if (parent->loc[a] == location) l = a;
+  }
+  if (f < 0 || l < 0) {
+    set_error("rlt2_create_child: facility or location is not free in the parent");
+    return RLT2_EINVAL;
+  }
+  const int nr = parent->n - 1;
+  if (nr < 3) {
+    set_error("rlt2_create_child: the child's residual size would be below 3");
+    return RLT2_EINVAL;
+  }
+  rlt2_params prm = parent->prm;
+  if (p) prm = *p;
+  if (!params_valid(prm) || prm.variant != 0) {
+    set_error("rlt2_create_child: parameters out of range (S variant only)");
+    return RLT2_EINVAL;
+  }
+  rlt2_ctx* c = new rlt2_ctx();
+  c->n_full = parent->n_full;
+  c->prm = prm;
+  c->stream = parent->stream;
+  for (int a = 0; a < parent->n; ++a) {
+    if (a != f) c->fac.push_back(parent->fac[a]);
+    if (a != l) c->loc.push_back(parent->loc[a]);
+  }
+  c->fixf = parent->fixf;
+  c->fixl = parent->fixl;
+  c->fixf.push_back(facility);
+  c->fixl.push_back(location);
+  c->n = nr;
+  c->m = nr - 2;
+  c->T = (long long)nr * nr * (nr - 1) * (nr - 1);
+  c->E = c->T * c->m * c->m;
+  c->ntrip = nr * (nr - 1) * (nr - 2) / 6;
+  rlt2_status st = ctx_alloc(c, true);
+  if (st != RLT2_OK) return st;
+  cudaStream_t s = c->stream;
+  cudaError_t e;
+  {
+    const long long blocks = (c->E + 255) / 256;
+    k_child_z<<<(int)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(parent->n, f, l, parent->Dhat, c->Dhat, c->E);
+    const long long b2 = (c->T + 255) / 256;
+    k_child_yx<<<(int)(b2 < 4096 ? b2 : 4096), 256, 0, s>>>(
+        parent->n, f, l, parent->Dhat, parent->Chat, parent->bprime, parent->bqap, parent->Fr, parent->Dr,
+        parent->d_cst, parent->d_cst_qap, c->Chat, c->bprime, c->bqap, c->Fr, c->Dr, c->d_cst, c->d_cst_qap, c->T);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&c->sc->lb_base, c->d_cst, sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpy(&c->cst_host, c->d_cst, 8, cudaMemcpyDeviceToHost);
+  for (int mm2 : {nr - 2, nr - 1, nr})
+    if (e == cudaSuccess) e = prepare_lap(mm2);
+  if (e != cudaSuccess) {
+    rlt2_status r = cuda_fail(e, "rlt2_create_child");
+    ctx_free(c);
+    return r;
+  }
   *out = c;
   return RLT2_OK;
 }
@@ -590,6 +776,8 @@ FinArgs rlt2::make_fin(const IterView& v) {
   f.Fr = v.Fr;
   f.Dr = v.Dr;
   f.bprime = v.bprime;
+  f.bqap = v.bqap ? v.bqap : v.bprime;
+  f.cst_qap = v.cst_qap ? v.cst_qap : v.d_cst;
   f.ring = v.ring;
   f.min_gap = p.min_gap;
   f.ub_known = p.ub;

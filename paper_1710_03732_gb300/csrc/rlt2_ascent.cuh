@@ -317,6 +317,8 @@ struct FinArgs {
   const double* Fr;
   const double* Dr;
   const double* bprime;
+  const double* bqap;     // QAP linear costs (b' without multipliers) for the upper bound
+  const double* cst_qap;  // QAP constant of the fixed facilities
   double* ring;
   double min_gap, ub_known, feas_tol, stall_tol;
   int stall_window;
@@ -336,7 +338,7 @@ __device__ __forceinline__ void finalize_block(const FinArgs& a) {
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e - i * n;
     const int si = a.xperm[i], sj = a.xperm[j];
-    part += (i == j) ? a.bprime[i * n + si] : a.Fr[i * n + j] * a.Dr[si * n + sj];
+    part += (i == j) ? a.bqap[i * n + si] : a.Fr[i * n + j] * a.Dr[si * n + sj];
   }
   red[tid] = part;
   __syncthreads();
@@ -344,7 +346,7 @@ __device__ __forceinline__ void finalize_block(const FinArgs& a) {
     if (tid < s) red[tid] += red[tid + s];
     __syncthreads();
   }
-  const double ub = *a.cst + red[0];
+  const double ub = *a.cst_qap + red[0];
   // feasibility check: every y and z built from the X primal has zero slack (Eq. 2.19)
   if (a.feas_tol > 0.0) {
     const double tol = a.feas_tol * fmax(1.0, fabs(lb));

@@ -103,6 +103,8 @@ struct IterView {
   int sa_count;
   const int* zmap;  // half-Z scheme: the tiles with first facility < second facility
   long long Tz;     // number of Z-LAPs solved (T, or T/2 with the half scheme)
+  const double* bqap;     // nullable: QAP linear costs for upper bounds (default bprime)
+  const double* cst_qap;  // nullable: QAP constant for upper bounds (default d_cst)
   int *xperm, *ubperm, *trips;
   DevScalars* sc;
 };

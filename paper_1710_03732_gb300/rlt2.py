@@ -30,6 +30,12 @@ class rlt2_params(ctypes.Structure):
                 ("half_z", ctypes.c_int)]
 
 
+class rlt2_bnb_options(ctypes.Structure):
+    _fields_ = [("order_rule", ctypes.c_int), ("iters_root", ctypes.c_int), ("iters_node", ctypes.c_int),
+                ("warm_depth", ctypes.c_int), ("max_states", ctypes.c_int), ("max_nodes", ctypes.c_longlong),
+                ("time_limit_s", ctypes.c_double), ("ub0", ctypes.c_double), ("abs_tol", ctypes.c_double)]
+
+
 class Rlt2Error(RuntimeError):
     def __init__(self, status: int, where: str, detail: str):
         super().__init__(f"{where}: status {status} ({detail})")
@@ -47,7 +53,8 @@ EXPORTS = ["rlt2_params_default", "rlt2_create", "rlt2_iterate", "rlt2_iterate_a
            "rlt2_iterate_noalloc", "rlt2_mlp_create", "rlt2_mlp_destroy", "rlt2_mlp_get_weights",
            "rlt2_mlp_set_weights", "rlt2_mlp_add_samples", "rlt2_mlp_samples", "rlt2_mlp_clear_samples",
            "rlt2_mlp_grad", "rlt2_mlp_fit", "rlt2_mlp_set_gate", "rlt2_mlp_predict", "rlt2_set_mlp",
-           "rlt2_export_xstate", "rlt2_import_xstate", "rlt2_set_sa", "rlt2_strerror", "rlt2_last_error"]
+           "rlt2_export_xstate", "rlt2_import_xstate", "rlt2_set_sa", "rlt2_create_child", "rlt2_bnb_options_default",
+           "rlt2_bnb_solve", "rlt2_strerror", "rlt2_last_error"]
 
 
 def lib():
@@ -72,6 +79,11 @@ def lib():
     L.rlt2_export_xstate.argtypes = [_vp, _dp, _dp]
     L.rlt2_import_xstate.argtypes = [_vp, _dp, ctypes.c_double]
     L.rlt2_set_sa.argtypes = [_vp, ctypes.c_int, _dp, _dp, _dp]
+    L.rlt2_create_child.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(rlt2_params), ctypes.POINTER(_vp)]
+    L.rlt2_bnb_options_default.argtypes = [ctypes.POINTER(rlt2_bnb_options)]
+    L.rlt2_bnb_options_default.restype = None
+    L.rlt2_bnb_solve.argtypes = [ctypes.c_int, _dp, _dp, _dp, ctypes.POINTER(rlt2_params),
+                                 ctypes.POINTER(rlt2_bnb_options), _dp, _ip, _dp, ctypes.POINTER(ctypes.c_longlong), _vp]
     L.rlt2_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_longlong)]
     L.rlt2_sizes.argtypes = [_vp, _ip, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), _dp]
     L.rlt2_set_timing.argtypes = [_vp, ctypes.c_int]
@@ -100,7 +112,7 @@ def lib():
     L.rlt2_strerror.restype = ctypes.c_char_p
     L.rlt2_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("rlt2_params_default", "rlt2_strerror", "rlt2_last_error"):
+        if name not in ("rlt2_params_default", "rlt2_bnb_options_default", "rlt2_strerror", "rlt2_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -263,6 +275,39 @@ def rlt2_set_sa(ctx: int, kappa_fac, kappa_loc, neglog_u):
     count = int(ng.shape[0])
     _check(lib().rlt2_set_sa(ctx, count, _host_d(kf) if count else None, _host_d(kl) if count else None,
                              _host_d(ng) if count else None), "rlt2_set_sa")
+
+
+def rlt2_create_child(ctx: int, facility: int, location: int, prm: Optional[rlt2_params] = None) -> int:
+    out = _vp()
+    _check(lib().rlt2_create_child(ctx, int(facility), int(location), None if prm is None else ctypes.byref(prm),
+                                   ctypes.byref(out)), "rlt2_create_child")
+    return out.value
+
+
+def bnb_options(**kw) -> rlt2_bnb_options:
+    o = rlt2_bnb_options()
+    lib().rlt2_bnb_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def rlt2_bnb_solve(F, D, B=None, prm: Optional[rlt2_params] = None, opts: Optional[rlt2_bnb_options] = None,
+                   stream=None):
+    """Branch and bound to optimality; returns (best value, permutation, root bound,
+    stats {bounded, branched, enumerated, iterations, max_depth, proven, warm, cold})."""
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    B = None if B is None else np.ascontiguousarray(B, dtype=np.float64)
+    n = F.shape[0]
+    best, rlb = ctypes.c_double(), ctypes.c_double()
+    perm = np.zeros(n, dtype=np.int32)
+    st = (ctypes.c_longlong * 8)()
+    _check(lib().rlt2_bnb_solve(n, _host_d(F), _host_d(D), _host_d(B), None if prm is None else ctypes.byref(prm),
+                                None if opts is None else ctypes.byref(opts), ctypes.byref(best),
+                                perm.ctypes.data_as(_ip), ctypes.byref(rlb), st, _stream(stream)), "rlt2_bnb_solve")
+    keys = ["bounded", "branched", "enumerated", "iterations", "max_depth", "proven", "warm", "cold"]
+    return best.value, perm, rlb.value, dict(zip(keys, list(st)))
 
 
 def rlt2_destroy(ctx: int):
@@ -438,6 +483,14 @@ class Context:
     def import_state(self, Dhat, Chat):
         rlt2_import_state(self.ctx, np.ascontiguousarray(Dhat, dtype=np.float64),
                           np.ascontiguousarray(Chat, dtype=np.float64))
+
+    def child(self, facility: int, location: int, prm: Optional[rlt2_params] = None) -> "Context":
+        """Branch-and-bound child starting from this context's multipliers."""
+        c = Context.__new__(Context)
+        c.n_full = self.n_full
+        c.ctx = rlt2_create_child(self.ctx, facility, location, prm)
+        c.n, c.T, c.E, c.const = rlt2_sizes(c.ctx)
+        return c
 
     def export_xstate(self):
         """(incremental x costs, bound base) of an F-variant checkpoint."""
