@@ -298,6 +298,27 @@ def variant_runs(R, torch, iters: int = 300):
     return res
 
 
+def bnb_runs(R, torch):
+    """rlt2_bnb_solve on the n = 12 grid workload and on n = 12 and n = 14
+    random instances (F 0..9 at density 0.7, asymmetric, with B; seeds 70, 71):
+    seconds, nodes, ascent iterations, proven optimality; warm (parent
+    multipliers) against cold children; each capped at 60 s."""
+    res = {}
+    cases = [("n12_grid3x4", I.config(2)),
+             ("n12_random_seed70", I.random_instance(12, 70, with_b=True, asymmetric=True)),
+             ("n14_random_seed71", I.random_instance(14, 71, with_b=True, asymmetric=True))]
+    for name, inst in cases:
+        for wd, tag in ((64, "warm"), (-1, "cold")):
+            opts = R.bnb_options(iters_root=300, iters_node=100, warm_depth=wd, time_limit_s=60.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            best, _, rlb, st = R.rlt2_bnb_solve(inst.F, inst.D, inst.B, prm=R.params(warm=1, stall_window=25),
+                                                opts=opts)
+            dt = time.perf_counter() - t0
+            res[f"{name}_{tag}"] = dict(best=best, root_lb=rlb, seconds=dt, **{k: int(v) for k, v in st.items()})
+    return res
+
+
 def extra_workloads(R, torch):
     """The other configurations, measured after the headline timed region:
     config 4 (64 branch-and-bound nodes of a 2x11-grid QAP with n = 22, depths
@@ -350,6 +371,8 @@ def extra_workloads(R, torch):
     out["config5_n30"] = c5
     # Section 3.4 variants on the headline workload: speed and bound reached
     out["variants_n20"] = variant_runs(R, torch)
+    # branch and bound to optimality (Section 4)
+    out["branch_and_bound"] = bnb_runs(R, torch)
     # learned start on the headline workload: augmenting searches, identical bounds
     if mlp is not None:
         inst = I.config(CFG)
