@@ -488,8 +488,10 @@ def main():
     E = T * m * m
     # FP64 ops per z entry with kz = 1 and equal phi: 2 (pi_z) + 1 (s) + 5/6 (class
     # sum) + 2 (S - s, D - s) + 1 (fma)
-    mz_ops = E * (6 + 5.0 / 6.0)
-    mz_bytes = E * 16 + 2 * T * m * 8 + T * 8  # D^ read + write, xi/psi and tile terms read once
+    # folded uniform z move (kz = 1, equal phi): per entry 2 for s = (D - xi) - psi',
+    # 5/6 for the class sum S, 2 fused multiply-adds for D' = fma(-(1+phi), s, fma(phi, S, D))
+    mz_ops = E * (4 + 5.0 / 6.0)
+    mz_bytes = E * 16 + 2 * T * m * 8  # D^ read + write, xi and psi' read once
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     traffic = profiled_traffic("lap_z", "n20")

@@ -38,7 +38,9 @@
  *     D^'(a) = (D^(a) - s(a)) + sum over the five partners b of phi(b->a)*s(b),
  *     the partner terms added one fused multiply-add (C99 fma) at a time; with
  *     all phi equal, D^'(a) = fma(phi, S - s(a), D^(a) - s(a)), S = sum of the
- *     class's six s in member order;
+ *     class's six s in member order; with all phi equal and kz = 1 (the
+ *     default) the same formula is regrouped as
+ *     s(a) = (D^ - xi_k') - (psi_r' - ty), D^'(a) = fma(-(1+phi), s, fma(phi, S, D^));
  *   - an LAP optimum is summed as a pairwise tree;
  *   - y move (Eq. 2.21): C^'_ijpq = (C^_ijpq - phi_y*pi_y(ijpq)) + phi_y*pi_y(jiqp).
  * Variants (Section 3.4):
@@ -529,6 +531,8 @@ void or_redistribute_z_v(int n, const double* prm, int variant, const double* sa
     for (int l = 0; l < 5; l++) gives[a][pmap[a][l]] = phi[l];
   }
   int uniform = phi[0] == phi[1] && phi[0] == phi[2] && phi[0] == phi[3] && phi[0] == phi[4];
+  int folded = variant == 0 && uniform && kz == 1.0;
+  double c1 = -(1.0 + phi[0]);
   int ntrip = 0;
   int(*trip)[3] = (int(*)[3])malloc(sizeof(int[3]) * (size_t)(n * n * n / 6 + 1));
   for (int i = 0; i < n; i++)
@@ -554,6 +558,26 @@ void or_redistribute_z_v(int n, const double* prm, int variant, const double* sa
           int l3[3] = {p, q, r};
           double s[6], base[6];
           long long idx[6];
+          if (folded) {
+            /* kz = 1, all phi equal, S variant: the same pool regrouped,
+             * s = (D^ - xi_k') - (psi_r' - ty) and D^' = (D^ + phi S) - (1 + phi) s */
+            double Dv[6], S;
+            for (int a = 0; a < 6; a++) {
+              int fi = f[M[a][0]], fj = f[M[a][1]], fk = f[M[a][2]];
+              int li = l3[M[a][0]], lj = l3[M[a][1]], lk = l3[M[a][2]];
+              long long t = tile_of(n, fi, li, fj, lj);
+              double ty = cy * piy[t] + cx * pix[fi * n + li];
+              if (sa) ty = ty + sa[fi * n + li];
+              idx[a] = zidx(n, fi, fj, fk, li, lj, lk);
+              Dv[a] = Dhat[idx[a]];
+              double psi_f = psi[t * (n - 2) + cmp2(lk, li, lj)] - ty;
+              s[a] = (Dv[a] - xi[t * (n - 2) + cmp2(fk, fi, fj)]) - psi_f;
+            }
+            S = s[0];
+            for (int b = 1; b < 6; b++) S = S + s[b];
+            for (int a = 0; a < 6; a++) Dhat[idx[a]] = fma(c1, s[a], fma(phi[0], S, Dv[a]));
+            continue;
+          }
           for (int a = 0; a < 6; a++) {
             int fi = f[M[a][0]], fj = f[M[a][1]], fk = f[M[a][2]];
             int li = l3[M[a][0]], lj = l3[M[a][1]], lk = l3[M[a][2]];

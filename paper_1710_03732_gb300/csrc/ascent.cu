@@ -707,6 +707,8 @@ MoveYArgs rlt2::make_move_y(const IterView& v) {
   a.fast = p.variant == 1;
   a.half = p.half_z;
   a.cxy = p.kx / (double)(n - 1);
+  a.shift_psi = make_move_z(v).folded;
+  a.psi = v.psi;
   a.keep_y = (1.0 - p.ky) - p.phi_y;
   a.keep_x = 1.0 - p.kx;
   a.piy = v.piy;
@@ -750,6 +752,8 @@ MoveZArgs rlt2::make_move_z(const IterView& v) {
                 p.phi_z[0] == p.phi_z[4]);
   mz.fast = p.variant == 1;
   mz.half = p.half_z;
+  mz.folded = p.variant == 0 && !p.half_z && mz.kz_one && mz.uniform;
+  mz.c1 = -(1.0 + p.phi_z[0]);
   mz.saterm = v.saterm;
   mz.Dhat = v.Dhat;
   mz.xi = v.xi;

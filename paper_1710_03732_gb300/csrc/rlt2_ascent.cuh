@@ -29,6 +29,8 @@ struct MoveYArgs {
   int half;              // half-Z scheme (see move_y_range)
   double keep_y, keep_x;  // (1 - ky) - phi_y and 1 - kx (F variant)
   double cxy;             // half-Z scheme: kx / (n-1), Type 3 on the y level for the lower rows
+  int shift_psi;          // folded z move: psi <- psi - tile term, in place (psi is rewritten by the next Z solve)
+  double* psi;
   const double* piy;
   const double* pix;
   double* Chat;
@@ -79,6 +81,10 @@ __device__ __forceinline__ void move_y_range(const MoveYArgs& a, long long start
     double ty = dadd_(dmul_(a.cy, pyz), dmul_(a.cx, a.pix[ip]));
     if (on) ty = dadd_(ty, dadd_(dmul_(kf[i], g), dmul_(kl[p], g)));
     a.tterm[t] = ty;
+    if (a.shift_psi) {
+      double* ps = a.psi + t * (n - 2);
+      for (int c = 0; c < n - 2; ++c) ps[c] = dsub_(ps[c], ty);
+    }
     if (a.half) {
       // y move of Eq. 2.21, then Type 3 on the y level: a lower y (i > j) gives
       // kx pi_x(ip) / (n-1) to its mirror (the lower z stay at zero)
@@ -121,6 +127,9 @@ struct MoveZArgs {
   int uniform;  // all phi equal: member b gets phi * (S - s_b)
   int fast;     // F variant: the member keeps fma(-kz, pi_z, pi_z) (minus a Type 4 amount)
   int half;     // half-Z scheme: only the three upper members move (lower ones stay 0)
+  int folded;   // S, kz = 1, all phi equal: psi holds psi - tile term, s = (D - xi) - psi,
+                // D' = fma(c1, s, fma(phi, S, D)) with c1 = -(1 + phi)
+  double c1;
   const double* saterm;  // n*n Type 4 amounts (F variant, when sc->sa_on)
   double* Dhat;
   const double* xi;
@@ -200,6 +209,27 @@ __device__ __forceinline__ void move_z_block(const MoveZArgs& a, int blk) {
     const int L3[3] = {p, q, r};
     double s[6], base[6];
     long long idx[6];
+    if (a.folded) {
+      // the uniform pool of Eq. 2.20-2.23 with kz = 1, regrouped:
+      // D' = D - s + phi (S - s) = (D + phi S) - (1 + phi) s
+      double Dv[6];
+#pragma unroll
+      for (int b = 0; b < 6; ++b) {
+        const int f0 = F3[kOrd[b][0]], f1 = F3[kOrd[b][1]], f2 = F3[kOrd[b][2]];
+        const int l0 = L3[kOrd[b][0]], l1 = L3[kOrd[b][1]], l2 = L3[kOrd[b][2]];
+        const long long t = ((long long)(f0 * n + l0) * n1 + (f1 - (f1 > f0))) * n1 + (l1 - (l1 > l0));
+        const int kr = f2 - (f2 > f0) - (f2 > f1), cc = l2 - (l2 > l0) - (l2 > l1);
+        idx[b] = t * mm + kr * m + cc;
+        Dv[b] = a.Dhat[idx[b]];
+        s[b] = dsub_(dsub_(Dv[b], __ldg(a.xi + t * m + kr)), __ldg(a.psi + t * m + cc));
+      }
+      double S = s[0];
+#pragma unroll
+      for (int b = 1; b < 6; ++b) S = dadd_(S, s[b]);
+#pragma unroll
+      for (int b = 0; b < 6; ++b) a.Dhat[idx[b]] = __fma_rn(a.c1, s[b], __fma_rn(a.w[0], S, Dv[b]));
+      continue;
+    }
 #pragma unroll
     for (int b = 0; b < 6; ++b) {
       const int f0 = F3[kOrd[b][0]], f1 = F3[kOrd[b][1]], f2 = F3[kOrd[b][2]];
