@@ -521,7 +521,8 @@ def main():
                        "z_aug_per_lap": cold["stats"][1] / (steps * T)},
         "warm": {"lb_last": warm["lb"], "z_aug_per_lap": warm["stats"][1] / (steps * T),
                  "same_bound_as_cold_rel": abs(warm["lb"] - cold["lb"]) / abs(cold["lb"])},
-        "kernels_ms_per_launch": {k: v[0] / max(v[1], 1) for k, v in warm["kt"].items()},
+        "kernels_ms_per_iteration": {k: v[0] / steps for k, v in warm["kt"].items()},
+        "kernel_launches_per_iteration": {k: v[1] / steps for k, v in warm["kt"].items()},
         "roofline": {"bound": "alu", "kernel": "lap_z", "achieved": ach_lz, "peak": FP64_PEAK_GOPS,
                      "unit": FP64_UNIT, "frac": ach_lz / FP64_PEAK_GOPS, "traffic": traffic,
                      "algorithmic_flops_per_launch": fl_lz, "avg_launch_ms": avg_lz,

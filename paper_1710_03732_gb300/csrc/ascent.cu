@@ -95,6 +95,11 @@ __global__ void k_move_y(MoveYArgs a) {
   move_y_range(a, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
+__global__ void k_shift_psi(MoveYArgs a) {
+  if (!a.sc->have_snap || a.sc->done) return;
+  shift_psi_range(a, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
 __global__ void __launch_bounds__(512) k_move_z(MoveZArgs a) {
   if (!a.sc->have_snap || a.sc->done) return;
   move_z_block(a, blockIdx.x);
@@ -795,7 +800,10 @@ FinArgs rlt2::make_fin(const IterView& v) {
 
 // Enqueue one iteration (six kernels) on stream s.  With ev != nullptr, the 12
 // events ev[2k], ev[2k+1] bracket kernel k.
-cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent_t* ev) {
+cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent_t* ev, int* launched) {
+  auto count = [&](int k, int nk) {
+    if (launched) launched[k] += nk;
+  };
   const int n = v.n, m = v.m;
   const long long T = v.T;
   const rlt2_params& p = v.prm;
@@ -808,8 +816,14 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   // 1) y move (and F's x move) + tile terms
   if ((e = rec(0, 0)) != cudaSuccess) return e;
   {
+    const MoveYArgs my = make_move_y(v);
     const long long blocks = (T + 255) / 256;
-    k_move_y<<<(int)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(make_move_y(v));
+    k_move_y<<<(int)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(my);
+    count(0, my.shift_psi ? 2 : 1);
+    if (my.shift_psi) {
+      const long long b2 = (T * m + 255) / 256;
+      k_shift_psi<<<(int)(b2 < 16384 ? b2 : 16384), 256, 0, s>>>(my);
+    }
   }
   if ((e = cudaGetLastError()) != cudaSuccess || (e = rec(0, 1)) != cudaSuccess) return e;
   // 2) z move
@@ -817,6 +831,7 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   if ((e = rec(1, 0)) != cudaSuccess) return e;
   // one thread per (q, r) class of the block's (triple, p): round to whole warps
   k_move_z<<<v.ntrip * n, move_z_threads(n), 0, s>>>(mz);
+  count(1, 1);
   if ((e = cudaGetLastError()) != cudaSuccess || (e = rec(1, 1)) != cudaSuccess) return e;
   // 3) Z stage
   LapArgs z{};
@@ -828,7 +843,9 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   z.warm_gate = &v.sc->have_snap;
   if (p.warm == 2 && v.mlp && v.u0buf) {
     // learned start from the tile and the row's previous dual (zero before the first solve)
-    if ((e = mlp_predict_enqueue(v.mlp, T, m, v.Dhat, v.xi, v.u0buf, s)) != cudaSuccess) return e;
+    if ((e = mlp_predict_enqueue(v.mlp, T, m, v.Dhat, v.xi, v.u0buf, s, launched ? launched + 2 : nullptr)) !=
+        cudaSuccess)
+      return e;
     z.u0 = v.u0buf;
     z.warm_gate = nullptr;
   }
@@ -840,11 +857,13 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   z.skip = done;
   if ((e = rec(2, 0)) != cudaSuccess) return e;
   if ((e = launch_lap(z, s)) != cudaSuccess) return e;
+  count(2, 1);
   if ((e = rec(2, 1)) != cudaSuccess) return e;
   // 3b) two-phase Z solve: move slack onto the zero-slack members, solve again
   if ((e = rec(6, 0)) != cudaSuccess) return e;
   if (p.two_phase) {
     k_phase2<<<v.ntrip * n, move_z_threads(n), 0, s>>>(make_phase2(v));
+    count(6, 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if ((e = rec(6, 1)) != cudaSuccess || (e = rec(7, 0)) != cudaSuccess) return e;
@@ -853,6 +872,7 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
     z2.u0 = p.warm >= 1 ? v.xi : nullptr;  // from the first phase's row duals
     z2.warm_gate = nullptr;
     if ((e = launch_lap(z2, s)) != cudaSuccess) return e;
+    count(7, 1);
   }
   if ((e = rec(7, 1)) != cudaSuccess) return e;
   // 4) Y stage on C^ + Theta, writes pi_y
@@ -872,6 +892,7 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   y.skip = done;
   if ((e = rec(3, 0)) != cudaSuccess) return e;
   if ((e = launch_lap(y, s)) != cudaSuccess) return e;
+  count(3, 1);
   if ((e = rec(3, 1)) != cudaSuccess) return e;
   // 5) X stage on b' + Delta, writes pi_x
   LapArgs x{};
@@ -891,17 +912,19 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   x.skip = done;
   if ((e = rec(4, 0)) != cudaSuccess) return e;
   if ((e = launch_lap(x, s)) != cudaSuccess) return e;
+  count(4, 1);
   if ((e = rec(4, 1)) != cudaSuccess) return e;
   // 6) finalize
   const FinArgs f = make_fin(v);
   if ((e = rec(5, 0)) != cudaSuccess) return e;
   k_finalize<<<1, 256, 0, s>>>(f);
+  count(5, 1);
   if ((e = cudaGetLastError()) != cudaSuccess || (e = rec(5, 1)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
-static cudaError_t enqueue_iteration_ctx(rlt2_ctx* c, cudaStream_t s, int ev_base) {
-  return enqueue_iteration(view_of(c), s, ev_base < 0 ? nullptr : c->ev.data() + ev_base);
+static cudaError_t enqueue_iteration_ctx(rlt2_ctx* c, cudaStream_t s, int ev_base, int* launched = nullptr) {
+  return enqueue_iteration(view_of(c), s, ev_base < 0 ? nullptr : c->ev.data() + ev_base, launched);
 }
 
 static rlt2_status build_graph(rlt2_ctx* c) {
@@ -935,10 +958,12 @@ static rlt2_status enqueue_many(rlt2_ctx* c, int iters) {
     // the event pool was created by rlt2_set_timing; reuse it every kEvChunk iterations
     for (int base = 0; base < iters; base += kEvChunk) {
       const int cnt = (iters - base) < kEvChunk ? (iters - base) : kEvChunk;
+      int launched[kKinds] = {};
       for (int it = 0; it < cnt; ++it) {
-        cudaError_t e = enqueue_iteration_ctx(c, c->stream, it * kKinds * 2);
+        cudaError_t e = enqueue_iteration_ctx(c, c->stream, it * kKinds * 2, launched);
         if (e != cudaSuccess) return cuda_fail(e, "enqueue_iteration");
       }
+      for (int k = 0; k < kKinds; ++k) c->kcount[k] += launched[k];
       // finalize (kind 5) is the last interval recorded in an iteration
       CK(cudaEventSynchronize(c->ev[(cnt - 1) * kKinds * 2 + 2 * 5 + 1]));
       for (int it = 0; it < cnt; ++it)
@@ -946,7 +971,6 @@ static rlt2_status enqueue_many(rlt2_ctx* c, int iters) {
           float ms = 0.f;
           CK(cudaEventElapsedTime(&ms, c->ev[it * kKinds * 2 + 2 * k], c->ev[it * kKinds * 2 + 2 * k + 1]));
           c->kms[k] += ms;
-          c->kcount[k] += 1;
         }
     }
     return RLT2_OK;

@@ -523,7 +523,7 @@ cudaError_t ensure_dataset(rlt2_mlp* m, long long need) {
 namespace rlt2 {
 // Predict Z-LAP row duals u0 (FP64) for ntiles tiles of size m; prev_u nullable.
 cudaError_t mlp_predict_enqueue(rlt2_mlp* m, long long ntiles, int mz, const double* tiles, const double* prev_u,
-                                double* u0, cudaStream_t s) {
+                                double* u0, cudaStream_t s, int* launched) {
   cudaError_t e;
   const long long tiles_per_chunk = std::max<long long>(1, kChunk / mz);
   for (long long t0 = 0; t0 < ntiles; t0 += tiles_per_chunk) {
@@ -539,6 +539,7 @@ cudaError_t mlp_predict_enqueue(rlt2_mlp* m, long long ntiles, int mz, const dou
     k_u0<<<(int)std::min<long long>(4096, (rows + 255) / 256), 256, 0, s>>>(
         rows, mz, m->out, m->scale, prev_u ? prev_u + t0 * mz : nullptr, m->gate, u0 + t0 * mz);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (launched) *launched += 5;  // features, two GEMMs, output layer, starts
   }
   return cudaSuccess;
 }

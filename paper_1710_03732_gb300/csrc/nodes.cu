@@ -40,6 +40,12 @@ __global__ void __launch_bounds__(512) k_move_z_nodes(const MoveZArgs* nodes, co
   move_z_block(a, blockIdx.x);
 }
 
+__global__ void k_shift_psi_nodes(const MoveYArgs* nodes) {
+  const MoveYArgs a = nodes[blockIdx.y];
+  if (!a.shift_psi || !a.sc->have_snap || a.sc->done) return;
+  shift_psi_range(a, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
 __global__ void __launch_bounds__(512) k_phase2_nodes(const Phase2Args* nodes, const int* nblocks) {
   if ((int)blockIdx.x >= nblocks[blockIdx.y]) return;
   const Phase2Args a = nodes[blockIdx.y];
@@ -163,6 +169,9 @@ cudaError_t enqueue_wave_iteration(const Wave& w, const WaveDev& d, int dual_mod
   {
     const int bx = std::max(1, std::min(1024, (w.max_T + 255) / 256));
     k_move_y_nodes<<<dim3(bx, w.nn), 256, 0, s>>>(d.my);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int bx2 = std::max(1, std::min(4096, (int)(((long long)w.max_T * (w.max_n - 2) + 255) / 256)));
+    k_shift_psi_nodes<<<dim3(bx2, w.nn), 256, 0, s>>>(d.my);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   k_move_z_nodes<<<dim3(w.max_blocks, w.nn), move_z_threads(w.max_n), 0, s>>>(d.mz, d.mz_blocks);

@@ -81,10 +81,6 @@ __device__ __forceinline__ void move_y_range(const MoveYArgs& a, long long start
     double ty = dadd_(dmul_(a.cy, pyz), dmul_(a.cx, a.pix[ip]));
     if (on) ty = dadd_(ty, dadd_(dmul_(kf[i], g), dmul_(kl[p], g)));
     a.tterm[t] = ty;
-    if (a.shift_psi) {
-      double* ps = a.psi + t * (n - 2);
-      for (int c = 0; c < n - 2; ++c) ps[c] = dsub_(ps[c], ty);
-    }
     if (a.half) {
       // y move of Eq. 2.21, then Type 3 on the y level: a lower y (i > j) gives
       // kx pi_x(ip) / (n-1) to its mirror (the lower z stay at zero)
@@ -104,6 +100,14 @@ __device__ __forceinline__ void move_y_range(const MoveYArgs& a, long long start
     a.sc->sa_on = on ? 1 : 0;
     if (a.fast) a.sc->lb_base = a.sc->lb;
   }
+}
+
+// Folded z move: psi <- psi - tile term, one element per thread (coalesced);
+// runs after move_y_range has written the tile terms.
+__device__ __forceinline__ void shift_psi_range(const MoveYArgs& a, long long start, long long stride) {
+  const int m = a.n - 2;
+  const long long Tm = a.T * m;
+  for (long long e = start; e < Tm; e += stride) a.psi[e] = dsub_(a.psi[e], a.tterm[e / m]);
 }
 
 // The six members of a class {(i,p),(j,q),(k,r)} are the position orders of the

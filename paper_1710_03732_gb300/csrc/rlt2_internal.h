@@ -113,11 +113,12 @@ struct IterView {
 cudaError_t enqueue_setup(const IterView& v, int n_full, const double* dF, const double* dD, const double* dB,
                           const int* dfac, const int* dloc, const int* dfixf, const int* dfixl, int nfix,
                           cudaStream_t s);
-cudaError_t enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent_t* ev);
+// launched (nullable, kKinds entries): incremented by the kernels launched per timing kind.
+cudaError_t enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent_t* ev, int* launched = nullptr);
 
 // Predicted Z-LAP row duals for ntiles tiles of size mz (mlp.cu).
 cudaError_t mlp_predict_enqueue(rlt2_mlp* m, long long ntiles, int mz, const double* tiles, const double* prev_u,
-                                double* u0, cudaStream_t s);
+                                double* u0, cudaStream_t s, int* launched = nullptr);
 
 // Parameter validation shared by the entry points.
 bool params_valid(const rlt2_params& p);
