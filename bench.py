@@ -390,6 +390,23 @@ def extra_workloads(R, torch):
     return out
 
 
+def rank_max(x: float, dist, device: str) -> float:
+    """Max of x over all ranks (x itself on one process): the timed region of a
+    replicated run ends when the slowest rank ends."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, slowest_ms: float) -> float:
+    """Replicas: every rank processes the same units; the whole job processed
+    world * units in the slowest rank's time."""
+    return world * units_per_rank / (slowest_ms / 1000.0)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -452,11 +469,7 @@ def main():
     barrier()
 
     def per_rank_max(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(x, dist, "cuda")
 
     warm_ms = per_rank_max(warm["ms"])
     cold_ms = per_rank_max(cold["ms"])
@@ -499,7 +512,7 @@ def main():
     launches = sum(v[1] for v in warm["kt"].values())
     line = {
         "metric": METRIC,
-        "value": world * steps / (warm_ms / 1000.0),
+        "value": whole_job_rate(world, steps, warm_ms),
         "unit": "iters/s",
         "n_gpus": world,
         "steps": steps,
@@ -513,10 +526,10 @@ def main():
         "config": {"workload": WORKLOAD, "n": n, "z_laps_per_iter": T, "z_lap_size": m, "z_entries": E,
                    "warm_start": "previous-iteration Z duals", "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (374 MB z array), no flush"},
-        "laps_per_s": {"warm": world * steps * T / (warm_ms / 1000.0),
-                       "cold": world * steps * T / (cold_ms / 1000.0),
+        "laps_per_s": {"warm": whole_job_rate(world, steps * T, warm_ms),
+                       "cold": whole_job_rate(world, steps * T, cold_ms),
                        "z_stage_only_warm": T / (avg_lz * 1e-3)},
-        "plain_cold": {"value": world * steps / (cold_ms / 1000.0), "unit": "iters/s",
+        "plain_cold": {"value": whole_job_rate(world, steps, cold_ms), "unit": "iters/s",
                        "ms_per_step": cold_ms / steps, "lb_last": cold["lb"],
                        "z_aug_per_lap": cold["stats"][1] / (steps * T)},
         "warm": {"lb_last": warm["lb"], "z_aug_per_lap": warm["stats"][1] / (steps * T),
@@ -533,7 +546,7 @@ def main():
                             "hbm_frac_of_measured": (mz_bytes / (mz_ms * 1e-3) / 1e9 / hbm) if hbm else None,
                             "avg_launch_ms": mz_ms},
         "cpu_baseline": cpu,
-        "e2e": {"value": world * got / e2e_s, "unit": "iters/s",
+        "e2e": {"value": whole_job_rate(world, got, e2e_s * 1000.0), "unit": "iters/s",
                 "h2d_bytes_per_step": 3 * 20 * 20 * 8 / steps, "d2h_bytes_per_step": 8,
                 "note": "rlt2_create from host F,D,B + rlt2_iterate(K) with host bound history + destroy"},
         "gpu_launches": int(launches),
