@@ -117,3 +117,13 @@ def test_child_rejections(R):
         ctx.iterate(2)
         with pytest.raises(R.Rlt2Error):
             ctx.child(0, 3)
+
+
+def test_bnb_with_half_z_scheme(R):
+    """Children of a half-Z-scheme parent inherit its multipliers (the lower-order
+    z stay 0 under the renumbering, which keeps the index order); the search
+    still returns the brute-force optimum."""
+    for inst in (I.config(1), I.random_instance(9, 66, with_b=True, asymmetric=True)):
+        opts = R.bnb_options(iters_root=40, iters_node=20)
+        best, perm, rlb, st = R.rlt2_bnb_solve(inst.F, inst.D, inst.B, prm=R.half_z_params(warm=1), opts=opts)
+        assert best == _opt(inst) and st["proven"] == 1
