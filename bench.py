@@ -87,7 +87,10 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to $RLT2_CLOCKS_DIR (kept) or a temporary folder
+        import tempfile
+        folder = os.environ.get("RLT2_CLOCKS_DIR") or tempfile.mkdtemp(prefix="rlt2_clocks_")
+        self.path = os.path.join(folder, f"clocks_rank{index}.csv")
 
     def __enter__(self):
         try:

@@ -26,7 +26,7 @@
  *   xi[t*m + k'], psi[t*m + r']; gamma/delta[(i*n+p)*(n-1) + j'/q'];
  *   Delta[i*n+p], pi_x[i*n+p], alpha[i], beta[p].
  *
- * Readings of points the paper leaves open (all listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - state is (b', C^, D^); Theta and Delta are rebuilt every iteration
  *     (Algorithm 1's "C' <- C' + Theta" is read as a temporary, S1 variant);
  *   - all reduced costs come from one snapshot before any cost moves (Jacobi);
