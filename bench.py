@@ -210,19 +210,28 @@ def timed_device_run(R, torch, inst, warm: int, steps: int, warmup: int, barrier
     barrier()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    ctx.iterate_async(steps)
-    e1.record(stream)
+    # events every 50 iterations: the first and last windows show how the
+    # iteration time grows as the costs spread (the paper's observation, Section 5)
+    chunk = 50
+    marks = [torch.cuda.Event(enable_timing=True)]
+    marks[0].record(stream)
+    left = steps
+    while left > 0:
+        k = min(chunk, left)
+        ctx.iterate_async(k)
+        marks.append(torch.cuda.Event(enable_timing=True))
+        marks[-1].record(stream)
+        left -= k
     torch.cuda.synchronize()
     barrier()
-    ms = e0.elapsed_time(e1)
+    ms = marks[0].elapsed_time(marks[-1])
+    windows = [(min(chunk, steps - chunk * w), marks[w].elapsed_time(marks[w + 1])) for w in range(len(marks) - 1)]
     s1 = ctx.stats()
     kt = ctx.kernel_times()
     lb, best, ub, _, _, its = ctx.bound()
     ctx.close()
     d = s1 - s0
-    return dict(ms=ms, stats=d, kt=kt, lb=lb, best=best, ub=ub, iters=its, T=ctx.T, n=ctx.n)
+    return dict(ms=ms, stats=d, kt=kt, lb=lb, best=best, ub=ub, iters=its, T=ctx.T, n=ctx.n, windows=windows)
 
 
 def run_profile_case(args):
@@ -537,6 +546,11 @@ def main():
                        "z_aug_per_lap": cold["stats"][1] / (steps * T)},
         "warm": {"lb_last": warm["lb"], "z_aug_per_lap": warm["stats"][1] / (steps * T),
                  "same_bound_as_cold_rel": abs(warm["lb"] - cold["lb"]) / abs(cold["lb"])},
+        "ms_per_iteration_windows": {
+            "first_50_after_warmup": warm["windows"][0][1] / warm["windows"][0][0],
+            "last_50": warm["windows"][-1][1] / warm["windows"][-1][0],
+            "cold_first_50_after_warmup": cold["windows"][0][1] / cold["windows"][0][0],
+            "cold_last_50": cold["windows"][-1][1] / cold["windows"][-1][0]},
         "kernels_ms_per_iteration": {k: v[0] / steps for k, v in warm["kt"].items()},
         "kernel_launches_per_iteration": {k: v[1] / steps for k, v in warm["kt"].items()},
         "roofline": {"bound": "alu", "kernel": "lap_z", "achieved": ach_lz, "peak": FP64_PEAK_GOPS,

@@ -409,3 +409,43 @@ def test_warm_start_raw_bit_exact_and_canonical_equal(R, which):
         with R.Context(inst.F, inst.D, inst.B, partial=partial, prm=_prm(R, 1, warm=warm)) as ctx:
             out[warm], _ = ctx.iterate(iters)
     assert np.max(np.abs(out[1] - out[0]) / np.maximum(1.0, np.abs(out[0]))) <= 1e-9
+
+
+def test_max_residual_size_n32_sampled(R):
+    """The largest residual size a context takes (n = 32: 984,064 Z-LAPs of size 30,
+    a 7.1 GB z array, 30 of 32 lanes per LAP): the first bound equals the
+    Gilmore-Lawler closed form; after three iterations the bound has not
+    decreased and sampled Z tiles (copied from the device state) re-solved by
+    the oracle's LAP give the GPU's optimum and canonical duals."""
+    from scipy.optimize import linear_sum_assignment
+    inst = I.grid_instance("n32_grid4x8", 4, 8, 9, 0.5, 5, 3)
+    n, m = 32, 30
+    F, Dm = inst.F, inst.D
+    L = np.zeros((n, n))
+    for i in range(n):
+        for p in range(n):
+            L[i, p] = F[i, i] * Dm[p, p] + float(np.dot(np.sort(np.delete(F[i], i)), np.sort(np.delete(Dm[p], p))[::-1]))
+    r, c = linear_sum_assignment(L)
+    gl = L[r, c].sum()
+    with R.Context(inst.F, inst.D, inst.B, prm=R.params(feas_tol=0.0, warm=1)) as ctx:
+        lbs, done = ctx.iterate(3)
+        T, E = ctx.T, ctx.E
+        assert T == 984064 and E == T * m * m
+        D = torch.empty(E, dtype=torch.float64, device="cuda")
+        R.rlt2_export_state(ctx.ctx, D, None, on_device=1)
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(4)
+        pick = [int(t) for t in rng.choice(T, 40, replace=False)] + [0, T - 1]
+        tiles = {t: D[t * m * m:(t + 1) * m * m].view(m, m).cpu().numpy().copy() for t in pick}
+        del D
+        torch.cuda.empty_cache()
+        duals = ctx.duals()
+    assert done == 3
+    assert abs(lbs[0] - gl) <= 1e-9 * gl
+    assert np.all(np.diff(lbs) >= -1e-9 * np.abs(lbs[:-1]))
+    for t, tile in tiles.items():
+        o = O.lap(tile, canonical=True)
+        xi, psi = duals["xi"][t * m:(t + 1) * m], duals["psi"][t * m:(t + 1) * m]
+        scale = max(1.0, np.abs(tile).max())
+        assert abs(xi.sum() + psi.sum() - o.value) <= 1e-9 * scale * m
+        assert np.allclose(xi, o.u, atol=1e-9 * scale) and np.allclose(psi, o.v, atol=1e-9 * scale)
