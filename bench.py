@@ -310,6 +310,26 @@ def variant_runs(R, torch, iters: int = 300):
     return res
 
 
+def run_bnb_hard():
+    """Branch and bound to proven optimality on a Nugent-like n = 20 instance."""
+    import torch
+    from paper_1710_03732_gb300 import rlt2 as R
+    R.lib()
+    inst = I.grid_instance("n20_grid4x5", 4, 5, 9, 0.5, 12, 1)
+    res = {"workload": "QAP n=20, D = Manhattan 4x5 grid, F symmetric 0..9 at density 0.5 (seed 12), B = 0"}
+    for wd, tag in ((64, "warm"), (-1, "cold")):
+        opts = R.bnb_options(iters_root=300, iters_node=60, warm_depth=wd, time_limit_s=600.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        best, perm, rlb, st = R.rlt2_bnb_solve(inst.F, inst.D, inst.B, prm=R.params(warm=1, stall_window=25),
+                                               opts=opts)
+        dt = time.perf_counter() - t0
+        res[tag] = dict(best=best, perm=[int(x) for x in perm], root_lb=rlb, seconds=dt,
+                        nodes_per_s=st["bounded"] / dt, **{k: int(v) for k, v in st.items()})
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def bnb_runs(R, torch):
     """rlt2_bnb_solve on the n = 12 grid workload and on n = 12 and n = 14
     random instances (F 0..9 at density 0.7, asymmetric, with B; seeds 70, 71):
@@ -427,6 +447,9 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the config 4 / config 5 / learned measurements")
+    ap.add_argument("--bnb-hard", action="store_true",
+                    help="only solve a Nugent-like n=20 QAP (4x5 grid, F 0..9 at density 0.5, seed 12) to proven "
+                         "optimality with rlt2_bnb_solve and print its statistics (about two minutes)")
     ap.add_argument("--profile", nargs="?", const="n20", choices=["n20", "nodes", "learned"],
                     help="only run a small case for ncu captures: n20 = warmup+steps iterations of the n=20 "
                          "workload (graph replay, warm start); nodes = 16 nodes of the n=22 grid QAP; "
@@ -437,6 +460,8 @@ def main():
         return run_reference(args)
     if args.profile:
         return run_profile_case(args)
+    if args.bnb_hard:
+        return run_bnb_hard()
 
     rank, world, local = env_rank()
     inst = I.config(CFG)

@@ -306,7 +306,8 @@ rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D, const doub
  * (deeper first among equal bounds); a node is fathomed when its bound reaches
  * the incumbent minus abs_tol.  Children of a parent at depth <= warm_depth
  * start from the parent's multipliers (rlt2_create_child) while at most
- * max_states parent contexts are kept; other children start from zero.  Each
+ * max_states parent contexts, together at most max_state_bytes of device
+ * memory, are kept; other children start from zero.  Each
  * node's ascent stops at iters_node iterations (iters_root at the root), when
  * it is fathomed (min-gap against the incumbent) or by the stall rule of p.
  * Nodes with at most two free facilities are enumerated.  Every bounded node's
@@ -316,12 +317,13 @@ typedef struct rlt2_bnb_options {
   int iters_root;       /* default 200 */
   int iters_node;       /* default 100 */
   int warm_depth;       /* default 64 (all); -1: every node starts from zero multipliers */
-  int max_states;       /* parent contexts kept for warm starts at once; default 64 */
+  int max_states;       /* parent contexts kept for warm starts at once; default 4096 */
   long long max_nodes;  /* stop after this many bounded nodes (0: no limit) */
   double time_limit_s;  /* stop after this many seconds (0: no limit) */
   double ub0;           /* known incumbent value (<= 0: none) */
   double abs_tol;       /* fathom when LB >= UB - abs_tol; < 0 (default): 1 - 1e-6 when F, D, B are
                            integral (the optimum is then an integer), else 1e-9 max(1, |UB|) */
+  double max_state_bytes; /* device memory for kept parent contexts; 0 (default): half the free memory */
 } rlt2_bnb_options;
 void rlt2_bnb_options_default(rlt2_bnb_options* o);
 

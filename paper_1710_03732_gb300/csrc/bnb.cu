@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "rlt2.h"
 
 namespace {
@@ -93,11 +95,12 @@ extern "C" void rlt2_bnb_options_default(rlt2_bnb_options* o) {
   o->iters_root = 200;
   o->iters_node = 100;
   o->warm_depth = 64;
-  o->max_states = 64;
+  o->max_states = 4096;
   o->max_nodes = 0;
   o->time_limit_s = 0.0;
   o->ub0 = 0.0;
   o->abs_tol = -1.0;
+  o->max_state_bytes = 0.0;
 }
 
 extern "C" rlt2_status rlt2_bnb_solve(int n, const double* F, const double* D, const double* B, const rlt2_params* p,
@@ -108,8 +111,15 @@ extern "C" rlt2_status rlt2_bnb_solve(int n, const double* F, const double* D, c
   rlt2_bnb_options_default(&o);
   if (opt) o = *opt;
   if (o.order_rule < 1 || o.order_rule > 3 || o.iters_root < 1 || o.iters_node < 1 || o.max_states < 0 ||
-      o.max_nodes < 0 || !std::isfinite(o.time_limit_s) || !std::isfinite(o.ub0) || !std::isfinite(o.abs_tol))
+      o.max_nodes < 0 || !std::isfinite(o.time_limit_s) || !std::isfinite(o.ub0) || !std::isfinite(o.abs_tol) ||
+      !(o.max_state_bytes >= 0.0))
     return RLT2_EINVAL;
+  double state_budget = o.max_state_bytes;
+  if (state_budget <= 0.0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return RLT2_ECUDA;
+    state_budget = 0.5 * (double)fr;
+  }
   rlt2_params prm;
   rlt2_params_default(&prm);
   if (p) prm = *p;
@@ -123,6 +133,12 @@ extern "C" rlt2_status rlt2_bnb_solve(int n, const double* F, const double* D, c
   std::vector<int> inc_perm;
   long long bounded = 0, branched = 0, leaves = 0, iterations = 0, warm = 0, cold = 0;
   int max_depth = 0, kept = 0;
+  double kept_bytes = 0.0;
+  // device bytes of a context with residual size r (z array, tile arrays, duals)
+  auto ctx_bytes = [](int r) {
+    const double T = (double)r * r * (r - 1) * (r - 1);
+    return 8.0 * (T * (r - 2) * (r - 2) + 6.0 * T + 2.0 * T * (r - 2)) + (1 << 20);
+  };
   bool limited = false;
   rlt2_status st = RLT2_OK;
   auto tol = [&]() { return o.abs_tol >= 0.0 ? o.abs_tol : (whole ? 1.0 - 1e-6 : 1e-9 * std::max(1.0, std::fabs(inc))); };
@@ -188,9 +204,10 @@ extern "C" rlt2_status rlt2_bnb_solve(int n, const double* F, const double* D, c
       return st;
     }
     Node* nd = new Node{rlb, 0, std::vector<int>(n, -1), nullptr, seq++};
-    if (o.warm_depth >= 0 && o.max_states > 0) {
+    if (o.warm_depth >= 0 && o.max_states > 0 && ctx_bytes(n) <= state_budget) {
       nd->state = root;
       ++kept;
+      kept_bytes += ctx_bytes(n);
     } else {
       rlt2_destroy(root);
     }
@@ -204,6 +221,7 @@ extern "C" rlt2_status rlt2_bnb_solve(int n, const double* F, const double* D, c
       if (nd->state) {
         rlt2_destroy(nd->state);
         --kept;
+        kept_bytes -= ctx_bytes(n - nd->depth);
       }
       delete nd;
       continue;
@@ -250,9 +268,10 @@ extern "C" rlt2_status rlt2_bnb_solve(int n, const double* F, const double* D, c
         continue;
       }
       Node* ch = new Node{lb, depth, part, nullptr, seq++};
-      if (depth <= o.warm_depth && kept < o.max_states) {
+      if (depth <= o.warm_depth && kept < o.max_states && kept_bytes + ctx_bytes(n - depth) <= state_budget) {
         ch->state = c;
         ++kept;
+        kept_bytes += ctx_bytes(n - depth);
       } else {
         rlt2_destroy(c);
       }
@@ -261,6 +280,7 @@ extern "C" rlt2_status rlt2_bnb_solve(int n, const double* F, const double* D, c
     if (nd->state) {
       rlt2_destroy(nd->state);
       --kept;
+      kept_bytes -= ctx_bytes(n - nd->depth);
     }
     delete nd;
     if (st != RLT2_OK) break;

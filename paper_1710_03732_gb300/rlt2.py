@@ -33,7 +33,8 @@ class rlt2_params(ctypes.Structure):
 class rlt2_bnb_options(ctypes.Structure):
     _fields_ = [("order_rule", ctypes.c_int), ("iters_root", ctypes.c_int), ("iters_node", ctypes.c_int),
                 ("warm_depth", ctypes.c_int), ("max_states", ctypes.c_int), ("max_nodes", ctypes.c_longlong),
-                ("time_limit_s", ctypes.c_double), ("ub0", ctypes.c_double), ("abs_tol", ctypes.c_double)]
+                ("time_limit_s", ctypes.c_double), ("ub0", ctypes.c_double), ("abs_tol", ctypes.c_double),
+                ("max_state_bytes", ctypes.c_double)]
 
 
 class Rlt2Error(RuntimeError):
