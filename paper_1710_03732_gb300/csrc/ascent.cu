@@ -254,6 +254,7 @@ struct rlt2_ctx {
   double kms[kKinds] = {};
   long long kcount[kKinds] = {};
   int iter_host = 0;
+  long long enqueued = 0;  // iterations enqueued so far (the graph is captured past kDirectIters)
   double cst_host = 0.0;
   rlt2_mlp* mlp = nullptr;
   double* u0buf = nullptr;
@@ -948,6 +949,11 @@ static rlt2_status build_graph(rlt2_ctx* c) {
 }
 
 constexpr int kEvChunk = 64;  // iterations per batch of timing events
+// A context's first kDirectIters iterations are launched kernel by kernel:
+// capturing and instantiating the CUDA graph costs about as much as one
+// iteration of a mid-size node, which short-lived branch-and-bound contexts
+// never win back; the iterations are GPU-bound either way.
+constexpr long long kDirectIters = 64;
 
 static rlt2_status enqueue_many(rlt2_ctx* c, int iters) {
   if (c->prm.warm == 2 && !c->mlp) {
@@ -975,9 +981,18 @@ static rlt2_status enqueue_many(rlt2_ctx* c, int iters) {
     }
     return RLT2_OK;
   }
+  if (!c->graph && c->enqueued + iters <= kDirectIters) {
+    for (int it = 0; it < iters; ++it) {
+      cudaError_t e = enqueue_iteration_ctx(c, c->stream, -1);
+      if (e != cudaSuccess) return cuda_fail(e, "enqueue_iteration");
+    }
+    c->enqueued += iters;
+    return RLT2_OK;
+  }
   rlt2_status st = build_graph(c);
   if (st != RLT2_OK) return st;
   for (int it = 0; it < iters; ++it) CK(cudaGraphLaunch(c->graph, c->stream));
+  c->enqueued += iters;
   return RLT2_OK;
 }
 
@@ -996,8 +1011,15 @@ extern "C" rlt2_status rlt2_iterate(rlt2_ctx* c, int iters, double* lb_hist, int
     return RLT2_EINVAL;
   }
   int total = 0;
-  for (int off = 0; off < iters; off += kRing) {
-    const int chunk = (iters - off) < kRing ? (iters - off) : kRing;
+  // chunks of 8, 16, 32, ... iterations: a stop on the device (feasibility,
+  // min-gap, stall) ends the call after the chunk it falls in, so stopped
+  // contexts (fathomed branch-and-bound nodes) do not run many no-op launches
+  int step = 8;
+  for (int off = 0; off < iters;) {
+    int chunk = iters - off;
+    if (chunk > step) chunk = step;
+    if (chunk > kRing) chunk = kRing;
+    step = step < 1024 ? 2 * step : step;
     const int it0 = c->iter_host;
     rlt2_status st = enqueue_many(c, chunk);
     if (st != RLT2_OK) return st;
@@ -1023,6 +1045,7 @@ extern "C" rlt2_status rlt2_iterate(rlt2_ctx* c, int iters, double* lb_hist, int
         for (int k = off + chunk; k < iters; ++k) lb_hist[k] = NAN;
       break;
     }
+    off += chunk;
   }
   if (done) *done = total;
   return RLT2_OK;
