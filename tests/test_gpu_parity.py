@@ -449,3 +449,19 @@ def test_max_residual_size_n32_sampled(R):
         scale = max(1.0, np.abs(tile).max())
         assert abs(xi.sum() + psi.sum() - o.value) <= 1e-9 * scale * m
         assert np.allclose(xi, o.u, atol=1e-9 * scale) and np.allclose(psi, o.v, atol=1e-9 * scale)
+
+
+def test_direct_launches_and_graph_replay_agree(R):
+    """A context launches its first 64 iterations kernel by kernel and later ones
+    as CUDA-graph replays; splitting a run over many calls, or running it in one
+    call, gives the same trajectory bit for bit (raw duals)."""
+    inst = I.random_instance(9, 81, with_b=True, asymmetric=True)
+    prm = R.params(dual_mode=0, feas_tol=0.0, warm=1)
+    with R.Context(inst.F, inst.D, inst.B, prm=prm) as a:
+        one, _ = a.iterate(90)
+    parts = []
+    with R.Context(inst.F, inst.D, inst.B, prm=prm) as b:
+        for k in (5, 7, 20, 30, 28):
+            h, _ = b.iterate(k)
+            parts.append(h)
+    assert np.array_equal(one, np.concatenate(parts))
