@@ -618,6 +618,7 @@ extern "C" rlt2_status rlt2_create(int n, const double* F, const double* D, cons
   if ((e = cudaMemcpy(&c->cst_host, c->d_cst, 8, cudaMemcpyDeviceToHost)) != cudaSuccess) return fail(e, "cst");
   for (int mm2 : {nr - 2, nr - 1, nr})
     if ((e = prepare_lap(mm2)) != cudaSuccess) return fail(e, "prepare_lap");
+  if ((e = prepare_lap(nr - 1, 0, 4)) != cudaSuccess) return fail(e, "prepare_lap");
   *out = c;
   return RLT2_OK;
 }
@@ -692,6 +693,7 @@ extern "C" rlt2_status rlt2_create_child(rlt2_ctx* parent, int facility, int loc
   if (e == cudaSuccess) e = cudaMemcpy(&c->cst_host, c->d_cst, 8, cudaMemcpyDeviceToHost);
   for (int mm2 : {nr - 2, nr - 1, nr})
     if (e == cudaSuccess) e = prepare_lap(mm2);
+  if (e == cudaSuccess) e = prepare_lap(nr - 1, 0, 4);
   if (e != cudaSuccess) {
     rlt2_status r = cuda_fail(e, "rlt2_create_child");
     ctx_free(c);
@@ -891,6 +893,7 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   y.dual_mode = p.dual_mode;
   y.stats = v.sc->stats + 2;
   y.skip = done;
+  y.warps_per_block = 4;  // n^2 LAPs only: spread them over more SMs
   if ((e = rec(3, 0)) != cudaSuccess) return e;
   if ((e = launch_lap(y, s)) != cudaSuccess) return e;
   count(3, 1);

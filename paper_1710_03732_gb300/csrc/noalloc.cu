@@ -186,6 +186,7 @@ extern "C" rlt2_status rlt2_iterate_noalloc(int n, const double* F, const double
     return cuda_fail(e, "rlt2_iterate_noalloc: x costs");
   for (int mm : {n - 2, n - 1, n})
     if ((e = prepare_lap(mm)) != cudaSuccess) return cuda_fail(e, "rlt2_iterate_noalloc: prepare");
+  if ((e = prepare_lap(n - 1, 0, 4)) != cudaSuccess) return cuda_fail(e, "rlt2_iterate_noalloc: prepare");
   for (int it = 0; it < iters; ++it)
     if ((e = enqueue_iteration(v, s, nullptr)) != cudaSuccess) return cuda_fail(e, "rlt2_iterate_noalloc: iterate");
   return RLT2_OK;
