@@ -9,10 +9,11 @@
 // exactly those of a cold start; what the network saves is augmenting searches.
 //
 // Network: 34 -> H -> H -> 1, ReLU, BF16 weights and activations, FP32
-// accumulation.  The two matrix products per layer run on the tensor cores
-// through a hand-written mma.sync (m16n8k16, BF16 -> FP32) GEMM with ldmatrix
-// fragment loads and a cp.async double-buffered shared-memory pipeline; the
-// same kernel, with transposed-operand variants, computes the backward pass.
+// accumulation.  Inference of the H = 256 network runs on the 5th-generation
+// tensor cores (tcgen05.mma with TMEM accumulators, umma.cu); training and
+// other widths use a hand-written mma.sync (m16n8k16, BF16 -> FP32) GEMM with
+// ldmatrix fragment loads and a cp.async double-buffered shared-memory
+// pipeline, whose transposed-operand variants compute the backward pass.
 // Features are built without FP64 arithmetic (FP64 -> FP32 by truncating the
 // significand on the integer pipe) because FP64 is GB300's scarce resource.
 #include <cuda_bf16.h>
@@ -418,6 +419,7 @@ struct rlt2_mlp {
   bf16 *Xc = nullptr, *H1 = nullptr, *H2 = nullptr, *dH2 = nullptr, *dH1 = nullptr;
   float *out = nullptr, *tgt = nullptr, *dout = nullptr, *scale = nullptr;
   double* loss = nullptr;
+  int* err = nullptr;  // set by the tensor-core inference kernel on a timed-out wait
 };
 
 namespace {
@@ -521,6 +523,11 @@ cudaError_t ensure_dataset(rlt2_mlp* m, long long need) {
 }  // namespace
 
 namespace rlt2 {
+// tcgen05 inference of the H = 256 network (umma.cu)
+cudaError_t umma_mlp_forward(const bf16* X, long long rows, const bf16* W1, const float* b1, const bf16* W2,
+                             const float* b2, const float* w3, const float* b3, float* out, int* err,
+                             cudaStream_t s);
+
 // Predict Z-LAP row duals u0 (FP64) for ntiles tiles of size m; prev_u nullable.
 cudaError_t mlp_predict_enqueue(rlt2_mlp* m, long long ntiles, int mz, const double* tiles, const double* prev_u,
                                 double* u0, cudaStream_t s, int* launched) {
@@ -535,11 +542,18 @@ cudaError_t mlp_predict_enqueue(rlt2_mlp* m, long long ntiles, int mz, const dou
     if (prows > rows && (e = cudaMemsetAsync(m->Xc + rows * kInPad, 0, sizeof(bf16) * (prows - rows) * kInPad, s)) !=
                             cudaSuccess)
       return e;
-    if ((e = forward(m, m->Xc, prows, m->out, s)) != cudaSuccess) return e;
+    if (m->H == 256) {
+      // tcgen05 path: the whole network in one persistent kernel
+      if ((e = umma_mlp_forward(m->Xc, rows, m->W1b, m->b1, m->W2b, m->b2, m->w3, m->b3, m->out, m->err, s)) !=
+          cudaSuccess)
+        return e;
+    } else if ((e = forward(m, m->Xc, prows, m->out, s)) != cudaSuccess) {
+      return e;
+    }
     k_u0<<<(int)std::min<long long>(4096, (rows + 255) / 256), 256, 0, s>>>(
         rows, mz, m->out, m->scale, prev_u ? prev_u + t0 * mz : nullptr, m->gate, u0 + t0 * mz);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (launched) *launched += 5;  // features, two GEMMs, output layer, starts
+    if (launched) *launched += m->H == 256 ? 3 : 5;  // features, the network, starts
   }
   return cudaSuccess;
 }
@@ -584,6 +598,8 @@ extern "C" rlt2_status rlt2_mlp_create(int hidden, unsigned long long seed, void
   if ((e = cudaMalloc((void**)&m->dout, sizeof(float) * cr)) != cudaSuccess) return fail(e);
   if ((e = cudaMalloc((void**)&m->scale, sizeof(float) * cr)) != cudaSuccess) return fail(e);
   if ((e = cudaMalloc((void**)&m->loss, sizeof(double))) != cudaSuccess) return fail(e);
+  if ((e = cudaMalloc((void**)&m->err, sizeof(int))) != cudaSuccess) return fail(e);
+  if ((e = cudaMemsetAsync(m->err, 0, sizeof(int), m->stream)) != cudaSuccess) return fail(e);
   cudaStream_t s = m->stream;
   // He initialisation of W1 (34 valid input rows) and W2, small w3, zero biases
   if ((e = cudaMemsetAsync(m->W1, 0, sizeof(float) * m->nparams, s)) != cudaSuccess) return fail(e);
@@ -601,7 +617,7 @@ extern "C" rlt2_status rlt2_mlp_destroy(rlt2_mlp* m) {
   if (!m) return RLT2_OK;
   if (m->stream) cudaStreamSynchronize(m->stream);
   void* ptrs[] = {m->W1, m->mom, m->grad, m->W1b, m->W2b, m->Xd, m->Td, m->Xc, m->H1, m->H2, m->dH1, m->dH2,
-                  m->out, m->tgt, m->dout, m->scale, m->loss};
+                  m->out, m->tgt, m->dout, m->scale, m->loss, m->err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete m;
@@ -786,5 +802,11 @@ extern "C" rlt2_status rlt2_mlp_predict(rlt2_mlp* m, long long ntiles, int mz, c
   }
   CKM(mlp_predict_enqueue(m, ntiles, mz, tiles, prev_u, u0, m->stream));
   CKM(cudaStreamSynchronize(m->stream));
+  int err = 0;
+  CKM(cudaMemcpy(&err, m->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    set_error("rlt2_mlp_predict: a tensor-core wait timed out");
+    return RLT2_ETIMEOUT;
+  }
   return RLT2_OK;
 }
