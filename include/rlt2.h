@@ -297,6 +297,16 @@ rlt2_status rlt2_lap_batched(int batch, int m, const double* cost, const double*
  * Errors: EINVAL (bad input), EADMIT (a node alone exceeds mem_budget),
  * ENOMEM, ECUDA.  Device memory is allocated for the call and freed on return. */
 typedef struct rlt2_mlp rlt2_mlp;
+
+/* Failure-detection check of the tensor-core inference kernel (no counterpart
+ * in the paper): runs it on one tile with its MMA and commit withheld, so its
+ * bounded mbarrier wait runs out (about 2^22 polls); the kernel then sets the
+ * network's error flag, releases its TMEM and returns, and the device stays
+ * usable.  Returns RLT2_ETIMEOUT when the timeout was detected and reported
+ * (the expected outcome, error flag cleared again), RLT2_OK if the wait did
+ * not run out, EINVAL for a network whose width is not 256, ECUDA otherwise. */
+rlt2_status rlt2_mlp_check_wait_timeout(rlt2_mlp* mlp);
+
 rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D, const double* B, int n_nodes,
                              const int* partials, const rlt2_params* p, rlt2_mlp* mlp, int iters, size_t mem_budget,
                              double* lb_out, double* lb_hist, int* iters_out, long long* stats_out, void* stream);

@@ -526,7 +526,7 @@ namespace rlt2 {
 // tcgen05 inference of the H = 256 network (umma.cu)
 cudaError_t umma_mlp_forward(const bf16* X, long long rows, const bf16* W1, const float* b1, const bf16* W2,
                              const float* b2, const float* w3, const float* b3, float* out, int* err,
-                             cudaStream_t s);
+                             cudaStream_t s, bool withhold_commit = false);
 
 // Predict Z-LAP row duals u0 (FP64) for ntiles tiles of size m; prev_u nullable.
 cudaError_t mlp_predict_enqueue(rlt2_mlp* m, long long ntiles, int mz, const double* tiles, const double* prev_u,
@@ -791,6 +791,26 @@ extern "C" rlt2_status rlt2_mlp_fit(rlt2_mlp* m, int steps, int batch_rows, doub
 extern "C" rlt2_status rlt2_mlp_set_gate(rlt2_mlp* m, double gate) {
   if (!m || !(gate >= 0.0)) return RLT2_EINVAL;
   m->gate = (float)gate;
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_mlp_check_wait_timeout(rlt2_mlp* m) {
+  if (!m || m->H != 256) {
+    set_error("rlt2_mlp_check_wait_timeout: needs a network with H = 256");
+    return RLT2_EINVAL;
+  }
+  CKM(cudaMemsetAsync(m->err, 0, sizeof(int), m->stream));
+  CKM(cudaMemsetAsync(m->Xc, 0, sizeof(bf16) * 128 * kInPad, m->stream));
+  CKM(umma_mlp_forward(m->Xc, 128, m->W1b, m->b1, m->W2b, m->b2, m->w3, m->b3, m->out, m->err, m->stream, true));
+  CKM(cudaStreamSynchronize(m->stream));
+  int err = 0;
+  CKM(cudaMemcpy(&err, m->err, sizeof(int), cudaMemcpyDeviceToHost));
+  CKM(cudaMemsetAsync(m->err, 0, sizeof(int), m->stream));
+  CKM(cudaStreamSynchronize(m->stream));
+  if (err) {
+    set_error("rlt2_mlp_check_wait_timeout: the inference kernel's wait ran out (expected)");
+    return RLT2_ETIMEOUT;
+  }
   return RLT2_OK;
 }
 

@@ -55,7 +55,7 @@ EXPORTS = ["rlt2_params_default", "rlt2_create", "rlt2_iterate", "rlt2_iterate_a
            "rlt2_mlp_set_weights", "rlt2_mlp_add_samples", "rlt2_mlp_samples", "rlt2_mlp_clear_samples",
            "rlt2_mlp_grad", "rlt2_mlp_fit", "rlt2_mlp_set_gate", "rlt2_mlp_predict", "rlt2_set_mlp",
            "rlt2_export_xstate", "rlt2_import_xstate", "rlt2_set_sa", "rlt2_create_child", "rlt2_bnb_options_default",
-           "rlt2_bnb_solve", "rlt2_strerror", "rlt2_last_error"]
+           "rlt2_bnb_solve", "rlt2_mlp_check_wait_timeout", "rlt2_strerror", "rlt2_last_error"]
 
 
 def lib():
@@ -108,6 +108,7 @@ def lib():
                                _dp]
     L.rlt2_mlp_predict.argtypes = [_vp, ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp]
     L.rlt2_mlp_set_gate.argtypes = [_vp, ctypes.c_double]
+    L.rlt2_mlp_check_wait_timeout.argtypes = [_vp]
     L.rlt2_set_mlp.argtypes = [_vp, _vp]
     L.rlt2_strerror.argtypes = [ctypes.c_int]
     L.rlt2_strerror.restype = ctypes.c_char_p

@@ -126,3 +126,26 @@ def test_training_reduces_loss_and_augmentations(R):
             res[warm] = (lbs, ctx.stats())
     assert np.max(np.abs(res[2][0] - res[0][0]) / np.abs(res[0][0])) <= 1e-6
     assert res[2][1][1] < res[0][1][1]
+
+
+def test_inference_wait_timeout_is_detected(R):
+    """Failure detection without a fault: the tensor-core inference kernel is run
+    with its MMA commit withheld, its bounded mbarrier wait runs out, the error
+    is reported to the host and the device stays usable (a normal prediction
+    afterwards still matches the oracle)."""
+    mlp = R.Mlp(256)
+    st = R.lib().rlt2_mlp_check_wait_timeout(mlp.ptr)
+    assert st == R.RLT2_ETIMEOUT
+    rng = np.random.default_rng(5)
+    m, nt = 18, 40
+    tiles = _tiles(rng, nt, m)
+    prev = rng.normal(size=(nt, m))
+    net = _random_weights(rng, 256)
+    mlp.set_weights(*net)
+    u0 = torch.empty(nt, m, dtype=torch.float64, device="cuda")
+    mlp.predict(torch.from_numpy(tiles).cuda(), u0, torch.from_numpy(prev).cuda())
+    u0 = u0.cpu().numpy()
+    f, _, s = O.mlp_features(tiles[3], prev_u=prev[3])
+    out, _, _ = O.mlp_forward(f, *net, bf16_acts=True)
+    ref = prev[3] + (np.float32(out.astype(np.float32)) * np.float32(s)).astype(np.float64)
+    assert np.allclose(u0[3], ref, rtol=2e-3, atol=2e-3 * abs(s))
