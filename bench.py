@@ -53,10 +53,18 @@ def measured_peaks():
         return {}
 
 
-def source_digest() -> str:
+# source files that define each profiled kernel (its traffic figure stays valid
+# until one of them changes)
+KERNEL_SOURCES = {
+    "lap_z": ["lap.cu", "rlt2_lap.cuh", "rlt2_internal.h"],
+    "move_z": ["ascent.cu", "rlt2_ascent.cuh", "rlt2_internal.h"],
+}
+
+
+def source_digest(kernel: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1710_03732_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in KERNEL_SOURCES[kernel]:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -69,7 +77,7 @@ def profiled_traffic(kernel: str, workload: str):
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
-    want = source_digest()
+    want = source_digest(kernel)
     for line in open(path):
         parts = line.split()
         if len(parts) >= 4 and parts[0] == kernel and parts[1] == workload and parts[3] == want:
