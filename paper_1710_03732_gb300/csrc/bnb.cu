@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include "rlt2.h"
+#include "rlt2_internal.h"
 
 namespace {
 
@@ -106,24 +107,33 @@ extern "C" void rlt2_bnb_options_default(rlt2_bnb_options* o) {
 extern "C" rlt2_status rlt2_bnb_solve(int n, const double* F, const double* D, const double* B, const rlt2_params* p,
                                       const rlt2_bnb_options* opt, double* best, int* perm, double* root_lb,
                                       long long* stats, void* stream) {
-  if (n < 3 || n > 64 || !F || !D || !best || !perm) return RLT2_EINVAL;
+  if (n < 3 || n > 64 || !F || !D || !best || !perm) {
+    rlt2::set_error("rlt2_bnb_solve: need 3 <= n <= 64 and non-NULL F, D, best, perm");
+    return RLT2_EINVAL;
+  }
   rlt2_bnb_options o;
   rlt2_bnb_options_default(&o);
   if (opt) o = *opt;
   if (o.order_rule < 1 || o.order_rule > 3 || o.iters_root < 1 || o.iters_node < 1 || o.max_states < 0 ||
       o.max_nodes < 0 || !std::isfinite(o.time_limit_s) || !std::isfinite(o.ub0) || !std::isfinite(o.abs_tol) ||
-      !(o.max_state_bytes >= 0.0))
+      !(o.max_state_bytes >= 0.0)) {
+    rlt2::set_error("rlt2_bnb_solve: options out of range");
     return RLT2_EINVAL;
+  }
   double state_budget = o.max_state_bytes;
   if (state_budget <= 0.0) {
     size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return RLT2_ECUDA;
+    const cudaError_t e = cudaMemGetInfo(&fr, &tot);
+    if (e != cudaSuccess) return rlt2::cuda_fail(e, "rlt2_bnb_solve: cudaMemGetInfo");
     state_budget = 0.5 * (double)fr;
   }
   rlt2_params prm;
   rlt2_params_default(&prm);
   if (p) prm = *p;
-  if (prm.variant != 0) return RLT2_EINVAL;  // children inherit the S variant's multiplier-adjusted costs
+  if (prm.variant != 0) {  // children inherit the S variant's multiplier-adjusted costs
+    rlt2::set_error("rlt2_bnb_solve: node parameters must select the S variant");
+    return RLT2_EINVAL;
+  }
   const size_t nn = (size_t)n * n;
   const bool whole = integral(F, nn) && integral(D, nn) && (!B || integral(B, nn));
   const auto t_start = std::chrono::steady_clock::now();

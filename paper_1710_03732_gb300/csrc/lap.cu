@@ -1,6 +1,7 @@
 // Batched LAP kernel (one warp per LAP) and the rlt2_lap_batched entry point.
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 
 #include "rlt2_internal.h"
 #include "rlt2_lap.cuh"
@@ -93,6 +94,10 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap(LapArgs a) {
 }
 
 // blocks per SM for (m, G, warps per block), 0 = not configured
+// Launch configuration (occupancy per size, shared-memory attributes), set once
+// per (size, group, warps) under g_cfg_mu: contexts may be created and used
+// from different host threads.
+static std::mutex g_cfg_mu;
 static int g_occ[33][3][2];
 
 static int gidx(int G) { return G == 8 ? 0 : (G == 16 ? 1 : 2); }
@@ -128,6 +133,7 @@ cudaError_t prepare_lap(int m, int group, int warps_per_block) {
   const int G = group ? group : default_group(m);
   const int wpb = warps_per_block ? warps_per_block : kMaxWarpsPerBlock;
   if (G < m || (G != 8 && G != 16 && G != 32) || (wpb != 4 && wpb != 8)) return cudaErrorInvalidValue;
+  std::lock_guard<std::mutex> lock(g_cfg_mu);
   cudaError_t e;
   if (!g_sms) {
     int dev = 0;
@@ -265,6 +271,7 @@ cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s) {
   const size_t pre = (((size_t)(a.nnodes + 1) * sizeof(long long)) + 255) & ~size_t(255);
   const size_t smem = pre + warp_smem_bytes(a.max_m, G) * wpb;
   cudaError_t e;
+  std::unique_lock<std::mutex> lock(g_cfg_mu);
   if (!g_sms) {
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -309,9 +316,10 @@ cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s) {
     occ = o1 < o2 ? o1 : o2;
   }
   if (occ < 1) occ = 1;
+  const long long cap = (long long)g_sms * occ;
+  lock.unlock();
   const long long per_block = (long long)wpb * (32 / G);
   const long long need = (a.total + per_block - 1) / per_block;
-  const long long cap = (long long)g_sms * occ;
   const int grid = (int)(need < cap ? need : cap);
   if (G == 8) {
     if (a.pre) k_lap_nodes<8, true><<<grid, wpb * 32, smem, s>>>(a);

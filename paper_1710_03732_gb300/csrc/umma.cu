@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "rlt2_internal.h"
 
@@ -250,19 +251,23 @@ cudaError_t umma_mlp_forward(const bf16* X, long long rows, const bf16* W1, cons
                              const float* b2, const float* w3, const float* b3, float* out, int* err,
                              cudaStream_t s, bool withhold_commit) {
   if (rows <= 0) return cudaSuccess;
+  static std::mutex mu;  // one-time launch configuration, from any host thread
   static int sms = 0;
   static bool attr = false;
   cudaError_t e;
-  if (!sms) {
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  }
-  if (!attr) {
-    if ((e = cudaFuncSetAttribute(k_umma_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem)) !=
-        cudaSuccess)
-      return e;
-    attr = true;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!sms) {
+      int dev = 0;
+      if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+      if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    }
+    if (!attr) {
+      if ((e = cudaFuncSetAttribute(k_umma_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem)) !=
+          cudaSuccess)
+        return e;
+      attr = true;
+    }
   }
   const long long tiles = (rows + kRowsPerTile - 1) / kRowsPerTile;
   const int grid = (int)(tiles < sms ? tiles : sms);
