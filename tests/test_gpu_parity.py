@@ -465,3 +465,31 @@ def test_direct_launches_and_graph_replay_agree(R):
             h, _ = b.iterate(k)
             parts.append(h)
     assert np.array_equal(one, np.concatenate(parts))
+
+
+def test_contexts_on_two_host_threads(R):
+    """Separate contexts are independent: two host threads each create and run
+    their own context (own stream) at the same time, and each gets exactly the
+    trajectory of a run on its own (raw duals)."""
+    import threading
+    insts = [I.random_instance(9, 91, with_b=True), I.random_instance(10, 92, with_b=True, asymmetric=True)]
+    prm = R.params(dual_mode=0, feas_tol=0.0, warm=1)
+    ref = []
+    for inst in insts:
+        with R.Context(inst.F, inst.D, inst.B, prm=prm) as ctx:
+            ref.append(ctx.iterate(80)[0])
+    got = [None, None]
+
+    def work(k):
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            with R.Context(insts[k].F, insts[k].D, insts[k].B, prm=prm, stream=s.cuda_stream) as ctx:
+                got[k] = ctx.iterate(80)[0]
+
+    th = [threading.Thread(target=work, args=(k,)) for k in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for k in range(2):
+        assert np.array_equal(got[k], ref[k])
