@@ -239,7 +239,8 @@ def timed_device_run(R, torch, inst, warm: int, steps: int, warmup: int, barrier
     lb, best, ub, _, _, its = ctx.bound()
     ctx.close()
     d = s1 - s0
-    return dict(ms=ms, stats=d, kt=kt, lb=lb, best=best, ub=ub, iters=its, T=ctx.T, n=ctx.n, windows=windows)
+    return dict(ms=ms, stats=d, kt=kt, lb=lb, best=best, ub=ub, iters=its, T=ctx.T, n=ctx.n, windows=windows,
+                warm=warm)
 
 
 def run_profile_case(args):
@@ -533,11 +534,15 @@ def main():
         cnt = max(cnt, 1)
         avg_ms = ms_lz / cnt
         aug, relax = int(r["stats"][1]), int(r["stats"][2])  # totals over the timed launches
-        # useful FP64 work of one Z-stage launch: 3 additions per label relaxation
-        # (only unscanned columns count), 3 per column per search for the dual
-        # update and row duals, m for the optimum and 3 per relaxation of the
-        # canonical-dual search (m(m-1)/2 per LAP)
-        per_launch = (3 * relax + 3 * m * aug) / cnt + T * m + T * 3 * (m * (m - 1) // 2)
+        # FP64 work the method needs in one Z-stage launch: 3 additions per label
+        # relaxation (only unscanned columns count; the m start labels of a
+        # search, which the counter includes, take 2), 3 per column per search
+        # for the dual update and row duals; per LAP, m^2 for the warm start's column
+        # reduction (c - u_r), m - 1 for the optimum, and for the canonical duals
+        # 2 m^2 for the reduced tile, (m-1)(m-2)/2 Dijkstra relaxations and 3 m
+        # for the final row and column duals
+        per_lap = (m * m if r["warm"] else 0) + (m - 1) + 2 * m * m + (m - 1) * (m - 2) // 2 + 3 * m
+        per_launch = (3 * relax + 2 * m * aug) / cnt + T * per_lap
         achieved = per_launch / (avg_ms * 1e-3) / 1e9
         return avg_ms, per_launch, achieved
 
