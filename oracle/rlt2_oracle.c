@@ -924,7 +924,8 @@ void or_redistribute_half(int n, const double* prm, double* Dhat, double* Chat, 
                 D[u] = Dhat[idx[u]];
               }
               double S = (s[0] + s[1]) + s[2];
-              for (int u = 0; u < 3; u++) Dhat[idx[u]] = fma(0.5, S - s[u], D[u] - s[u]);
+              /* D - s + (S - s)/2, regrouped as (D + S/2) - (3/2) s */
+              for (int u = 0; u < 3; u++) Dhat[idx[u]] = fma(-1.5, s[u], fma(0.5, S, D[u]));
             }
           }
   /* y move of Eq. 2.21 with phi_y (1/2): every y keeps (1 - phi_y) of its slack and

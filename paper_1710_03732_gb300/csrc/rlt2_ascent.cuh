@@ -150,8 +150,9 @@ struct MoveZArgs {
 // of the same triple, which run back to back.
 // Half-Z scheme (Section 5): the upper members (i,j,k|p,q,r), (i,k,j|p,r,q) and
 // (j,k,i|q,r,p) -- members 0, 1, 3 -- pool s = kz pi_z + tile term and each
-// receives half of the other two pools: D' = fma(1/2, S - s, D - s) with S the
-// sum of the three pools in member order.  Lower members are never touched.
+// receives half of the other two pools: D' = D - s + (S - s)/2 with S the sum
+// of the three pools in member order, evaluated as fma(-3/2, s, fma(1/2, S, D)).
+// Lower members are never touched.
 __device__ __forceinline__ void move_z_half_block(const MoveZArgs& a, int blk) {
   RLT2_CLASS_TABLES
   (void)kPart;
@@ -186,7 +187,7 @@ __device__ __forceinline__ void move_z_half_block(const MoveZArgs& a, int blk) {
     }
     const double S = dadd_(dadd_(s[0], s[1]), s[2]);
 #pragma unroll
-    for (int u = 0; u < 3; ++u) a.Dhat[idx[u]] = __fma_rn(0.5, dsub_(S, s[u]), dsub_(Dv[u], s[u]));
+    for (int u = 0; u < 3; ++u) a.Dhat[idx[u]] = __fma_rn(-1.5, s[u], __fma_rn(0.5, S, Dv[u]));
   }
 }
 
