@@ -54,37 +54,31 @@ __device__ __forceinline__ float f32_trunc(double x) {
 // ------------------------------------------------------------- features ----
 // One warp per tile; lane j holds column j.  Writes 64 BF16 inputs per row
 // (34 features + zero padding), optional FP32 targets and the tile scale.
-__global__ void __launch_bounds__(256) k_features(long long ntiles, int m, const double* __restrict__ tiles,
-                                                  const double* __restrict__ prev_u,
-                                                  const double* __restrict__ target_u, bf16* __restrict__ X,
-                                                  float* __restrict__ target, float* __restrict__ scale) {
+// The tile (at most 8 KB) is read three times -- column minima, the scale, then
+// row by row for the sorts -- so only the first pass reaches DRAM and the
+// kernel keeps few registers (occupancy hides the load latency).
+__global__ void __launch_bounds__(256, 4) k_features(long long ntiles, int m, const double* __restrict__ tiles,
+                                                     const double* __restrict__ prev_u,
+                                                     const double* __restrict__ target_u, bf16* __restrict__ X,
+                                                     float* __restrict__ target, float* __restrict__ scale) {
   const int lane = threadIdx.x & 31;
+  const bool col = lane < m;
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < ntiles; t += nw) {
     const double* c = tiles + t * m * m;
-    float cf[32];
     float cmin = INFINITY;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      cf[i] = 0.0f;
-      if (i < m && lane < m) {
-        cf[i] = f32_trunc(c[i * m + lane]);
-        cmin = fminf(cmin, cf[i]);
-      }
-    }
+    for (int i = 0; i < m; ++i)
+      if (col) cmin = fminf(cmin, f32_trunc(c[i * m + lane]));
     float rmax = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 32; ++i)
-      if (i < m && lane < m) rmax = fmaxf(rmax, __fsub_rn(cf[i], cmin));
+    for (int i = 0; i < m; ++i)
+      if (col) rmax = fmaxf(rmax, __fsub_rn(f32_trunc(c[i * m + lane]), cmin));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(kFull, rmax, off));
     const float s = rmax > 0.0f ? rmax : 1.0f;
     const float inv = __fdiv_rn(1.0f, s);
     if (lane == 0 && scale) scale[t] = s;
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      if (i >= m) break;
-      float v = lane < m ? __fmul_rn(__fsub_rn(cf[i], cmin), inv) : INFINITY;
+    for (int i = 0; i < m; ++i) {
+      float v = col ? __fmul_rn(__fsub_rn(f32_trunc(c[i * m + lane]), cmin), inv) : INFINITY;
       // bitonic sort across the warp, ascending
 #pragma unroll
       for (int k = 2; k <= 32; k <<= 1) {
@@ -98,13 +92,13 @@ __global__ void __launch_bounds__(256) k_features(long long ntiles, int m, const
       }
       const long long row = t * m + i;
       bf16* xr = X + row * kInPad;
-      xr[lane] = __float2bfloat16_rn(lane < m ? v : 0.0f);
+      xr[lane] = __float2bfloat16_rn(col ? v : 0.0f);
       float hi = 0.0f;
       if (lane == 0) hi = prev_u ? __fmul_rn(f32_trunc(prev_u[row]), inv) : 0.0f;
       if (lane == 1) hi = (float)m / 32.0f;
       xr[32 + lane] = __float2bfloat16_rn(hi);
     }
-    if (target && target_u && lane < m) {
+    if (target && target_u && col) {
       // the network predicts the change of the row dual since the previous iteration
       const long long r = t * m + lane;
       const double d = prev_u ? __dsub_rn(target_u[r], prev_u[r]) : target_u[r];
