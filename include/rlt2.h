@@ -7,7 +7,9 @@
  * RLT2 and its Lagrangian dual: Section 2.3, Eq. 2.6-2.16; the three-stage
  * LAP decomposition: Figure 1 and the Theta/Delta definitions after it; the
  * ascent rules: Eq. 2.20-2.23 and their combination in the proof of
- * Theorem 1; the iteration: Algorithm 1 / Algorithm 2 (S1 variant).
+ * Theorem 1; the iteration: Algorithm 1 / Algorithm 2 (S and F variants,
+ * one or two phases, Section 3.4; the half-Z scheme and the Type 4 rule,
+ * Sections 2.3 and 5); branch and bound: Section 4.
  *
  * General conventions
  *  - Every function returns an rlt2_status; nothing throws or aborts.

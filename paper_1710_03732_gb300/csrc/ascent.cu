@@ -1,21 +1,29 @@
-// RLT2 dual ascent on one GPU: context, setup, ascent moves, stage driver and C ABI.
+// RLT2 dual ascent on one GPU: context, setup, ascent moves, stage driver,
+// branch-and-bound child derivation and the C ABI.
 //
-// One iteration (Algorithm 2, S1 variant, one GPU, no MPI) is six kernels on the
-// context's stream, captured once into a CUDA graph and replayed:
-//   k_move_y   per tile: pending y move (Eq. 2.21) and the tile term
-//              cy*pi_y + cx*pi_x that rules 2 and 3 (Eq. 2.22, 2.23) add to every z
-//   k_move_z   class-owned z move (Eq. 2.20 + 2.22 + 2.23, combined as in the
-//              proof of Theorem 1), in place on D^ (Section 3.3)
-//   k_lap(Z)   n^2 (n-1)^2 LAPs of size n-2 on the tiles of D^
-//   k_lap(Y)   n^2 LAPs of size n-1 on C^ + Theta (fold fused into the tile load),
-//              writes pi_y
-//   k_lap(X)   one LAP of size n on b' + Delta, writes pi_x
-//   k_finalize bound, best bound, upper bound of the X primal, the feasibility
-//              check that follows Algorithm 1, stop flags, bound history
-// The ascent step of iteration m runs at the start of iteration m+1, so after
-// every call the state, duals and reduced costs describe the same multipliers.
-// Device-side flags (done / have_snapshot) make every kernel a no-op after a
-// stop, so whole batches of iterations can be enqueued without host round trips.
+// One iteration (Algorithm 2 on one GPU, no MPI; S or F variant, Section 3.4)
+// is these kernels on the context's stream:
+//   k_move_y     per tile: pending y move (Eq. 2.21; the F and half-Z forms)
+//                and the tile term cy*pi_y + cx*pi_x that rules 2 and 3
+//                (Eq. 2.22, 2.23) add to every z pool, plus an accepted Type 4
+//                amount (Section 2.3 rule 4)
+//   k_shift_psi  psi <- psi - tile term for the folded z move (kz = 1, equal phi)
+//   k_move_z     class-owned z move (Eq. 2.20 + 2.22 + 2.23, combined as in the
+//                proof of Theorem 1), in place on D^ (Section 3.3)
+//   k_lap(Z)     n^2 (n-1)^2 LAPs of size n-2 on the tiles of D^ (half of them
+//                with the half-Z scheme, Section 5)
+//   [k_phase2, k_lap(Z)]  the two-phase Z solve (Section 3.4)
+//   k_lap(Y)     n^2 LAPs of size n-1 on C^ + Theta (fold fused into the tile
+//                load), writes pi_y
+//   k_lap(X)     one LAP of size n on b' + Delta, writes pi_x
+//   k_finalize   bound, best bound, upper bound of the X primal, the feasibility
+//                check that follows Algorithm 1, stop flags, bound history
+// A context's first 64 iterations are launched kernel by kernel, later ones as
+// replays of one captured CUDA graph.  The ascent step of iteration m runs at
+// the start of iteration m+1, so after every call the state, duals and reduced
+// costs describe the same multipliers.  Device-side flags (done / have_snap)
+// make every kernel a no-op after a stop, so whole batches of iterations can
+// be enqueued without host round trips.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -801,8 +809,9 @@ FinArgs rlt2::make_fin(const IterView& v) {
   return f;
 }
 
-// Enqueue one iteration (six kernels) on stream s.  With ev != nullptr, the 12
-// events ev[2k], ev[2k+1] bracket kernel k.
+// Enqueue one iteration on stream s.  With ev != nullptr, the 2 kKinds events
+// ev[2k], ev[2k+1] bracket timing kind k (kinds 6 and 7, the second Z phase,
+// are empty intervals without two_phase); launched[k] counts the kernels.
 cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent_t* ev, int* launched) {
   auto count = [&](int k, int nk) {
     if (launched) launched[k] += nk;

@@ -109,7 +109,7 @@ struct IterView {
   DevScalars* sc;
 };
 
-// Step A0 (setup kernels) and one iteration (six kernels) on a view.
+// Step A0 (setup kernels) and one iteration (seven to nine kernels) on a view.
 cudaError_t enqueue_setup(const IterView& v, int n_full, const double* dF, const double* dD, const double* dB,
                           const int* dfac, const int* dloc, const int* dfixf, const int* dfixl, int nfix,
                           cudaStream_t s);
