@@ -57,7 +57,7 @@ def measured_peaks():
 # until one of them changes)
 KERNEL_SOURCES = {
     "lap_z": ["lap.cu", "rlt2_lap.cuh", "rlt2_internal.h"],
-    "move_z": ["ascent.cu", "rlt2_ascent.cuh", "rlt2_internal.h"],
+    "move_z": ["rlt2_ascent.cuh", "rlt2_internal.h"],
 }
 
 
