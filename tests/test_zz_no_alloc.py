@@ -64,3 +64,24 @@ def test_noalloc_rejects_sizes_beyond_the_workspace(R):
     with pytest.raises(R.Rlt2Error) as e:
         _noalloc_bounds(R, inst, 3, None)
     assert e.value.status == R.RLT2_EINVAL and "n must be in [3, 10]" in str(e.value)
+
+
+@pytest.mark.parametrize("variant,two_phase", [(1, 0), (0, 1), (1, 1)])
+def test_noalloc_runs_the_variants(R, variant, two_phase):
+    """The fixed array also holds the F variant's x costs; the F variant and the
+    two-phase Z solve give the context path's trajectory (raw duals: identical)."""
+    inst = I.random_instance(9, 17, with_b=True, asymmetric=True)
+    prm = R.params(dual_mode=0, feas_tol=0.0, warm=1, variant=variant, two_phase=two_phase)
+    ref, done = _context_bounds(R, inst, 15, prm)
+    assert done == 15
+    got = _noalloc_bounds(R, inst, 15, prm)
+    assert np.array_equal(got, ref)
+
+
+def test_noalloc_rejects_the_half_z_scheme(R):
+    inst = I.config(1)
+    F = torch.from_numpy(inst.F).cuda()
+    D = torch.from_numpy(inst.D).cuda()
+    out = torch.empty(3, dtype=torch.float64, device="cuda")
+    with pytest.raises(R.Rlt2Error):
+        R.rlt2_iterate_noalloc(F, D, out, prm=R.half_z_params())
