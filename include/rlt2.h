@@ -57,9 +57,12 @@ typedef enum {
  *  phi_y      : varphi of Eq. 2.21 (y_ijpq <-> y_jiqp), in [0,1], phi_y + ky <= 1
  *  phi_z[5]   : phi_1..phi_5 of Eq. 2.20 (used by rules 1-3), each in [0,1],
  *               summing to 1 within 1e-12
- *  dual_mode  : 0 = the Hungarian's own duals, 1 = canonical duals (the
- *               pointwise-largest optimal row duals with u_0 = 0; unique for a
- *               given cost matrix, so warm and cold solves agree)
+ *  dual_mode  : 0 = the Hungarian's own duals (FP64, the CPU oracle's
+ *               operation order), 1 = canonical duals (the pointwise-largest
+ *               optimal row duals with u_0 = 0; unique for a given cost
+ *               matrix) computed exactly in 64-bit fixed point on a per-tile
+ *               grid of 2^-48 of the tile's magnitude bound, so warm and cold
+ *               solves agree bit for bit, 2 = canonical duals computed in FP64
  *  warm       : 0 = cold LAPs, 1 = start every Z, Y and X LAP from its
  *               previous iteration's row duals, 2 = as 1 but the Z-LAPs start
  *               from row duals predicted by the network attached with
@@ -269,7 +272,8 @@ rlt2_status rlt2_destroy(rlt2_ctx* ctx);
  *  u, v     : device, batch*m row / column duals (nullable)
  *  row_to_col: device, batch*m assignment (nullable)
  *  n_aug    : device, batch augmenting searches per LAP (nullable)
- *  dual_mode: 0 raw, 1 canonical.  Asynchronous on `stream`. */
+ *  dual_mode: 0 raw (FP64), 1 canonical (exact fixed point), 2 canonical
+ *             (FP64), as in rlt2_params.  Asynchronous on `stream`. */
 rlt2_status rlt2_lap_batched(int batch, int m, const double* cost, const double* u0, double* value, double* u,
                              double* v, int* row_to_col, int* n_aug, int dual_mode, void* stream);
 

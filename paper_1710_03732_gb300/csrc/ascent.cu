@@ -380,7 +380,7 @@ bool rlt2::params_valid(const rlt2_params& p) {
     s += p.phi_z[l];
   }
   if (std::fabs(s - 1.0) > 1e-12) return false;
-  if (p.dual_mode != 0 && p.dual_mode != 1) return false;
+  if (p.dual_mode < 0 || p.dual_mode > 2) return false;
   if (p.warm < 0 || p.warm > 2) return false;
   if (!std::isfinite(p.min_gap) || !std::isfinite(p.ub) || !std::isfinite(p.feas_tol)) return false;
   if (p.stall_window < 0 || p.stall_window >= kStallRing || !std::isfinite(p.stall_tol)) return false;

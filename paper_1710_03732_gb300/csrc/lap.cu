@@ -2,6 +2,7 @@
 #include <cmath>
 #include <cstdio>
 #include <mutex>
+#include <type_traits>
 
 #include "rlt2_internal.h"
 #include "rlt2_lap.cuh"
@@ -19,11 +20,72 @@ __host__ __device__ inline size_t warp_smem_bytes(int m, int G) {
 
 int default_group(int m) { return m <= 8 ? 8 : (m <= 16 ? 16 : 32); }
 
-// Grid-stride over LAPs, 32/G LAPs per warp per step; each group of G lanes
-// stages its own tile (coalesced: a group reads a contiguous m*m run).
-template <int G, bool PRE>
+// Stages one group's tile (plus an optional addend) into shared memory, the
+// group's G lanes reading a contiguous m*m run (coalesced).  FX: the tile is
+// rounded down onto the group's fixed-point grid and the grid exponent L is
+// returned (0 for FP64).  All 32 lanes call it; src == nullptr for a group
+// without a LAP.
+template <int G, bool FX>
+__device__ __forceinline__ int stage_tile(typename std::conditional<FX, long long, double>::type* tile, int ld,
+                                          int m, int gl, const double* src, const double* add) {
+  const int mm = m * m;
+  if constexpr (!FX) {
+    if (src) {
+      for (int e = gl; e < mm; e += G) {
+        const int r = e / m, c = e - r * m;
+        double x = __ldcs(src + e);
+        if (add) x = __dadd_rn(x, __ldcs(add + e));
+        tile[r * ld + c] = x;
+      }
+    }
+    return 0;
+  } else {
+    unsigned eb = 0;
+    if (src) {
+      for (int e = gl; e < mm; e += G) {
+        const int r = e / m, c = e - r * m;
+        double x = __ldcs(src + e);
+        if (add) x = __dadd_rn(x, __ldcs(add + e));
+        tile[r * ld + c] = __double_as_longlong(x);  // bits; converted below once the grid is known
+        eb = max(eb, fx_expfield(x));
+      }
+    }
+    if constexpr (G == 32) {
+      eb = __reduce_max_sync(kFull, eb);
+    } else {
+#pragma unroll
+      for (int off = G / 2; off > 0; off >>= 1) eb = max(eb, __shfl_xor_sync(kFull, eb, off));
+    }
+    const int L = fx_grid(eb);
+    if (src) {
+      for (int e = gl; e < mm; e += G) {  // the entries this lane wrote
+        const int r = e / m, c = e - r * m;
+        tile[r * ld + c] = fx_floor(__longlong_as_double(tile[r * ld + c]), L, kFxEntryBits);
+      }
+    }
+    return L;
+  }
+}
+
+template <bool FX, typename T>
+__device__ __forceinline__ double out_value(T x, int L) {
+  if constexpr (FX) return fx_to_double(x, L);
+  else return x;
+}
+
+template <bool FX>
+__device__ __forceinline__ typename std::conditional<FX, long long, double>::type start_dual(double u0, int L) {
+  if constexpr (FX) return fx_floor(u0, L, kFxStartBits);
+  else return u0;
+}
+
+// Grid-stride over LAPs, 32/G LAPs per warp per step.  FX selects the exact
+// fixed-point arithmetic (canonical duals), else FP64.
+template <int G, bool PRE, bool FX>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap(LapArgs a) {
   if (a.skip && *a.skip) return;
+  using A = typename std::conditional<FX, ArithFx, ArithF64>::type;
+  using T = typename A::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int per = 32 / G;
   const int lane = threadIdx.x & 31;
@@ -33,8 +95,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap(LapArgs a) {
   const int m = a.m;
   const int ld = tile_ld(m);
   unsigned char* base = smem_raw + (size_t)wib * warp_smem_bytes(m, G);
-  double* tile = reinterpret_cast<double*>(base) + (size_t)grp * m * ld;
-  double* uv = reinterpret_cast<double*>(base) + (size_t)per * m * ld;  // [0..31] u, [32..63] v
+  T* tile = reinterpret_cast<T*>(base) + (size_t)grp * m * ld;
+  T* uv = reinterpret_cast<T*>(base) + (size_t)per * m * ld;  // [0..31] u, [32..63] v
   int* scr = reinterpret_cast<int*>(uv + 64) + grp * G;
   const bool warm = a.u0 != nullptr && (a.warm_gate == nullptr || *a.warm_gate != 0);
   const long long nwarps = (long long)gridDim.x * wpb;
@@ -45,28 +107,21 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap(LapArgs a) {
     const long long tb = t0 + grp;
     const bool have = tb < a.batch;
     const long long t = (have && a.map) ? (long long)a.map[tb] : tb;
-    if (have) {
-      const double* src = a.A + t * mm;
-      const double* add = a.Badd ? a.Badd + t * mm : nullptr;
-      for (int e = gl; e < mm; e += G) {
-        const int r = e / m, c = e - r * m;
-        double x = __ldcs(src + e);
-        if (add) x = __dadd_rn(x, __ldcs(add + e));
-        tile[r * ld + c] = x;
-      }
-    }
-    double u0 = 0.0;
-    if (warm && have && gl < m) u0 = a.u0[t * m + gl];
+    const int L = stage_tile<G, FX>(tile, ld, m, gl, have ? a.A + t * mm : nullptr,
+                                    (have && a.Badd) ? a.Badd + t * mm : nullptr);
+    T u0 = T(0);
+    if (warm && have && gl < m) u0 = start_dual<FX>(a.u0[t * m + gl], L);
     __syncwarp();
     // without a reduced-cost output (PRE) the tile may be overwritten by the canonical pass
-    const WarpLapResult R = group_lap<G, PRE>(tile, ld, have ? m : 0, lane, warm, u0, a.dual_mode, scr, uv + grp * G);
+    const WarpLapResult<T> R =
+        group_lap<G, PRE, A>(tile, ld, have ? m : 0, lane, warm, u0, a.dual_mode, scr, uv + grp * G);
     if (have && gl < m) {
-      if (a.u) a.u[t * m + gl] = R.u;
-      if (a.v) a.v[t * m + gl] = R.v;
+      if (a.u) a.u[t * m + gl] = out_value<FX>(R.u, L);
+      if (a.v) a.v[t * m + gl] = out_value<FX>(R.v, L);
       if (a.r2c) a.r2c[t * m + gl] = R.r2c;
     }
     if (have && gl == 0) {
-      a.value[t] = R.value;
+      a.value[t] = out_value<FX>(R.value, L);
       if (a.naug) a.naug[t] = R.naug;
       aug_acc += R.naug;
       relax_acc += R.nrelax;
@@ -77,11 +132,11 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap(LapArgs a) {
       __syncwarp();
       if (have) {
         double* dst = a.pi + t * mm;
-        const double* ug = uv + grp * G;
-        const double* vg = uv + 32 + grp * G;
+        const T* ug = uv + grp * G;
+        const T* vg = uv + 32 + grp * G;
         for (int e = gl; e < mm; e += G) {
           const int r = e / m, c = e - r * m;
-          dst[e] = __dsub_rn(__dsub_rn(tile[r * ld + c], ug[r]), vg[c]);
+          dst[e] = out_value<FX>(A::sub(A::sub(tile[r * ld + c], ug[r]), vg[c]), L);
         }
       }
     }
@@ -102,26 +157,38 @@ static int g_occ[33][3][2];
 
 static int gidx(int G) { return G == 8 ? 0 : (G == 16 ? 1 : 2); }
 
+using LapKernel = void (*)(LapArgs);
+
+// The kernel for (group, in-place canonical pass, fixed-point arithmetic).
 template <int G>
-static cudaError_t prepare_one(int m, int wpb) {
+static LapKernel lap_kernel(bool pre, bool fx) {
+  if (pre) return fx ? k_lap<G, true, true> : k_lap<G, true, false>;
+  return fx ? k_lap<G, false, true> : k_lap<G, false, false>;
+}
+static LapKernel lap_kernel(int G, bool pre, bool fx) {
+  return G == 8 ? lap_kernel<8>(pre, fx) : (G == 16 ? lap_kernel<16>(pre, fx) : lap_kernel<32>(pre, fx));
+}
+
+// Occupancy of the slowest of the four forms, so that one grid size serves all.
+static cudaError_t prepare_one(int G, int m, int wpb) {
   int& slot = g_occ[m][gidx(G)][wpb == 4 ? 0 : 1];
   if (slot > 0) return cudaSuccess;
   static bool attr_set[3] = {false, false, false};
   cudaError_t e;
   const int cap = (int)(warp_smem_bytes(32, 32) * kMaxWarpsPerBlock);
-  if (!attr_set[gidx(G)]) {
-    if ((e = cudaFuncSetAttribute(k_lap<G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess)
-      return e;
-    if ((e = cudaFuncSetAttribute(k_lap<G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess)
-      return e;
-    attr_set[gidx(G)] = true;
+  int occ = 1 << 20;
+  for (int k = 0; k < 4; ++k) {
+    const LapKernel kern = lap_kernel(G, (k & 1) != 0, (k & 2) != 0);
+    if (!attr_set[gidx(G)]) {
+      if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess)
+        return e;
+    }
+    int o = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, wpb * 32, warp_smem_bytes(m, G) * wpb);
+    if (e != cudaSuccess) return e;
+    occ = o < occ ? o : occ;
   }
-  int occ = 0, occ2 = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lap<G, true>, wpb * 32, warp_smem_bytes(m, G) * wpb);
-  if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_lap<G, false>, wpb * 32, warp_smem_bytes(m, G) * wpb);
-  if (e != cudaSuccess) return e;
-  occ = occ < occ2 ? occ : occ2;
+  attr_set[gidx(G)] = true;
   slot = occ < 1 ? 1 : occ;
   return cudaSuccess;
 }
@@ -140,9 +207,7 @@ cudaError_t prepare_lap(int m, int group, int warps_per_block) {
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   }
-  if (G == 8) return prepare_one<8>(m, wpb);
-  if (G == 16) return prepare_one<16>(m, wpb);
-  return prepare_one<32>(m, wpb);
+  return prepare_one(G, m, wpb);
 }
 
 cudaError_t launch_lap(const LapArgs& a, cudaStream_t s) {
@@ -156,17 +221,8 @@ cudaError_t launch_lap(const LapArgs& a, cudaStream_t s) {
   const long long need = (a.batch + per_block - 1) / per_block;
   const long long cap = (long long)g_sms * g_occ[a.m][gidx(G)][wpb == 4 ? 0 : 1];
   const int grid = (int)(need < cap ? need : cap);
-  const bool pre = a.pi == nullptr;
-  if (G == 8) {
-    if (pre) k_lap<8, true><<<grid, wpb * 32, smem, s>>>(a);
-    else k_lap<8, false><<<grid, wpb * 32, smem, s>>>(a);
-  } else if (G == 16) {
-    if (pre) k_lap<16, true><<<grid, wpb * 32, smem, s>>>(a);
-    else k_lap<16, false><<<grid, wpb * 32, smem, s>>>(a);
-  } else {
-    if (pre) k_lap<32, true><<<grid, wpb * 32, smem, s>>>(a);
-    else k_lap<32, false><<<grid, wpb * 32, smem, s>>>(a);
-  }
+  const LapKernel kern = lap_kernel(G, a.pi == nullptr, a.dual_mode == 1);
+  kern<<<grid, wpb * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -174,8 +230,10 @@ cudaError_t launch_lap(const LapArgs& a, cudaStream_t s) {
 // Batched branch-and-bound nodes: one persistent launch per stage over the LAPs
 // of every node of a wave.  Warps pull 32/G LAPs at a time from a device queue
 // (atomic head, no waiting), so nodes of uneven size share the GPU.
-template <int G, bool PRE>
+template <int G, bool PRE, bool FX>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap_nodes(NodeLapArgs a) {
+  using A = typename std::conditional<FX, ArithFx, ArithF64>::type;
+  using T = typename A::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int per = 32 / G;
   long long* s_prefix = reinterpret_cast<long long*>(smem_raw);
@@ -187,8 +245,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap_nodes(NodeLapArg
   const size_t pre = (((size_t)(a.nnodes + 1) * sizeof(long long)) + 255) & ~size_t(255);
   const int MM = a.max_m;
   unsigned char* base = smem_raw + pre + (size_t)wib * warp_smem_bytes(MM, G);
-  double* tile = reinterpret_cast<double*>(base) + (size_t)grp * MM * tile_ld(MM);
-  double* uv = reinterpret_cast<double*>(base) + (size_t)per * MM * tile_ld(MM);
+  T* tile = reinterpret_cast<T*>(base) + (size_t)grp * MM * tile_ld(MM);
+  T* uv = reinterpret_cast<T*>(base) + (size_t)per * MM * tile_ld(MM);
   int* scr = reinterpret_cast<int*>(uv + 64) + grp * G;
   unsigned long long aug_acc = 0, relax_acc = 0;
   for (;;) {
@@ -216,27 +274,19 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap_nodes(NodeLapArg
     const int m = have ? it.m : 0;
     const int ld = tile_ld(m);
     const int mm = m * m;
-    if (have) {
-      const double* src = it.A + li * mm;
-      const double* add = it.Badd ? it.Badd + li * mm : nullptr;
-      for (int e = gl; e < mm; e += G) {
-        const int r = e / m, c = e - r * m;
-        double x = __ldcs(src + e);
-        if (add) x = __dadd_rn(x, __ldcs(add + e));
-        tile[r * ld + c] = x;
-      }
-    }
+    const int L = stage_tile<G, FX>(tile, ld, m, gl, have ? it.A + li * mm : nullptr,
+                                    (have && it.Badd) ? it.Badd + li * mm : nullptr);
     const bool warm = have && it.u0 != nullptr && (it.warm_gate == nullptr || *it.warm_gate != 0);
-    const double u0 = (warm && gl < m) ? it.u0[li * m + gl] : 0.0;
+    const T u0 = (warm && gl < m) ? start_dual<FX>(it.u0[li * m + gl], L) : T(0);
     __syncwarp();
-    const WarpLapResult R = group_lap<G, PRE>(tile, ld, m, lane, warm, u0, a.dual_mode, scr, uv + grp * G);
+    const WarpLapResult<T> R = group_lap<G, PRE, A>(tile, ld, m, lane, warm, u0, a.dual_mode, scr, uv + grp * G);
     if (have && gl < m) {
-      if (it.u) it.u[li * m + gl] = R.u;
-      if (it.v) it.v[li * m + gl] = R.v;
+      if (it.u) it.u[li * m + gl] = out_value<FX>(R.u, L);
+      if (it.v) it.v[li * m + gl] = out_value<FX>(R.v, L);
       if (it.r2c) it.r2c[li * m + gl] = R.r2c;
     }
     if (have && gl == 0) {
-      it.value[li] = R.value;
+      it.value[li] = out_value<FX>(R.value, L);
       aug_acc += R.naug;
       relax_acc += R.nrelax;
     }
@@ -245,11 +295,11 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap_nodes(NodeLapArg
     __syncwarp();
     if (have && it.pi) {
       double* dst = it.pi + li * mm;
-      const double* ug = uv + grp * G;
-      const double* vg = uv + 32 + grp * G;
+      const T* ug = uv + grp * G;
+      const T* vg = uv + 32 + grp * G;
       for (int e = gl; e < mm; e += G) {
         const int r = e / m, c = e - r * m;
-        dst[e] = __dsub_rn(__dsub_rn(tile[r * ld + c], ug[r]), vg[c]);
+        dst[e] = out_value<FX>(A::sub(A::sub(tile[r * ld + c], ug[r]), vg[c]), L);
       }
     }
     __syncwarp();
@@ -258,6 +308,17 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap_nodes(NodeLapArg
     atomicAdd(a.stats + 0, aug_acc);
     atomicAdd(a.stats + 1, relax_acc);
   }
+}
+
+using NodeLapKernel = void (*)(NodeLapArgs);
+
+template <int G>
+static NodeLapKernel node_lap_kernel(bool pre, bool fx) {
+  if (pre) return fx ? k_lap_nodes<G, true, true> : k_lap_nodes<G, true, false>;
+  return fx ? k_lap_nodes<G, false, true> : k_lap_nodes<G, false, false>;
+}
+static NodeLapKernel node_lap_kernel(int G, bool pre, bool fx) {
+  return G == 8 ? node_lap_kernel<8>(pre, fx) : (G == 16 ? node_lap_kernel<16>(pre, fx) : node_lap_kernel<32>(pre, fx));
 }
 
 static int g_occ_nodes[33][3][2];
@@ -281,56 +342,32 @@ cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s) {
   const size_t cap_smem = (((size_t)(kMaxWaveNodes + 1) * sizeof(long long)) + 255) / 256 * 256 +
                           warp_smem_bytes(32, 32) * kMaxWarpsPerBlock;
   int& occ = g_occ_nodes[a.max_m][gidx(G)][wpb == 4 ? 0 : 1];
-  auto setup = [&](auto kern) -> cudaError_t {
-    cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap_smem);
-    if (e2 != cudaSuccess) return e2;
-    int o = 0;
-    e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, wpb * 32, smem);
-    if (e2 != cudaSuccess) return e2;
-    if (!occ || o < occ) occ = o;
-    return cudaSuccess;
-  };
-  if (!attr_set[gidx(G)]) {
-    if (G == 8) {
-      if ((e = setup(k_lap_nodes<8, true>)) != cudaSuccess || (e = setup(k_lap_nodes<8, false>)) != cudaSuccess) return e;
-    } else if (G == 16) {
-      if ((e = setup(k_lap_nodes<16, true>)) != cudaSuccess || (e = setup(k_lap_nodes<16, false>)) != cudaSuccess)
-        return e;
-    } else {
-      if ((e = setup(k_lap_nodes<32, true>)) != cudaSuccess || (e = setup(k_lap_nodes<32, false>)) != cudaSuccess)
-        return e;
+  // occupancy of the slowest of the four forms, computed once per size (the
+  // prefix table's share of shared memory varies with the node count; a grid
+  // above the resident count only queues blocks, which never wait on others)
+  if (!occ) {
+    int lo = 1 << 20;
+    for (int k = 0; k < 4; ++k) {
+      const NodeLapKernel kern = node_lap_kernel(G, (k & 1) != 0, (k & 2) != 0);
+      if (!attr_set[gidx(G)]) {
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap_smem)) !=
+            cudaSuccess)
+          return e;
+      }
+      int o = 0;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, wpb * 32, smem)) != cudaSuccess) return e;
+      lo = o < lo ? o : lo;
     }
     attr_set[gidx(G)] = true;
-  } else if (!occ) {
-    int o1 = 0, o2 = 0;
-    if (G == 8) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_lap_nodes<8, true>, wpb * 32, smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_lap_nodes<8, false>, wpb * 32, smem);
-    } else if (G == 16) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_lap_nodes<16, true>, wpb * 32, smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_lap_nodes<16, false>, wpb * 32, smem);
-    } else {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_lap_nodes<32, true>, wpb * 32, smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_lap_nodes<32, false>, wpb * 32, smem);
-    }
-    occ = o1 < o2 ? o1 : o2;
+    occ = lo < 1 ? 1 : lo;
   }
-  if (occ < 1) occ = 1;
   const long long cap = (long long)g_sms * occ;
   lock.unlock();
   const long long per_block = (long long)wpb * (32 / G);
   const long long need = (a.total + per_block - 1) / per_block;
   const int grid = (int)(need < cap ? need : cap);
-  if (G == 8) {
-    if (a.pre) k_lap_nodes<8, true><<<grid, wpb * 32, smem, s>>>(a);
-    else k_lap_nodes<8, false><<<grid, wpb * 32, smem, s>>>(a);
-  } else if (G == 16) {
-    if (a.pre) k_lap_nodes<16, true><<<grid, wpb * 32, smem, s>>>(a);
-    else k_lap_nodes<16, false><<<grid, wpb * 32, smem, s>>>(a);
-  } else {
-    if (a.pre) k_lap_nodes<32, true><<<grid, wpb * 32, smem, s>>>(a);
-    else k_lap_nodes<32, false><<<grid, wpb * 32, smem, s>>>(a);
-  }
+  const NodeLapKernel kern = node_lap_kernel(G, a.pre, a.dual_mode == 1);
+  kern<<<grid, wpb * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -341,7 +378,7 @@ using namespace rlt2;
 extern "C" rlt2_status rlt2_lap_batched(int batch, int m, const double* cost, const double* u0, double* value,
                                         double* u, double* v, int* row_to_col, int* n_aug, int dual_mode,
                                         void* stream) {
-  if (batch < 0 || m < 1 || m > 32 || (batch > 0 && (!cost || !value)) || (dual_mode != 0 && dual_mode != 1)) {
+  if (batch < 0 || m < 1 || m > 32 || (batch > 0 && (!cost || !value)) || dual_mode < 0 || dual_mode > 2) {
     set_error("rlt2_lap_batched: invalid argument");
     return RLT2_EINVAL;
   }

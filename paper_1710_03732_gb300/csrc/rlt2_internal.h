@@ -22,7 +22,7 @@ struct LapArgs {
   int* r2c;                  // nullable, batch*m
   int* naug;                 // nullable, batch
   double* pi;                // nullable, batch*m*m reduced costs ((cost - u_r) - v_c)
-  int dual_mode;             // 0 raw, 1 canonical
+  int dual_mode;             // 0 raw (FP64), 1 canonical (fixed point), 2 canonical (FP64)
   unsigned long long* stats; // nullable, [0] += augmentations, [1] += relaxations
   const int* skip;           // nullable: kernel does nothing when *skip != 0
   int group;                 // lanes per LAP (8, 16 or 32); 0 = smallest that fits m

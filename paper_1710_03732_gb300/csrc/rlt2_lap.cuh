@@ -16,8 +16,26 @@
 // two-step warp integer min reduction (redux.sync) plus a ballot.  The only
 // FP64 instructions left are the additions the method needs.
 //
-// Arithmetic order (shared with the CPU oracle by specification, so raw-mode
-// results match it bit for bit):
+// Two arithmetic forms, chosen per launch:
+//   FP64      IEEE double, round to nearest, in the CPU oracle's operation order
+//             (raw duals match it bit for bit); used for raw duals and for the
+//             FP64 canonical mode.
+//   fixed     exact 64-bit integer arithmetic on a per-tile grid (canonical
+//             duals, the default).  The tile is rounded down onto the grid
+//             2^L with L = E - 48, where 2^E bounds every |entry|; the start
+//             duals are rounded down and clamped to |u0| <= 2^(E+1).  Every
+//             quantity the Hungarian and the canonical pass form then stays
+//             below 2^59 grid steps for m <= 32 (labels are bounded by the
+//             growth of the matching cost, duals by the labels), so no
+//             addition can overflow, and the result is the exact optimum and
+//             the exact canonical dual of the rounded tile (whose entries are
+//             within 2^-47 of the tile's magnitude of the given ones): the
+//             same for every start, so warm and cold solves agree bit for bit,
+//             and dual feasible for the given tile too (rounding down only
+//             lowers costs).  GB300 issues integer additions ~40x faster than
+//             FP64 ones.
+//
+// Arithmetic order (the oracle's, by specification):
 //   start     u = u0 or 0;  v_c = min_r (c_rc - u_r), ties to the lowest row
 //   greedy    column c takes its argmin row if no lower column took that row
 //   search    for every free row i (increasing): Dijkstra on reduced costs
@@ -27,7 +45,7 @@
 //   duals     v_c = v_c + (d_c - d_sink) on scanned columns, augment, then
 //             u_r = c_{r,sigma(r)} - v_{sigma(r)} for every matched row
 //   value     sum_r c_{r,sigma(r)} as a pairwise tree (lane i += lane i+h, h = P/2..1)
-//   canonical (dual_mode 1) Dijkstra from row 0 over arcs r'->r with weight
+//   canonical (dual_mode 1, 2) Dijkstra from row 0 over arcs r'->r with weight
 //             pi(r, sigma(r')) (>= 0), u^c_r = dist_r + (u_r - u_0),
 //             v^c_c = c_{sigma^-1(c),c} - u^c_{sigma^-1(c)}
 #pragma once
@@ -58,12 +76,71 @@ __device__ __forceinline__ int warp_argmin(unsigned long long key) {
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 
+// Arithmetic of group_lap: value type, subtraction, addition and an
+// order-preserving unsigned key.
+struct ArithF64 {
+  using T = double;
+  static __device__ __forceinline__ T sub(T a, T b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ T add(T a, T b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ unsigned long long key(T x) { return okey(x); }
+};
+struct ArithFx {
+  using T = long long;
+  static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
+  static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+  static __device__ __forceinline__ unsigned long long key(T x) {
+    return (unsigned long long)x ^ 0x8000000000000000ull;
+  }
+};
+
+// ---- fixed-point grid of a tile -------------------------------------------
+// Biased exponent field of a double (0 for zeros and subnormals).
+__device__ __forceinline__ unsigned fx_expfield(double x) {
+  return (unsigned)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ffull);
+}
+// Grid exponent L of a tile whose largest exponent field is eb: every entry is
+// below 2^E with E = max(eb, 1) - 1022, and L = E - 48.
+__device__ __forceinline__ int fx_grid(unsigned eb) { return (int)(eb ? eb : 1u) - 1070; }
+
+// floor(x / 2^L) for |x| < 2^(L + lim) (lim <= 53 + L - e_min keeps the shift
+// positive); larger |x| clamp to +-2^lim.  Integer operations only.
+__device__ __forceinline__ long long fx_floor(double x, int L, int lim) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int eb = (int)((b >> 52) & 0x7ffull);
+  const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (eb ? (1ull << 52) : 0ull);
+  const int e = (eb ? eb : 1) - 1075;  // |x| = mant * 2^e
+  const bool neg = (b >> 63) != 0;
+  if (e + 53 - L > lim) return neg ? -(1ll << lim) : (1ll << lim);
+  const int sh = L - e;                // >= 53 - lim > 0
+  unsigned long long q, lost;
+  if (sh >= 64) {
+    q = 0;
+    lost = mant;
+  } else {
+    q = mant >> sh;
+    lost = mant & ((1ull << sh) - 1ull);
+  }
+  const long long r = (long long)q;
+  return neg ? -r - (lost != 0) : r;
+}
+
+// q * 2^L rounded to the nearest double (L >= -1069 by construction of fx_grid).
+__device__ __forceinline__ double fx_to_double(long long q, int L) {
+  const double p2 = L >= -1022 ? __longlong_as_double((long long)(L + 1023) << 52)
+                               : __longlong_as_double(1ll << (L + 1074));
+  return __dmul_rn(__ll2double_rn(q), p2);
+}
+
+constexpr int kFxEntryBits = 48;  // |entry| < 2^48 grid steps
+constexpr int kFxStartBits = 49;  // |u0| <= 2^49 grid steps
+
+template <typename T>
 struct WarpLapResult {
-  double u;      // row dual of row `gl` (group lane)
-  double v;      // column dual of column `gl`
+  T u;           // row dual of row `gl` (group lane)
+  T v;           // column dual of column `gl`
   int r2c;       // column matched to row `gl`
   int c2r;       // row matched to column `gl`
-  double value;  // LAP optimum (all lanes of the group)
+  T value;       // LAP optimum (all lanes of the group)
   int naug;      // augmenting searches
   int nrelax;    // label relaxations (instrumentation for the roofline)
 };
@@ -101,28 +178,31 @@ __device__ __forceinline__ unsigned group_bits(unsigned ball, int gb) {
 // scratch, m the group's LAP size (0 = no LAP, 1 <= m <= G otherwise).  The
 // arithmetic is identical for every G.
 // PRE: the caller does not need the tile afterwards, so the canonical pass may
-// replace it by its reduced costs first (uvs: 64 doubles of group staging).
-template <int G, bool PRE>
-__device__ __forceinline__ WarpLapResult group_lap(double* __restrict__ cs, int ld, int m, int lane, bool warm,
-                                                   double u0, int dual_mode, int* scr, double* uvs) {
+// replace it by its reduced costs first (uvs: 64 values of group staging).
+// A: ArithF64 or ArithFx (the tile and u0 already on the grid).
+template <int G, bool PRE, typename A>
+__device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T* __restrict__ cs, int ld, int m,
+                                                                  int lane, bool warm, typename A::T u0,
+                                                                  int dual_mode, int* scr, typename A::T* uvs) {
+  using T = typename A::T;
   const int gl = lane & (G - 1);
   const int gb = lane - gl;
   const bool cv = gl < m;
   const int M = (G == 32) ? m : (int)__reduce_max_sync(kFull, (unsigned)m);
-  WarpLapResult R;
-  double u = (cv && warm) ? u0 : 0.0;
-  double v = 0.0;
+  WarpLapResult<T> R;
+  T u = (cv && warm) ? u0 : T(0);
+  T v = T(0);
   int naug = 0, nrelax = 0;
 
   // column reduction with the argmin row
   unsigned long long bestk = ~0ull;
   int arg = -1;
   for (int r = 0; r < M; ++r) {
-    const double ur = __shfl_sync(kFull, u, gb + r);
+    const T ur = __shfl_sync(kFull, u, gb + r);
     if (cv && r < m) {
-      const double c = cs[r * ld + gl];
-      const double x = warm ? dsub(c, ur) : c;  // c - 0 == c exactly
-      const unsigned long long k = okey(x);
+      const T c = cs[r * ld + gl];
+      const T x = warm ? A::sub(c, ur) : c;  // c - 0 == c exactly
+      const unsigned long long k = A::key(x);
       if (arg < 0 || k < bestk) {
         bestk = k;
         arg = r;
@@ -151,18 +231,18 @@ __device__ __forceinline__ WarpLapResult group_lap(double* __restrict__ cs, int 
       ++naug;
       nrelax += m;
     }
-    const double ui = __shfl_sync(kFull, u, gb + i);
-    double d = (act && cv) ? dsub(dsub(cs[i * ld + gl], ui), v) : 0.0;
-    unsigned long long dk = okey(d);
+    const T ui = __shfl_sync(kFull, u, gb + i);
+    T d = (act && cv) ? A::sub(A::sub(cs[i * ld + gl], ui), v) : T(0);
+    unsigned long long dk = A::key(d);
     int pred = i;
     bool scanned = !(act && cv);
     const unsigned freecols = group_bits<G>(__ballot_sync(kFull, cv && c2r < 0), gb);
     bool searching = act;
     int sink = 0;
-    double dlast = 0.0;
+    T dlast = T(0);
     while (__any_sync(kFull, searching)) {
       const int c = group_argmin<G>(scanned ? ~0ull : dk, gb);
-      const double dm = __shfl_sync(kFull, d, gb + c);
+      const T dm = __shfl_sync(kFull, d, gb + c);
       if (searching && gl == c) scanned = true;
       const bool found = searching && ((freecols >> c) & 1u);
       if (found) {
@@ -172,10 +252,10 @@ __device__ __forceinline__ WarpLapResult group_lap(double* __restrict__ cs, int 
       const bool relaxing = searching && !found;
       const int r0 = __shfl_sync(kFull, c2r, gb + c);
       const int r = r0 < 0 ? 0 : r0;
-      const double ur = __shfl_sync(kFull, u, gb + r);
+      const T ur = __shfl_sync(kFull, u, gb + r);
       if (relaxing && !scanned) {
-        const double nd = dadd(dm, dsub(dsub(cs[r * ld + gl], ur), v));
-        const unsigned long long nk = okey(nd);
+        const T nd = A::add(dm, A::sub(A::sub(cs[r * ld + gl], ur), v));
+        const unsigned long long nk = A::key(nd);
         if (nk < dk) {
           d = nd;
           dk = nk;
@@ -186,7 +266,7 @@ __device__ __forceinline__ WarpLapResult group_lap(double* __restrict__ cs, int 
       if (relaxing) nrelax += unsc;
       searching = relaxing;
     }
-    if (act && cv && scanned) v = dadd(v, dsub(d, dlast));
+    if (act && cv && scanned) v = A::add(v, A::sub(d, dlast));
     // augment back to row i (groups walk their own chains in lockstep)
     bool walking = act;
     int col = sink;
@@ -201,24 +281,24 @@ __device__ __forceinline__ WarpLapResult group_lap(double* __restrict__ cs, int 
       }
     }
     const int mc = (cv && r2c >= 0) ? r2c : 0;
-    const double vm = __shfl_sync(kFull, v, gb + mc);
-    if (act && cv && r2c >= 0) u = dsub(cs[gl * ld + r2c], vm);
+    const T vm = __shfl_sync(kFull, v, gb + mc);
+    if (act && cv && r2c >= 0) u = A::sub(cs[gl * ld + r2c], vm);
   }
 
   // optimum: pairwise tree over P = next power of two >= m rows (empty rows add
   // nothing), lane i adding lane i + h for h = P/2, ..., 1
-  const double xr = cv ? cs[gl * ld + r2c] : 0.0;
+  const T xr = cv ? cs[gl * ld + r2c] : T(0);
   int P = 1;
   while (P < m) P <<= 1;
   const int PM = (G == 32) ? P : (int)__reduce_max_sync(kFull, (unsigned)P);
-  double val = xr;
+  T val = xr;
   for (int h = PM >> 1; h >= 1; h >>= 1) {
-    const double o = __shfl_xor_sync(kFull, val, h);
-    if (h < P) val = dadd(val, o);
+    const T o = __shfl_xor_sync(kFull, val, h);
+    if (h < P) val = A::add(val, o);
   }
   val = __shfl_sync(kFull, val, gb);
 
-  if (dual_mode == 1) {
+  if (dual_mode != 0) {
     // canonical duals: shortest paths from row 0 on reduced weights
     // pi(r, sigma(r')) = (c_{r,sigma(r')} - u_r) - v_{sigma(r')} >= 0
     const int s0 = __shfl_sync(kFull, r2c, gb);
@@ -228,45 +308,45 @@ __device__ __forceinline__ WarpLapResult group_lap(double* __restrict__ cs, int 
       __syncwarp();
       for (int e = gl; e < m * m; e += G) {
         const int r = e / m, c = e - r * m;
-        cs[r * ld + c] = dsub(dsub(cs[r * ld + c], uvs[r]), uvs[32 + c]);
+        cs[r * ld + c] = A::sub(A::sub(cs[r * ld + c], uvs[r]), uvs[32 + c]);
       }
       __syncwarp();
     }
-    const double vs0 = __shfl_sync(kFull, v, gb + (s0 < 0 ? 0 : s0));
-    double dist = 0.0;
+    const T vs0 = __shfl_sync(kFull, v, gb + (s0 < 0 ? 0 : s0));
+    T dist = T(0);
     if (cv && gl != 0) {
       if constexpr (PRE) dist = cs[gl * ld + s0];
-      else dist = dsub(dsub(cs[gl * ld + s0], u), vs0);
+      else dist = A::sub(A::sub(cs[gl * ld + s0], u), vs0);
     }
-    unsigned long long dk = okey(dist);
+    unsigned long long dk = A::key(dist);
     bool done = !cv || gl == 0;
     for (int it = 0; it < M - 2; ++it) {
       const bool stepping = it < m - 2;
       const int rs = group_argmin<G>(done ? ~0ull : dk, gb);
-      const double dr = __shfl_sync(kFull, dist, gb + rs);
+      const T dr = __shfl_sync(kFull, dist, gb + rs);
       if (stepping && gl == rs) done = true;
       const int s = __shfl_sync(kFull, r2c, gb + rs);
-      const double vs = __shfl_sync(kFull, v, gb + (s < 0 ? 0 : s));
+      const T vs = __shfl_sync(kFull, v, gb + (s < 0 ? 0 : s));
       if (stepping && !done) {
-        double w;
+        T w;
         if constexpr (PRE) w = cs[gl * ld + s];
-        else w = dsub(dsub(cs[gl * ld + s], u), vs);
-        const double nd = dadd(dr, w);
-        const unsigned long long nk = okey(nd);
+        else w = A::sub(A::sub(cs[gl * ld + s], u), vs);
+        const T nd = A::add(dr, w);
+        const unsigned long long nk = A::key(nd);
         if (nk < dk) {
           dist = nd;
           dk = nk;
         }
       }
     }
-    const double u0r = __shfl_sync(kFull, u, gb);
-    const double ucan = cv ? (m > 1 ? dadd(dist, dsub(u, u0r)) : 0.0) : 0.0;
+    const T u0r = __shfl_sync(kFull, u, gb);
+    const T ucan = cv ? (m > 1 ? A::add(dist, A::sub(u, u0r)) : T(0)) : T(0);
     // v_c = c_{sigma^-1(c), c} - u_{sigma^-1(c)}, from the matched row's own entry
-    const double wrow = dsub(xr, ucan);
+    const T wrow = A::sub(xr, ucan);
     const int rr = cv ? c2r : 0;
-    const double vcan = __shfl_sync(kFull, wrow, gb + rr);
+    const T vcan = __shfl_sync(kFull, wrow, gb + rr);
     u = ucan;
-    v = cv ? vcan : 0.0;
+    v = cv ? vcan : T(0);
   }
   R.u = u;
   R.v = v;

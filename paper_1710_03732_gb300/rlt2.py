@@ -154,8 +154,10 @@ def _stream(stream) -> Optional[int]:
 def params(kz=1.0, ky=0.5, kx=1.0, phi_y=0.5, phi_z=(0.2,) * 5, dual_mode=1, warm=0, min_gap=0.0, ub=0.0,
            feas_tol=1e-9, stall_window=0, stall_tol=0.0002, variant=0, two_phase=0, phase2_tol=1e-9, sa_t0=0.04,
            sa_cool=0.99, sa_period=100, half_z=0) -> rlt2_params:
-    """Parameters (variant 0 = S, 1 = F; two_phase; annealing schedule of the Type 4 rule;
-    half_z = the half-Z-LAP scheme, see half_z_params)."""
+    """Parameters (dual_mode 0 = raw FP64 Hungarian duals, 1 = canonical duals in exact
+    fixed point, 2 = canonical duals in FP64; variant 0 = S, 1 = F; two_phase;
+    annealing schedule of the Type 4 rule; half_z = the half-Z-LAP scheme, see
+    half_z_params)."""
     p = rlt2_params()
     lib().rlt2_params_default(ctypes.byref(p))
     p.kz, p.ky, p.kx, p.phi_y = kz, ky, kx, phi_y

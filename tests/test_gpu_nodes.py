@@ -29,7 +29,7 @@ def _nodes(n, depths, seed):
     return out
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_nodes_bit_identical_to_single_contexts(R, mode):
     """Each node of the batch follows exactly the trajectory of its own context
     (same kernels, same arithmetic; the batch only changes the launch shape)."""

@@ -3,7 +3,10 @@
 Tolerances: LAP optima within 1e-9 relative; every dual feasible (reduced costs
 >= -1e-9 relative); raw-mode Hungarian duals, assignments and the whole raw
 dual-ascent trajectory and state bit-identical (same operation order, lowest-
-index ties); canonical-mode bound trajectories within 1e-6 relative.
+index ties); canonical-mode bound trajectories within 1e-6 relative.  Canonical
+duals come in two arithmetic forms: exact 64-bit fixed point on a per-tile grid
+of 2^-48 of the tile's magnitude bound (dual_mode 1, the default) and FP64
+(dual_mode 2); both are held to the same tolerances against the FP64 oracle.
 """
 import os
 
@@ -78,8 +81,9 @@ def test_lap_batched_raw_bit_exact(R, m, kind):
         assert naug[b] == o.n_aug
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("m", [1, 2, 4, 9, 18, 28, 32])
-def test_lap_batched_canonical(R, m):
+def test_lap_batched_canonical(R, m, mode):
     rng = np.random.default_rng(100 + m)
     batch = 300
     c = np.concatenate([_rand_costs(rng, batch // 3, m, "real"), _rand_costs(rng, batch // 3, m, "int"),
@@ -88,7 +92,7 @@ def test_lap_batched_canonical(R, m):
     val = torch.empty(batch, dtype=torch.float64, device="cuda")
     u = torch.empty(batch, m, dtype=torch.float64, device="cuda")
     v = torch.empty_like(u)
-    R.rlt2_lap_batched(dc, val, u=u, v=v, dual_mode=1)
+    R.rlt2_lap_batched(dc, val, u=u, v=v, dual_mode=mode)
     torch.cuda.synchronize()
     val, u, v = val.cpu().numpy(), u.cpu().numpy(), v.cpu().numpy()
     for b in range(batch):
@@ -100,6 +104,67 @@ def test_lap_batched_canonical(R, m):
         assert abs(u[b].sum() + v[b].sum() - o.value) <= 1e-9 * scale * m
         assert np.allclose(u[b], o.u, rtol=0, atol=1e-9 * scale)
         assert np.allclose(v[b], o.v, rtol=0, atol=1e-9 * scale)
+
+
+def _fixed_point_solve(R, c, u0=None):
+    batch, m = c.shape[0], c.shape[1]
+    val = torch.empty(batch, dtype=torch.float64, device="cuda")
+    u = torch.empty(batch, m, dtype=torch.float64, device="cuda")
+    v = torch.empty_like(u)
+    R.rlt2_lap_batched(torch.from_numpy(c).cuda(), val, u0=None if u0 is None else torch.from_numpy(u0).cuda(),
+                       u=u, v=v, dual_mode=1)
+    torch.cuda.synchronize()
+    return val.cpu().numpy(), u.cpu().numpy(), v.cpu().numpy()
+
+
+@pytest.mark.parametrize("m", [3, 7, 18, 28])
+def test_lap_fixed_point_start_independent(R, m):
+    """The fixed-point canonical duals are exact for the tile rounded onto its
+    grid, so every start (cold, good, poor, absurdly large) returns the same
+    value and duals bit for bit, and the duals are feasible for the given tile."""
+    rng = np.random.default_rng(300 + m)
+    batch = 200
+    c = rng.normal(size=(batch, m, m)) * 100.0
+    c[: batch // 4] = np.round(c[: batch // 4])
+    cold = _fixed_point_solve(R, c)
+    good = np.array([O.lap(c[b], canonical=True).u for b in range(batch)]) + rng.normal(size=(batch, m)) * 1e-3
+    starts = [good, rng.normal(size=(batch, m)) * 500.0, np.full((batch, m), 1e200),
+              np.where(rng.random((batch, m)) < 0.5, -1e300, 1e-300)]
+    for u0 in starts:
+        warm = _fixed_point_solve(R, c, u0)
+        for a, b in zip(cold, warm):
+            assert np.array_equal(a, b)
+    val, u, v = cold
+    for b in range(batch):
+        scale = np.abs(c[b]).max()
+        assert (c[b] - u[b][:, None] - v[b][None, :]).min() >= -1e-14 * scale * m
+        assert abs(val[b] - O.lap(c[b]).value) <= 1e-13 * scale * m
+
+
+@pytest.mark.parametrize("kind", ["tiny", "huge", "mixed", "zero_rows", "subnormal"])
+def test_lap_fixed_point_scales(R, kind):
+    """Tiles at the ends of the double range and with entries of very different
+    magnitude: the fixed-point solve stays within the FP64 oracle's tolerance."""
+    rng = np.random.default_rng({"tiny": 1, "huge": 2, "mixed": 3, "zero_rows": 4, "subnormal": 5}[kind])
+    batch, m = 64, 18
+    c = rng.normal(size=(batch, m, m))
+    if kind == "tiny":
+        c *= 1e-300
+    elif kind == "huge":
+        c *= 1e300
+    elif kind == "mixed":
+        c *= 10.0 ** rng.integers(-12, 12, (batch, m, m))
+    elif kind == "zero_rows":
+        c[:, ::3, :] = 0.0
+    else:
+        c *= 1e-310
+    val, u, v = _fixed_point_solve(R, c)
+    for b in range(batch):
+        o = O.lap(c[b], canonical=True)
+        scale = np.abs(c[b]).max()
+        assert abs(val[b] - o.value) <= 1e-9 * max(scale, abs(o.value)) + 1e-320
+        assert np.allclose(u[b], o.u, rtol=0, atol=1e-9 * scale + 1e-320)
+        assert np.allclose(v[b], o.v, rtol=0, atol=1e-9 * scale + 1e-320)
 
 
 def test_lap_batched_warm_start(R):
@@ -191,8 +256,10 @@ def _golden(name):
 
 @pytest.mark.parametrize("name,cfg,iters,mode", [
     ("lb_n8_grid2x4_canonical.txt", 1, 50, 1),
+    ("lb_n8_grid2x4_canonical.txt", 1, 50, 2),
     ("lb_n8_grid2x4_raw.txt", 1, 50, 0),
     ("lb_n12_grid3x4_canonical.txt", 2, 200, 1),
+    ("lb_n12_grid3x4_canonical.txt", 2, 200, 2),
     ("lb_n12_grid3x4_raw.txt", 2, 200, 0),
 ])
 def test_trajectory_matches_golden(R, name, cfg, iters, mode):
@@ -390,7 +457,8 @@ def test_n30_full_size_sampled(R):
 def test_warm_start_raw_bit_exact_and_canonical_equal(R, which):
     """warm = 1 starts every Z, Y and X LAP from its previous row duals.  Raw
     duals: the trajectory equals the oracle's warm run bit for bit.  Canonical
-    duals: the bounds equal those of the cold run (the start does not matter)."""
+    duals: the bounds equal those of the cold run (the start does not matter),
+    bit for bit, and so does the whole state, in fixed point."""
     partial = None
     if which == "cfg1":
         inst, iters = I.config(1), 25
@@ -404,11 +472,15 @@ def test_warm_start_raw_bit_exact_and_canonical_equal(R, which):
         raw, _ = ctx.iterate(iters)
     _, ref, _ = O.run(inst.F, inst.D, inst.B, iters=iters, dual_mode=0, partial=partial, warm=True, prm=_oprm())
     assert np.array_equal(raw, np.array(ref))
-    out = {}
-    for warm in (0, 1):
-        with R.Context(inst.F, inst.D, inst.B, partial=partial, prm=_prm(R, 1, warm=warm)) as ctx:
-            out[warm], _ = ctx.iterate(iters)
-    assert np.max(np.abs(out[1] - out[0]) / np.maximum(1.0, np.abs(out[0]))) <= 1e-9
+    for mode in (1, 2):
+        out = {}
+        for warm in (0, 1):
+            with R.Context(inst.F, inst.D, inst.B, partial=partial, prm=_prm(R, mode, warm=warm)) as ctx:
+                out[warm], _ = ctx.iterate(iters)
+                out[warm, "D"] = ctx.export_state()[0]
+        if mode == 1:  # exact arithmetic: the start cannot change anything
+            assert np.array_equal(out[1], out[0]) and np.array_equal(out[1, "D"], out[0, "D"])
+        assert np.max(np.abs(out[1] - out[0]) / np.maximum(1.0, np.abs(out[0]))) <= 1e-9
 
 
 def test_max_residual_size_n32_sampled(R):
