@@ -64,12 +64,16 @@ __device__ __forceinline__ unsigned long long okey(double x) {
   return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
-// Lane holding the least key; lowest lane on ties.
+// Lane holding the least key; lowest lane on ties.  The low words are compared
+// only when several lanes share the least high word (a warp-uniform branch).
 __device__ __forceinline__ int warp_argmin(unsigned long long key) {
   const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
   const unsigned mhi = __reduce_min_sync(kFull, hi);
-  const unsigned mlo = __reduce_min_sync(kFull, hi == mhi ? lo : 0xffffffffu);
-  const unsigned ball = __ballot_sync(kFull, hi == mhi && lo == mlo);
+  unsigned ball = __ballot_sync(kFull, hi == mhi);
+  if (ball & (ball - 1u)) {
+    const unsigned mlo = __reduce_min_sync(kFull, hi == mhi ? lo : 0xffffffffu);
+    ball = __ballot_sync(kFull, hi == mhi && lo == mlo);
+  }
   return __ffs(ball) - 1;
 }
 
@@ -80,12 +84,14 @@ __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a,
 // order-preserving unsigned key.
 struct ArithF64 {
   using T = double;
+  static constexpr bool kExact = false;  // rounded: keys are cached next to the values
   static __device__ __forceinline__ T sub(T a, T b) { return __dsub_rn(a, b); }
   static __device__ __forceinline__ T add(T a, T b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ unsigned long long key(T x) { return okey(x); }
 };
 struct ArithFx {
   using T = long long;
+  static constexpr bool kExact = true;  // exact: keys are the values with the sign bit flipped
   static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
   static __device__ __forceinline__ T add(T a, T b) { return a + b; }
   static __device__ __forceinline__ unsigned long long key(T x) {
@@ -103,25 +109,16 @@ __device__ __forceinline__ unsigned fx_expfield(double x) {
 __device__ __forceinline__ int fx_grid(unsigned eb) { return (int)(eb ? eb : 1u) - 1070; }
 
 // floor(x / 2^L) for |x| < 2^(L + lim) (lim <= 53 + L - e_min keeps the shift
-// positive); larger |x| clamp to +-2^lim.  Integer operations only.
+// positive); larger |x| clamp to +-2^lim.  Integer operations only: the signed
+// mantissa shifted right arithmetically is the floor for either sign.
 __device__ __forceinline__ long long fx_floor(double x, int L, int lim) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int eb = (int)((b >> 52) & 0x7ffull);
-  const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (eb ? (1ull << 52) : 0ull);
+  const long long b = __double_as_longlong(x);
+  const int eb = (int)((b >> 52) & 0x7ff);
+  const long long mant = (b & 0xFFFFFFFFFFFFFll) | (eb ? (1ll << 52) : 0ll);
   const int e = (eb ? eb : 1) - 1075;  // |x| = mant * 2^e
-  const bool neg = (b >> 63) != 0;
-  if (e + 53 - L > lim) return neg ? -(1ll << lim) : (1ll << lim);
-  const int sh = L - e;                // >= 53 - lim > 0
-  unsigned long long q, lost;
-  if (sh >= 64) {
-    q = 0;
-    lost = mant;
-  } else {
-    q = mant >> sh;
-    lost = mant & ((1ull << sh) - 1ull);
-  }
-  const long long r = (long long)q;
-  return neg ? -r - (lost != 0) : r;
+  if (e + 53 - L > lim) return b < 0 ? -(1ll << lim) : (1ll << lim);
+  const int sh = min(L - e, 63);       // >= 53 - lim > 0
+  return (b < 0 ? -mant : mant) >> sh;
 }
 
 // q * 2^L rounded to the nearest double (L >= -1069 by construction of fx_grid).
@@ -160,6 +157,25 @@ __device__ __forceinline__ int group_argmin(unsigned long long key, int gb) {
     }
     const unsigned ball = __ballot_sync(kFull, key == k);
     return __ffs((ball >> gb) & ((1u << G) - 1u)) - 1;
+  }
+}
+
+// Least key among the G lanes of this lane's group.  Every lane of the warp must call it.
+template <int G>
+__device__ __forceinline__ unsigned long long group_min(unsigned long long key) {
+  if constexpr (G == 32) {
+    const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+    const unsigned mhi = __reduce_min_sync(kFull, hi);
+    const unsigned mlo = __reduce_min_sync(kFull, hi == mhi ? lo : 0xffffffffu);
+    return ((unsigned long long)mhi << 32) | mlo;
+  } else {
+    unsigned long long k = key;
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+      const unsigned long long o = __shfl_xor_sync(kFull, k, off);
+      k = o < k ? o : k;
+    }
+    return k;
   }
 }
 
@@ -202,9 +218,8 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
     if (cv && r < m) {
       const T c = cs[r * ld + gl];
       const T x = warm ? A::sub(c, ur) : c;  // c - 0 == c exactly
-      const unsigned long long k = A::key(x);
-      if (arg < 0 || k < bestk) {
-        bestk = k;
+      if (arg < 0 || (A::kExact ? x < v : A::key(x) < bestk)) {
+        if constexpr (!A::kExact) bestk = A::key(x);
         arg = r;
         v = x;
       }
@@ -233,15 +248,16 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
     }
     const T ui = __shfl_sync(kFull, u, gb + i);
     T d = (act && cv) ? A::sub(A::sub(cs[i * ld + gl], ui), v) : T(0);
-    unsigned long long dk = A::key(d);
+    unsigned long long dk = A::key(d);  // cached key of d (rounded form only)
     int pred = i;
     bool scanned = !(act && cv);
     const unsigned freecols = group_bits<G>(__ballot_sync(kFull, cv && c2r < 0), gb);
     bool searching = act;
     int sink = 0;
+    int step = 0;  // columns scanned so far in this search (one per step)
     T dlast = T(0);
     while (__any_sync(kFull, searching)) {
-      const int c = group_argmin<G>(scanned ? ~0ull : dk, gb);
+      const int c = group_argmin<G>(scanned ? ~0ull : (A::kExact ? A::key(d) : dk), gb);
       const T dm = __shfl_sync(kFull, d, gb + c);
       if (searching && gl == c) scanned = true;
       const bool found = searching && ((freecols >> c) & 1u);
@@ -255,15 +271,13 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
       const T ur = __shfl_sync(kFull, u, gb + r);
       if (relaxing && !scanned) {
         const T nd = A::add(dm, A::sub(A::sub(cs[r * ld + gl], ur), v));
-        const unsigned long long nk = A::key(nd);
-        if (nk < dk) {
+        if (A::kExact ? nd < d : A::key(nd) < dk) {
           d = nd;
-          dk = nk;
+          if constexpr (!A::kExact) dk = A::key(nd);
           pred = r;
         }
       }
-      const int unsc = __popc(group_bits<G>(__ballot_sync(kFull, !scanned), gb));
-      if (relaxing) nrelax += unsc;
+      if (relaxing) nrelax += m - (++step);  // the columns still unscanned were relaxed
       searching = relaxing;
     }
     if (act && cv && scanned) v = A::add(v, A::sub(d, dlast));
@@ -302,13 +316,32 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
     // canonical duals: shortest paths from row 0 on reduced weights
     // pi(r, sigma(r')) = (c_{r,sigma(r')} - u_r) - v_{sigma(r')} >= 0
     const int s0 = __shfl_sync(kFull, r2c, gb);
-    if constexpr (PRE) {
+    if constexpr (PRE && A::kExact) {
+      // integer subtractions are cheap: each column's lane walks its column
+      uvs[gl] = u;
+      __syncwarp();
+      if (cv) {
+        for (int r = 0; r < m; ++r) cs[r * ld + gl] = A::sub(A::sub(cs[r * ld + gl], uvs[r]), v);
+      }
+      __syncwarp();
+    } else if constexpr (PRE) {
+      // an FP64 instruction costs the same with few lanes active, so the group's
+      // lanes take the m*m entries in row-major turns (every lane busy); (r, c)
+      // of entry gl + k*G advance without a division per entry
       uvs[gl] = u;
       uvs[32 + gl] = v;
       __syncwarp();
-      for (int e = gl; e < m * m; e += G) {
-        const int r = e / m, c = e - r * m;
-        cs[r * ld + c] = A::sub(A::sub(cs[r * ld + c], uvs[r]), uvs[32 + c]);
+      if (m > 0) {
+        const int qg = G / m, rg = G - qg * m;
+        int r = gl / m, c = gl - r * m;
+        for (; r < m; r += qg) {
+          cs[r * ld + c] = A::sub(A::sub(cs[r * ld + c], uvs[r]), uvs[32 + c]);
+          c += rg;
+          if (c >= m) {
+            c -= m;
+            ++r;
+          }
+        }
       }
       __syncwarp();
     }
@@ -318,24 +351,24 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
       if constexpr (PRE) dist = cs[gl * ld + s0];
       else dist = A::sub(A::sub(cs[gl * ld + s0], u), vs0);
     }
-    unsigned long long dk = A::key(dist);
     bool done = !cv || gl == 0;
+    unsigned long long dk = A::key(dist);  // cached key of dist (rounded form only)
     for (int it = 0; it < M - 2; ++it) {
       const bool stepping = it < m - 2;
-      const int rs = group_argmin<G>(done ? ~0ull : dk, gb);
+      const int rs = group_argmin<G>(done ? ~0ull : (A::kExact ? A::key(dist) : dk), gb);
       const T dr = __shfl_sync(kFull, dist, gb + rs);
       if (stepping && gl == rs) done = true;
       const int s = __shfl_sync(kFull, r2c, gb + rs);
-      const T vs = __shfl_sync(kFull, v, gb + (s < 0 ? 0 : s));
+      T vs = T(0);
+      if constexpr (!PRE) vs = __shfl_sync(kFull, v, gb + (s < 0 ? 0 : s));
       if (stepping && !done) {
         T w;
         if constexpr (PRE) w = cs[gl * ld + s];
         else w = A::sub(A::sub(cs[gl * ld + s], u), vs);
         const T nd = A::add(dr, w);
-        const unsigned long long nk = A::key(nd);
-        if (nk < dk) {
+        if (A::kExact ? nd < dist : A::key(nd) < dk) {
           dist = nd;
-          dk = nk;
+          if constexpr (!A::kExact) dk = A::key(nd);
         }
       }
     }
