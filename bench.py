@@ -38,6 +38,12 @@ KERNELS = ["move_y", "move_z", "lap_z", "lap_y", "lap_x", "finalize"]
 # 2 FP64 lane-ops per clock per SM; every DADD/DSUB/DMUL/DFMA counts as one op.
 FP64_PEAK_GOPS = 625.0
 FP64_UNIT = "G FP64 ops/s (one DADD/DSUB/DMUL/DFMA lane = 1 op)"
+# 64-bit integer add peak: GB300 retires 128 32-bit integer add lanes per clock
+# per SM (measured 127.2 with add.s32) and a 64-bit add is two of them (low
+# word, then high word with carry; measured 63.8 add.s64 lanes per clock per
+# SM), so 64 lane-ops x 152 SMs x 2.07 GHz.
+INT64_PEAK_GOPS = 64 * 152 * 2.07
+INT64_UNIT = "G int64 ops/s (one 64-bit add/sub lane = 1 op)"
 
 
 def env_rank():
@@ -209,8 +215,8 @@ def run_reference(args):
     return 0
 
 
-def timed_device_run(R, torch, inst, warm: int, steps: int, warmup: int, barrier):
-    prm = R.params(dual_mode=1, warm=warm, feas_tol=0.0)
+def timed_device_run(R, torch, inst, warm: int, steps: int, warmup: int, barrier, mode: int = 1, pipeline: int = 0):
+    prm = R.params(dual_mode=mode, warm=warm, feas_tol=0.0, pipeline=pipeline)
     ctx = R.Context(inst.F, inst.D, inst.B, prm=prm)
     ctx.iterate(warmup)
     s0 = ctx.stats()
@@ -240,7 +246,7 @@ def timed_device_run(R, torch, inst, warm: int, steps: int, warmup: int, barrier
     ctx.close()
     d = s1 - s0
     return dict(ms=ms, stats=d, kt=kt, lb=lb, best=best, ub=ub, iters=its, T=ctx.T, n=ctx.n, windows=windows,
-                warm=warm)
+                warm=warm, mode=mode)
 
 
 def run_profile_case(args):
@@ -499,6 +505,11 @@ def main():
     with ClockSampler(local) as clocks:
         cold = timed_device_run(R, torch, inst, 0, args.steps, args.warmup, barrier)
         warm = timed_device_run(R, torch, inst, 1, args.steps, args.warmup, barrier)
+        # the same ascent with the canonical duals computed in FP64 (dual_mode 2)
+        f64 = timed_device_run(R, torch, inst, 1, args.steps, args.warmup, barrier, mode=2)
+        # the z move and the next Z-LAPs as one launch (rlt2_params.pipeline)
+        pcold = timed_device_run(R, torch, inst, 0, args.steps, args.warmup, barrier, pipeline=1)
+        pwarm = timed_device_run(R, torch, inst, 1, args.steps, args.warmup, barrier, pipeline=1)
     clk = clocks.summary()
 
     # end to end through the C ABI with host buffers: create (H2D of F, D, B and
@@ -519,6 +530,9 @@ def main():
 
     warm_ms = per_rank_max(warm["ms"])
     cold_ms = per_rank_max(cold["ms"])
+    f64_ms = per_rank_max(f64["ms"])
+    pcold_ms = per_rank_max(pcold["ms"])
+    pwarm_ms = per_rank_max(pwarm["ms"])
     e2e_s = per_rank_max(e2e_s)
     if rank != 0:
         if dist is not None:
@@ -534,7 +548,8 @@ def main():
         cnt = max(cnt, 1)
         avg_ms = ms_lz / cnt
         aug, relax = int(r["stats"][1]), int(r["stats"][2])  # totals over the timed launches
-        # FP64 work the method needs in one Z-stage launch: 3 additions per label
+        # Additions the method needs in one Z-stage launch (64-bit integer ones
+        # in the fixed-point form, FP64 ones in dual_mode 2): 3 per label
         # relaxation (only unscanned columns count; the m start labels of a
         # search, which the counter includes, take 2), 3 per column per search
         # for the dual update and row duals; per LAP, m^2 for the warm start's column
@@ -547,6 +562,7 @@ def main():
         return avg_ms, per_launch, achieved
 
     avg_lz, fl_lz, ach_lz = lap_z_roofline(warm)
+    avg_lz64, fl_lz64, ach_lz64 = lap_z_roofline(f64)
     mz_ms = warm["kt"]["move_z"][0] / max(warm["kt"]["move_z"][1], 1)
     E = T * m * m
     # FP64 ops per z entry with kz = 1 and equal phi: 2 (pi_z) + 1 (s) + 5/6 (class
@@ -571,7 +587,9 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f64+i64",
+        "dtype_note": "FP64 state and multiplier moves (bit-exact with the oracle's operation order); "
+                      "LAPs in exact 64-bit fixed point on a per-tile grid of 2^-48 of the tile's magnitude",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "z_laps_per_iter": T, "z_lap_size": m, "z_entries": E,
                    "warm_start": "previous-iteration Z duals", "parallelism": f"replicas x{world}",
@@ -583,6 +601,7 @@ def main():
                        "ms_per_step": cold_ms / steps, "lb_last": cold["lb"],
                        "z_aug_per_lap": cold["stats"][1] / (steps * T)},
         "warm": {"lb_last": warm["lb"], "z_aug_per_lap": warm["stats"][1] / (steps * T),
+                 "same_bound_as_cold": bool(warm["lb"] == cold["lb"]),
                  "same_bound_as_cold_rel": abs(warm["lb"] - cold["lb"]) / abs(cold["lb"])},
         "ms_per_iteration_windows": {
             "first_50_after_warmup": warm["windows"][0][1] / warm["windows"][0][0],
@@ -591,10 +610,23 @@ def main():
             "cold_last_50": cold["windows"][-1][1] / cold["windows"][-1][0]},
         "kernels_ms_per_iteration": {k: v[0] / steps for k, v in warm["kt"].items()},
         "kernel_launches_per_iteration": {k: v[1] / steps for k, v in warm["kt"].items()},
-        "roofline": {"bound": "alu", "kernel": "lap_z", "achieved": ach_lz, "peak": FP64_PEAK_GOPS,
-                     "unit": FP64_UNIT, "frac": ach_lz / FP64_PEAK_GOPS, "traffic": traffic,
-                     "algorithmic_flops_per_launch": fl_lz, "avg_launch_ms": avg_lz,
-                     "peak_source": "derived: 1.25 TFLOP/s nominal FP64 / 2 per FMA = 2 lane-ops/clk/SM x 152 x 2.07 GHz"},
+        "roofline": {"bound": "alu", "kernel": "lap_z", "achieved": ach_lz, "peak": INT64_PEAK_GOPS,
+                     "unit": INT64_UNIT, "frac": ach_lz / INT64_PEAK_GOPS, "traffic": traffic,
+                     "algorithmic_ops_per_launch": fl_lz, "avg_launch_ms": avg_lz,
+                     "arithmetic": "exact 64-bit fixed point (canonical duals, dual_mode 1)",
+                     "peak_source": "derived: 128 int32 add lanes/clk/SM (measured 127.2) / 2 per 64-bit add "
+                                    "x 152 SMs x 2.07 GHz (add.s64 measured 63.8 lanes/clk/SM)",
+                     "limiter": "the ALU pipe's compares, selects and warp reductions of the sequential "
+                                "Dijkstra steps (ncu: ALU pipe about 70 % busy), not the additions"},
+        "pipelined": {"cold": whole_job_rate(world, steps, pcold_ms), "warm": whole_job_rate(world, steps, pwarm_ms),
+                      "unit": "iters/s", "same_bounds": bool(pcold["lb"] == cold["lb"] and pwarm["lb"] == warm["lb"]),
+                      "note": "z move and next Z-LAPs in one persistent launch (rlt2_params.pipeline = 1)"},
+        "fp64_canonical": {"value": whole_job_rate(world, steps, f64_ms), "unit": "iters/s",
+                           "ms_per_step": f64_ms / steps, "lb_last": f64["lb"],
+                           "lb_rel_diff_vs_fixed_point": abs(f64["lb"] - warm["lb"]) / abs(warm["lb"]),
+                           "lap_z_ms": avg_lz64,
+                           "roofline_lap_z": {"bound": "alu", "achieved": ach_lz64, "peak": FP64_PEAK_GOPS,
+                                              "unit": FP64_UNIT, "frac": ach_lz64 / FP64_PEAK_GOPS}},
         "roofline_move_z": {"bound": "alu", "achieved": mz_ops / (mz_ms * 1e-3) / 1e9, "peak": FP64_PEAK_GOPS,
                             "unit": FP64_UNIT, "frac": mz_ops / (mz_ms * 1e-3) / 1e9 / FP64_PEAK_GOPS,
                             "hbm_gbs": mz_bytes / (mz_ms * 1e-3) / 1e9,

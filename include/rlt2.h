@@ -106,7 +106,18 @@ typedef enum {
  *               y (i > j) passes kx pi_x(ip)/(n-1) to its mirror on the y level.
  *               S variant, one phase, no Type 4 rule; phi_z ignored; the
  *               phi_y + ky <= 1 limit does not apply (each y's slack is
- *               first split by the y move, then pushed into z). */
+ *               first split by the y move, then pushed into z).
+ *  pipeline   : 1 = run the z move of each ascent step and the Z-LAPs of
+ *               the next solve as one launch, a tile's LAP starting once the
+ *               move has finished every class of its facility pair (identical
+ *               results; the FP64 move and the integer LAPs share the SMs);
+ *               0 (default) = two launches.  On GB300 it pays for cold starts
+ *               around n = 20 (13 % there) and loses elsewhere: the LAPs need
+ *               the warp slots the move takes.  Not used with half_z or
+ *               warm = 2, nor by rlt2_bound_nodes and the no-allocation entry
+ *               point.  A pipelined wait that gives up (about a second; only a
+ *               fault can cause it) stops the ascent and rlt2_iterate returns
+ *               RLT2_ETIMEOUT. */
 typedef struct rlt2_params {
   double kz, ky, kx, phi_y;
   double phi_z[5];
@@ -124,6 +135,7 @@ typedef struct rlt2_params {
   double sa_cool;
   int sa_period;
   int half_z;
+  int pipeline;
 } rlt2_params;
 
 typedef struct rlt2_ctx rlt2_ctx;
@@ -131,7 +143,8 @@ typedef struct rlt2_ctx rlt2_ctx;
 /* Default parameters: kz = kx = 1, ky = 1/2, phi_y = 1/2, phi_z = 1/5 each,
  * canonical duals, cold start, min_gap = 0, ub unknown, feas_tol = 1e-9,
  * no stall stop (stall_window = 0, stall_tol = 0.0002), S variant, one phase,
- * phase2_tol = 1e-9, sa_t0 = 0.04, sa_cool = 0.99, sa_period = 100 (Section 5). */
+ * phase2_tol = 1e-9, sa_t0 = 0.04, sa_cool = 0.99, sa_period = 100 (Section 5),
+ * z move and Z-LAPs as two launches. */
 void rlt2_params_default(rlt2_params* p);
 
 /* Create a dual-ascent context for one QAP node (Eq. 1.1; a branch-and-bound

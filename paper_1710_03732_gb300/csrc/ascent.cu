@@ -110,7 +110,7 @@ __global__ void k_shift_psi(MoveYArgs a) {
 
 __global__ void __launch_bounds__(512) k_move_z(MoveZArgs a) {
   if (!a.sc->have_snap || a.sc->done) return;
-  move_z_block(a, blockIdx.x);
+  move_z_block(a, blockIdx.x, threadIdx.x, blockDim.x);
 }
 
 // Second phase of the two-phase Z solve; runs on every iteration (the first
@@ -266,6 +266,8 @@ struct rlt2_ctx {
   double cst_host = 0.0;
   rlt2_mlp* mlp = nullptr;
   double* u0buf = nullptr;
+  const PipePlan* pplan = nullptr;     // pipelined z move + Z-LAPs: shared plan (not owned)
+  unsigned long long* pipe = nullptr;  // its queue head, exit count and pair counters
 };
 
 static void ctx_free(rlt2_ctx* c) {
@@ -285,6 +287,7 @@ static void ctx_free(rlt2_ctx* c) {
   if (c->d_cst_qap && c->d_cst_qap != c->d_cst) cudaFree(c->d_cst_qap);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->u0buf) cudaFree(c->u0buf);
+  if (c->pipe) cudaFree(c->pipe);
   delete c;
 }
 
@@ -327,6 +330,8 @@ static IterView view_of(const rlt2_ctx* c) {
   v.Tz = c->Tz;
   v.bqap = c->bqap;
   v.cst_qap = c->d_cst_qap;
+  v.pplan = c->pplan;
+  v.pipe = c->pipe;
   v.sa_count = c->sa_count;
   if (c->sa_count > 0) {
     const long long cn = (long long)c->sa_count * c->n;
@@ -365,6 +370,7 @@ extern "C" void rlt2_params_default(rlt2_params* p) {
   p->sa_cool = 0.99;
   p->sa_period = 100;
   p->half_z = 0;
+  p->pipeline = 0;
 }
 
 bool rlt2::params_valid(const rlt2_params& p) {
@@ -382,6 +388,7 @@ bool rlt2::params_valid(const rlt2_params& p) {
   if (std::fabs(s - 1.0) > 1e-12) return false;
   if (p.dual_mode < 0 || p.dual_mode > 2) return false;
   if (p.warm < 0 || p.warm > 2) return false;
+  if (p.pipeline != 0 && p.pipeline != 1) return false;
   if (!std::isfinite(p.min_gap) || !std::isfinite(p.ub) || !std::isfinite(p.feas_tol)) return false;
   if (p.stall_window < 0 || p.stall_window >= kStallRing || !std::isfinite(p.stall_tol)) return false;
   if (p.variant != 0 && p.variant != 1) return false;
@@ -468,6 +475,12 @@ static rlt2_status ctx_alloc(rlt2_ctx* c, bool own_qap) {
     AL(c->bqap, n2);
     AL(c->d_cst_qap, 1);
   }
+  if (prm.pipeline && !prm.half_z) {
+    AL(c->pipe, 4 + n2);
+    cudaError_t e2 = cudaSuccess;
+    c->pplan = prepare_pipe(nr, &e2);
+    if (!c->pplan) return fail(e2, "pipelined move and Z-LAP plan");
+  }
 #undef AL
   if (!c->xcost) c->xcost = c->bprime;  // S variant: the X-LAP reads b' itself
   if (!c->bqap) c->bqap = c->bprime;
@@ -502,6 +515,7 @@ static rlt2_status ctx_alloc(rlt2_ctx* c, bool own_qap) {
       (e = cudaMemsetAsync(c->xi, 0, sizeof(double) * T * m, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(c->psi, 0, sizeof(double) * T * m, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(c->Theta, 0, sizeof(double) * T, s)) != cudaSuccess ||
+      (c->pipe && (e = cudaMemsetAsync(c->pipe, 0, sizeof(unsigned long long) * (4 + n2), s)) != cudaSuccess) ||
       (prm.half_z &&
        (e = cudaMemcpyAsync(c->zmap, up.data(), up.size() * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess)) {
     cudaStreamSynchronize(s);
@@ -838,13 +852,17 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
     }
   }
   if ((e = cudaGetLastError()) != cudaSuccess || (e = rec(0, 1)) != cudaSuccess) return e;
-  // 2) z move
+  // 2) z move (inside the Z-stage launch when pipelined)
   const MoveZArgs mz = make_move_z(v);
+  const bool pipelined = v.pplan && v.pipe && !p.half_z && p.warm != 2;
   if ((e = rec(1, 0)) != cudaSuccess) return e;
-  // one thread per (q, r) class of the block's (triple, p): round to whole warps
-  k_move_z<<<v.ntrip * n, move_z_threads(n), 0, s>>>(mz);
-  count(1, 1);
-  if ((e = cudaGetLastError()) != cudaSuccess || (e = rec(1, 1)) != cudaSuccess) return e;
+  if (!pipelined) {
+    // one thread per (q, r) class of the block's (triple, p): round to whole warps
+    k_move_z<<<v.ntrip * n, move_z_threads(n), 0, s>>>(mz);
+    count(1, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if ((e = rec(1, 1)) != cudaSuccess) return e;
   // 3) Z stage
   LapArgs z{};
   z.batch = v.zmap ? v.Tz : T;
@@ -868,7 +886,11 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   z.stats = v.sc->stats + 0;
   z.skip = done;
   if ((e = rec(2, 0)) != cudaSuccess) return e;
-  if ((e = launch_lap(z, s)) != cudaSuccess) return e;
+  if (pipelined) {
+    if ((e = launch_move_lap_z(mz, z, *v.pplan, v.pipe, v.sc, s)) != cudaSuccess) return e;
+  } else if ((e = launch_lap(z, s)) != cudaSuccess) {
+    return e;
+  }
   count(2, 1);
   if ((e = rec(2, 1)) != cudaSuccess) return e;
   // 3b) two-phase Z solve: move slack onto the zero-slack members, solve again
@@ -1041,6 +1063,11 @@ extern "C" rlt2_status rlt2_iterate(rlt2_ctx* c, int iters, double* lb_hist, int
     const int got = h.iter - it0;
     c->iter_host = h.iter;
     total += got;
+    if (h.reason == 4) {
+      set_error("rlt2_iterate: a pipelined Z-stage wait gave up (the step's results are not valid)");
+      if (done) *done = total;
+      return RLT2_ETIMEOUT;
+    }
     if (lb_hist) {
       // copy only the entries of this chunk (at most two pieces around the ring's end)
       int k = 0;

@@ -9,75 +9,7 @@
 
 namespace rlt2 {
 
-constexpr int kMaxWarpsPerBlock = 8;
-
-__host__ __device__ inline int tile_ld(int m) { return m | 1; }  // odd stride: conflict-free rows and columns
-
-// Shared memory per warp: 32/G tiles, u/v staging (64 doubles) and 32 ints.
-__host__ __device__ inline size_t warp_smem_bytes(int m, int G) {
-  return (size_t)(32 / G) * m * tile_ld(m) * sizeof(double) + 64 * sizeof(double) + 32 * sizeof(int);
-}
-
 int default_group(int m) { return m <= 8 ? 8 : (m <= 16 ? 16 : 32); }
-
-// Stages one group's tile (plus an optional addend) into shared memory, the
-// group's G lanes reading a contiguous m*m run (coalesced).  FX: the tile is
-// rounded down onto the group's fixed-point grid and the grid exponent L is
-// returned (0 for FP64).  All 32 lanes call it; src == nullptr for a group
-// without a LAP.
-template <int G, bool FX>
-__device__ __forceinline__ int stage_tile(typename std::conditional<FX, long long, double>::type* tile, int ld,
-                                          int m, int gl, const double* src, const double* add) {
-  const int mm = m * m;
-  if constexpr (!FX) {
-    if (src) {
-      for (int e = gl; e < mm; e += G) {
-        const int r = e / m, c = e - r * m;
-        double x = __ldcs(src + e);
-        if (add) x = __dadd_rn(x, __ldcs(add + e));
-        tile[r * ld + c] = x;
-      }
-    }
-    return 0;
-  } else {
-    unsigned eb = 0;
-    if (src) {
-      for (int e = gl; e < mm; e += G) {
-        const int r = e / m, c = e - r * m;
-        double x = __ldcs(src + e);
-        if (add) x = __dadd_rn(x, __ldcs(add + e));
-        tile[r * ld + c] = __double_as_longlong(x);  // bits; converted below once the grid is known
-        eb = max(eb, fx_expfield(x));
-      }
-    }
-    if constexpr (G == 32) {
-      eb = __reduce_max_sync(kFull, eb);
-    } else {
-#pragma unroll
-      for (int off = G / 2; off > 0; off >>= 1) eb = max(eb, __shfl_xor_sync(kFull, eb, off));
-    }
-    const int L = fx_grid(eb);
-    if (src) {
-      for (int e = gl; e < mm; e += G) {  // the entries this lane wrote
-        const int r = e / m, c = e - r * m;
-        tile[r * ld + c] = fx_floor(__longlong_as_double(tile[r * ld + c]), L, kFxEntryBits);
-      }
-    }
-    return L;
-  }
-}
-
-template <bool FX, typename T>
-__device__ __forceinline__ double out_value(T x, int L) {
-  if constexpr (FX) return fx_to_double(x, L);
-  else return x;
-}
-
-template <bool FX>
-__device__ __forceinline__ typename std::conditional<FX, long long, double>::type start_dual(double u0, int L) {
-  if constexpr (FX) return fx_floor(u0, L, kFxStartBits);
-  else return u0;
-}
 
 // Grid-stride over LAPs, 32/G LAPs per warp per step.  FX selects the exact
 // fixed-point arithmetic (canonical duals), else FP64.

@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(512) k_move_z_nodes(const MoveZArgs* nodes, co
   if ((int)blockIdx.x >= nblocks[blockIdx.y]) return;
   const MoveZArgs a = nodes[blockIdx.y];
   if (!a.sc->have_snap || a.sc->done) return;
-  move_z_block(a, blockIdx.x);
+  move_z_block(a, blockIdx.x, threadIdx.x, blockDim.x);
 }
 
 __global__ void k_shift_psi_nodes(const MoveYArgs* nodes) {

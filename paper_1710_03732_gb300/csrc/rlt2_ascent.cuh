@@ -191,7 +191,19 @@ __device__ __forceinline__ void move_z_half_block(const MoveZArgs& a, int blk) {
   }
 }
 
-__device__ __forceinline__ void move_z_block(const MoveZArgs& a, int blk) {
+// Loads of the duals and tile terms: through the read-only cache in the
+// stand-alone move; plain loads where the same launch later rewrites the duals
+// (the pipelined move + Z-LAP kernel, whose move reads of a tile's duals all
+// precede that tile's LAP).
+template <bool RO>
+__device__ __forceinline__ double ldv(const double* p) {
+  if constexpr (RO) return __ldg(p);
+  else return *p;
+}
+
+// The classes (q, r) = first, first + stride, ... of block blk = (triple, p).
+template <bool RO = true>
+__device__ __forceinline__ void move_z_block(const MoveZArgs& a, int blk, int first, int stride) {
   if (a.half) {
     move_z_half_block(a, blk);
     return;
@@ -204,7 +216,7 @@ __device__ __forceinline__ void move_z_block(const MoveZArgs& a, int blk) {
   const int npairs = n1 * m;
   const long long mm = (long long)m * m;
   const bool sa = a.fast && a.sc->sa_on;
-  for (int c = threadIdx.x; c < npairs; c += blockDim.x) {
+  for (int c = first; c < npairs; c += stride) {
     const int qq = c / m, rr = c - qq * m;
     const int q = qq + (qq >= p);
     const int lo = p < q ? p : q, hi = p < q ? q : p;
@@ -226,7 +238,7 @@ __device__ __forceinline__ void move_z_block(const MoveZArgs& a, int blk) {
         const int kr = f2 - (f2 > f0) - (f2 > f1), cc = l2 - (l2 > l0) - (l2 > l1);
         idx[b] = t * mm + kr * m + cc;
         Dv[b] = a.Dhat[idx[b]];
-        s[b] = dsub_(dsub_(Dv[b], __ldg(a.xi + t * m + kr)), __ldg(a.psi + t * m + cc));
+        s[b] = dsub_(dsub_(Dv[b], ldv<RO>(a.xi + t * m + kr)), ldv<RO>(a.psi + t * m + cc));
       }
       double S = s[0];
 #pragma unroll
@@ -243,15 +255,15 @@ __device__ __forceinline__ void move_z_block(const MoveZArgs& a, int blk) {
       const int kr = f2 - (f2 > f0) - (f2 > f1), cc = l2 - (l2 > l0) - (l2 > l1);
       idx[b] = t * mm + kr * m + cc;
       const double Dv = a.Dhat[idx[b]];
-      const double pz = dsub_(dsub_(Dv, __ldg(a.xi + t * m + kr)), __ldg(a.psi + t * m + cc));
+      const double pz = dsub_(dsub_(Dv, ldv<RO>(a.xi + t * m + kr)), ldv<RO>(a.psi + t * m + cc));
       // s = kz*pi_z + tile term in one rounding (kz = 1: an exact fma(1, x, y) is x + y)
-      s[b] = a.kz_one ? dadd_(pz, __ldg(a.tterm + t)) : __fma_rn(a.kz, pz, __ldg(a.tterm + t));
+      s[b] = a.kz_one ? dadd_(pz, ldv<RO>(a.tterm + t)) : __fma_rn(a.kz, pz, ldv<RO>(a.tterm + t));
       if (!a.fast) {
         base[b] = dsub_(Dv, s[b]);
       } else {
         // (1 - kz) pi_z in one rounding; fma(-1, x, x) is +0 exactly
         base[b] = a.kz_one ? 0.0 : __fma_rn(-a.kz, pz, pz);
-        if (sa) base[b] = dsub_(base[b], __ldg(a.saterm + f0 * n + l0));
+        if (sa) base[b] = dsub_(base[b], ldv<RO>(a.saterm + f0 * n + l0));
       }
     }
     if (a.uniform) {

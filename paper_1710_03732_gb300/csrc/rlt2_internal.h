@@ -8,6 +8,9 @@
 
 namespace rlt2 {
 
+struct MoveZArgs;
+struct DevScalars;
+
 // One launch solves `batch` LAPs of size m; LAP b has cost A[b*m*m..] (+ Badd[b*m*m..]).
 struct LapArgs {
   long long batch;
@@ -64,6 +67,33 @@ struct NodeLapArgs {
 };
 cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s);
 
+// The z move of one ascent step and the Z-stage LAPs that follow it as one
+// persistent launch (fused.cu): a few warps of every block run the move's
+// (triple, p) blocks while the others solve the Z-LAPs, tiles grouped by
+// facility pair in the order the move finishes the pairs.  A tile's LAP waits
+// until every move block whose facility triple holds the tile's two
+// facilities is done (its pair counter reaches (n-2) n), so the FP64 move and
+// the integer LAPs overlap on the SMs while each LAP sees exactly the costs and
+// start duals of the two-kernel sequence.
+struct PipePlan {
+  int n = 0;
+  const int* order = nullptr;  // device, T tiles in pair-completion order
+  long long nmove = 0;         // move blocks: triples * n
+  int grid = 0;                // blocks (resident on every SM), 8 warps each
+};
+// The plan for residual size n on the current device: kernel attributes,
+// occupancy and tile order, built once per (device, n) and kept for the life
+// of the process.  Call outside stream capture.
+const PipePlan* prepare_pipe(int n, cudaError_t* err);
+struct PipeArgs {
+  const int* order;
+  long long nmove;
+  unsigned long long* ctr;   // [0] move head, [1] warps done, [2] LAP head, [4 + a*n + b] blocks done for pair a < b
+  DevScalars* sc;            // stop flags (a wait that gives up sets done, reason 4)
+};
+cudaError_t launch_move_lap_z(const MoveZArgs& mz, const LapArgs& z, const PipePlan& plan, unsigned long long* ctr,
+                              DevScalars* sc, cudaStream_t s);
+
 // Lanes per LAP the launcher would pick for size m (8, 16 or 32).
 int default_group(int m);
 
@@ -103,6 +133,8 @@ struct IterView {
   int sa_count;
   const int* zmap;  // half-Z scheme: the tiles with first facility < second facility
   long long Tz;     // number of Z-LAPs solved (T, or T/2 with the half scheme)
+  const PipePlan* pplan;   // nullable: pipelined z move + Z-LAPs (see PipePlan)
+  unsigned long long* pipe;  // their queues and pair counters (4 + n*n)
   const double* bqap;     // nullable: QAP linear costs for upper bounds (default bprime)
   const double* cst_qap;  // nullable: QAP constant for upper bounds (default d_cst)
   int *xperm, *ubperm, *trips;

@@ -27,7 +27,7 @@ class rlt2_params(ctypes.Structure):
                 ("feas_tol", ctypes.c_double), ("stall_window", ctypes.c_int), ("stall_tol", ctypes.c_double),
                 ("variant", ctypes.c_int), ("two_phase", ctypes.c_int), ("phase2_tol", ctypes.c_double),
                 ("sa_t0", ctypes.c_double), ("sa_cool", ctypes.c_double), ("sa_period", ctypes.c_int),
-                ("half_z", ctypes.c_int)]
+                ("half_z", ctypes.c_int), ("pipeline", ctypes.c_int)]
 
 
 class rlt2_bnb_options(ctypes.Structure):
@@ -153,11 +153,11 @@ def _stream(stream) -> Optional[int]:
 
 def params(kz=1.0, ky=0.5, kx=1.0, phi_y=0.5, phi_z=(0.2,) * 5, dual_mode=1, warm=0, min_gap=0.0, ub=0.0,
            feas_tol=1e-9, stall_window=0, stall_tol=0.0002, variant=0, two_phase=0, phase2_tol=1e-9, sa_t0=0.04,
-           sa_cool=0.99, sa_period=100, half_z=0) -> rlt2_params:
+           sa_cool=0.99, sa_period=100, half_z=0, pipeline=0) -> rlt2_params:
     """Parameters (dual_mode 0 = raw FP64 Hungarian duals, 1 = canonical duals in exact
     fixed point, 2 = canonical duals in FP64; variant 0 = S, 1 = F; two_phase;
     annealing schedule of the Type 4 rule; half_z = the half-Z-LAP scheme, see
-    half_z_params)."""
+    half_z_params; pipeline = the z move and the next Z-LAPs in one launch)."""
     p = rlt2_params()
     lib().rlt2_params_default(ctypes.byref(p))
     p.kz, p.ky, p.kx, p.phi_y = kz, ky, kx, phi_y
@@ -168,6 +168,7 @@ def params(kz=1.0, ky=0.5, kx=1.0, phi_y=0.5, phi_z=(0.2,) * 5, dual_mode=1, war
     p.variant, p.two_phase, p.phase2_tol = int(variant), int(two_phase), phase2_tol
     p.sa_t0, p.sa_cool, p.sa_period = sa_t0, sa_cool, int(sa_period)
     p.half_z = int(half_z)
+    p.pipeline = int(pipeline)
     return p
 
 
