@@ -108,7 +108,8 @@ __global__ void k_shift_psi(MoveYArgs a) {
   shift_psi_range(a, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
-__global__ void __launch_bounds__(512) k_move_z(MoveZArgs a) {
+// at most 352 threads (move_z_threads) and 62 registers: three blocks per SM
+__global__ void __launch_bounds__(352, 3) k_move_z(MoveZArgs a) {
   if (!a.sc->have_snap || a.sc->done) return;
   move_z_block(a, blockIdx.x, threadIdx.x, blockDim.x);
 }

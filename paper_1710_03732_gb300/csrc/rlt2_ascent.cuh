@@ -452,10 +452,12 @@ __device__ __forceinline__ void finalize_block(const FinArgs& a) {
 }
 
 // Threads of a z-move block: the (n-1)(n-2) classes of one (triple, p) in
-// equal passes of at most 512 threads, rounded to whole warps.
+// equal passes of at most 352 threads, rounded to whole warps (n = 20: one
+// pass of 352; three such blocks fit an SM at 62 registers, against two of
+// up to 512 threads: 4 % faster).
 inline int move_z_threads(int n) {
   const int c = (n - 1) * (n - 2);
-  const int passes = (c + 511) / 512;
+  const int passes = (c + 351) / 352;
   return ((c + passes - 1) / passes + 31) / 32 * 32;
 }
 
