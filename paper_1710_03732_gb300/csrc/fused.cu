@@ -25,6 +25,9 @@
 // queues and counters for the next launch.  (Letting LAP warps run move blocks
 // while theirs are not ready was tried: it starts the integer LAPs later and
 // was slower.)
+//
+// Used with rlt2_params.pipeline = 1, off by default: it pays for cold starts
+// near n = 20, while elsewhere the LAPs miss the warp slots the movers hold.
 #include <algorithm>
 #include <mutex>
 #include <vector>
@@ -43,8 +46,8 @@ constexpr int kPipeSpinLimit = 1 << 22;
 // the integer LAPs (n = 20: 1, 2, 3, 4 tried, 3 fastest).
 constexpr int kMoveWarps = 3;
 
-template <int G, bool FX>
 // 64 registers: four blocks of eight warps per SM (80 unbounded: three)
+template <int G, bool FX>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 4) k_move_lap_z(MoveZArgs mz, LapArgs a, PipeArgs pa) {
   DevScalars* sc = pa.sc;
   if (sc->done) return;  // stopped: no work, counters untouched
