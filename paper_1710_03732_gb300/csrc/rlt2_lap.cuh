@@ -12,9 +12,10 @@
 //
 // GB300 runs FP64 at ~1/70 of its FP32 rate, and FP64 compares and min/max use
 // the same slow pipe, so every comparison below is done on 64-bit integer
-// keys that order exactly like the doubles (okey), and every argmin is a
-// two-step warp integer min reduction (redux.sync) plus a ballot.  The only
-// FP64 instructions left are the additions the method needs.
+// keys that order exactly like the values (okey for doubles), and every argmin
+// is a two-step warp integer min reduction (redux.sync) plus a ballot.  In the
+// FP64 form the only FP64 instructions left are the additions the method
+// needs; the fixed-point form has none outside the output conversions.
 //
 // Two arithmetic forms, chosen per launch:
 //   FP64      IEEE double, round to nearest, in the CPU oracle's operation order
@@ -34,8 +35,15 @@
 //             and dual feasible for the given tile too (rounding down only
 //             lowers costs).  GB300 issues integer additions ~40x faster than
 //             FP64 ones.
+//             The bounds, in grid steps: |c| < 2^48 and |u0| <= 2^49 give start
+//             column duals below 2^49.6; a search's sink label is the growth
+//             of the matching's cost minus u_i + v_sink, so the sink labels of
+//             all searches sum below 2^56 and every dual stays below 2^56.2;
+//             reduced costs are below 2^57.1 and labels below 2^57.6; the
+//             canonical pass's distances are u^c_r - (u_r - u_0) with
+//             |u^c| < 31 * 2^49 < 2^54, below 2^57.3, candidates below 2^58.3.
 //
-// Arithmetic order (the oracle's, by specification):
+// Order of the operations (the oracle's, by specification; exact in fixed point):
 //   start     u = u0 or 0;  v_c = min_r (c_rc - u_r), ties to the lowest row
 //   greedy    column c takes its argmin row if no lower column took that row
 //   search    for every free row i (increasing): Dijkstra on reduced costs
