@@ -33,7 +33,7 @@ __global__ void k_move_y_nodes(const MoveYArgs* nodes) {
   move_y_range(a, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
-__global__ void __launch_bounds__(512) k_move_z_nodes(const MoveZArgs* nodes, const int* nblocks) {
+__global__ void __launch_bounds__(352, 3) k_move_z_nodes(const MoveZArgs* nodes, const int* nblocks) {
   if ((int)blockIdx.x >= nblocks[blockIdx.y]) return;
   const MoveZArgs a = nodes[blockIdx.y];
   if (!a.sc->have_snap || a.sc->done) return;

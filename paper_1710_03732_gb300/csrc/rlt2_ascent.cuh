@@ -143,6 +143,29 @@ struct MoveZArgs {
   const DevScalars* sc;
 };
 
+// The class (q, r) -- as indices qq < n-1, rr < n-2 with p (and q) skipped --
+// of thread slot c of a (triple, p) block.  Two members of a class lie in rows
+// along r, two in rows along q and two in a different tile for every (q, r):
+// with lanes along r (slot c = qq (n-2) + rr) a warp's six loads touch 144
+// 32-byte sectors.  For n >= 22 the slots run in bands of eight q with r
+// outer, so a warp's lanes cover 8 q x 4 r and touch 96: the z array is then
+// far larger than L2 and the move keeps its rate (n = 28: 3.60 instead of
+// 5.58 ms).  Below that the plain order is as fast or faster (n = 20 equal,
+// the batched nodes of residual 14..18 9 % faster without the bands' integer
+// divisions).
+__device__ __forceinline__ void class_of(int c, int n1, int m, int& qq, int& rr) {
+  constexpr int kBand = 8;
+  if (n1 < 21) {
+    qq = c / m;
+    rr = c - qq * m;
+    return;
+  }
+  const int band = c / (kBand * m), cb = c - band * kBand * m;
+  const int hb = min(kBand, n1 - kBand * band);
+  qq = kBand * band + cb % hb;
+  rr = cb / hb;
+}
+
 // One thread per class; a block covers one facility triple and one location p
 // of its first facility (all (q, r)).  Consecutive threads take consecutive r,
 // so members (i,j,k|p,q,r) and (j,i,k|q,p,r) are read and written as contiguous
@@ -164,7 +187,8 @@ __device__ __forceinline__ void move_z_half_block(const MoveZArgs& a, int blk) {
   const int npairs = n1 * m;
   const long long mm = (long long)m * m;
   for (int c = threadIdx.x; c < npairs; c += blockDim.x) {
-    const int qq = c / m, rr = c - qq * m;
+    int qq, rr;
+    class_of(c, n1, m, qq, rr);
     const int q = qq + (qq >= p);
     const int lo = p < q ? p : q, hi = p < q ? q : p;
     int r = rr;
@@ -217,7 +241,8 @@ __device__ __forceinline__ void move_z_block(const MoveZArgs& a, int blk, int fi
   const long long mm = (long long)m * m;
   const bool sa = a.fast && a.sc->sa_on;
   for (int c = first; c < npairs; c += stride) {
-    const int qq = c / m, rr = c - qq * m;
+    int qq, rr;
+    class_of(c, n1, m, qq, rr);
     const int q = qq + (qq >= p);
     const int lo = p < q ? p : q, hi = p < q ? q : p;
     int r = rr;
@@ -310,7 +335,8 @@ __device__ __forceinline__ void phase2_block(const Phase2Args& a, int blk) {
   const int npairs = n1 * m;
   const long long mm = (long long)m * m;
   for (int c = threadIdx.x; c < npairs; c += blockDim.x) {
-    const int qq = c / m, rr = c - qq * m;
+    int qq, rr;
+    class_of(c, n1, m, qq, rr);
     const int q = qq + (qq >= p);
     const int lo = p < q ? p : q, hi = p < q ? q : p;
     int r = rr;
