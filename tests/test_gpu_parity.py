@@ -356,6 +356,28 @@ def test_import_state_resync(R):
     assert abs(lbs[0] - out.lb) <= 1e-9 * abs(out.lb)
 
 
+def test_raw_bit_exact_n22_banded_move(R):
+    """From n = 22 on the z move hands its classes to a warp's lanes in bands of
+    8 q x 4 r instead of along r; every class is still moved by one thread with
+    the oracle's arithmetic, so raw-duals bounds and the moved state stay
+    bit-identical to the oracle (two iterations: the second applies the first
+    ascent step to all 85 M z entries)."""
+    inst = I.random_instance(22, 17, with_b=True, asymmetric=True)
+    iters = 2
+    with R.Context(inst.F, inst.D, inst.B, prm=_prm(R, 0)) as ctx:
+        lbs, done = ctx.iterate(iters)
+        D, C = ctx.export_state()
+    assert done == iters
+    ost = O.setup(inst.F, inst.D, inst.B)
+    ref = []
+    for it in range(iters):
+        before = O.State(ost.n, ost.const, ost.bprime, ost.Chat.copy(), ost.Dhat.copy()) if it == iters - 1 else None
+        out = O.iterate(ost, _oprm(), 0, threads=O.max_threads() or 1)
+        ref.append(ost.const + out.lb)
+    assert np.array_equal(lbs, np.array(ref)), (lbs, ref)
+    assert np.array_equal(D, before.Dhat) and np.array_equal(C, before.Chat)
+
+
 # ------------------------------------------------------- full-size sampled ----
 def test_n20_full_size_sampled(R):
     """n = 20 dense uniform 0..99 (144,400 Z-LAPs of size 18 per iteration), in the
