@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 4) k_move_lap_z(MoveZA
       }
       // move block (triple, p) = q, its classes across the warp's lanes, then
       // the counters of the triple's three facility pairs
-      move_z_block<false>(mz, (int)q, lane, 32);
+      move_z_block<false, false>(mz, (int)q, lane, 32);  // one warp per block: plain class order
       __threadfence();  // this lane's D^ writes before the pair counters move
       __syncwarp();
       if (lane == 0) {

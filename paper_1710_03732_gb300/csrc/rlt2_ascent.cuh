@@ -153,9 +153,10 @@ struct MoveZArgs {
 // 5.58 ms).  Below that the plain order is as fast or faster (n = 20 equal,
 // the batched nodes of residual 14..18 9 % faster without the bands' integer
 // divisions).
+template <bool BAND = true>
 __device__ __forceinline__ void class_of(int c, int n1, int m, int& qq, int& rr) {
   constexpr int kBand = 8;
-  if (n1 < 21) {
+  if (!BAND || n1 < 21) {
     qq = c / m;
     rr = c - qq * m;
     return;
@@ -225,8 +226,9 @@ __device__ __forceinline__ double ldv(const double* p) {
   else return *p;
 }
 
-// The classes (q, r) = first, first + stride, ... of block blk = (triple, p).
-template <bool RO = true>
+// The classes (q, r) = first, first + stride, ... of block blk = (triple, p);
+// BAND: the banded class order for n >= 22 (see class_of).
+template <bool RO = true, bool BAND = true>
 __device__ __forceinline__ void move_z_block(const MoveZArgs& a, int blk, int first, int stride) {
   if (a.half) {
     move_z_half_block(a, blk);
@@ -242,7 +244,7 @@ __device__ __forceinline__ void move_z_block(const MoveZArgs& a, int blk, int fi
   const bool sa = a.fast && a.sc->sa_on;
   for (int c = first; c < npairs; c += stride) {
     int qq, rr;
-    class_of(c, n1, m, qq, rr);
+    class_of<BAND>(c, n1, m, qq, rr);
     const int q = qq + (qq >= p);
     const int lo = p < q ? p : q, hi = p < q ? q : p;
     int r = rr;
