@@ -177,6 +177,30 @@ def cpu_oracle_baseline(inst, iters: int, budget_s: float):
     return done, dt, threads, lbs
 
 
+def cpu_oracle_detail():
+    """The oracle on one core at n = 20 (first 2 iterations) and on all cores at
+    n = 30 (first iteration, setup excluded): the survey's CPU timings, bounded to
+    about 20 s."""
+    import oracle as O
+    threads = max(1, O.max_threads() or 1)
+    prm = O.params_array()
+    inst20 = I.config(CFG)
+    st = O.setup(inst20.F, inst20.D, inst20.B)
+    t0 = time.perf_counter()
+    for _ in range(2):
+        O.iterate(st, prm, 1, threads=1)
+    one = 2 / (time.perf_counter() - t0)
+    del st
+    inst30 = I.config(5)
+    st = O.setup(inst30.F, inst30.D, inst30.B)
+    t0 = time.perf_counter()
+    O.iterate(st, prm, 1, threads=threads)
+    s30 = time.perf_counter() - t0
+    del st
+    return {"n20_one_core_iters_per_s": one, "n30_all_cores_s_per_iter": s30, "cores": threads,
+            "cpu": cpu_model(), "note": "CPU oracle, first iterations, setup excluded"}
+
+
 def cpu_model() -> str:
     try:
         for line in open("/proc/cpuinfo"):
@@ -490,10 +514,12 @@ def main():
     rank, world, local = env_rank()
     inst = I.config(CFG)
     cpu = None
+    cpu_detail = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         it, dt, threads, _ = cpu_oracle_baseline(inst, 40, 15.0)
         cpu = {"value": it / dt, "unit": "iters/s", "cores": threads, "kind": "oracle",
                "sample": f"first {it} iterations of the same n=20 workload, all host cores ({cpu_model()})"}
+        cpu_detail = cpu_oracle_detail()
 
     import torch
     from paper_1710_03732_gb300 import build as B
@@ -642,6 +668,7 @@ def main():
                             "hbm_frac_of_measured": (mz_bytes / (mz_ms * 1e-3) / 1e9 / hbm) if hbm else None,
                             "avg_launch_ms": mz_ms},
         "cpu_baseline": cpu,
+        "cpu_oracle_detail": cpu_detail,
         "e2e": {"value": whole_job_rate(world, got, e2e_s * 1000.0), "unit": "iters/s",
                 "h2d_bytes_per_step": 3 * 20 * 20 * 8 / steps, "d2h_bytes_per_step": 8,
                 "note": "rlt2_create from host F,D,B + rlt2_iterate(K) with host bound history + destroy"},
