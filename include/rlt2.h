@@ -276,6 +276,12 @@ rlt2_status rlt2_kernel_times(rlt2_ctx* ctx, double* ms, long long* count, int n
 
 rlt2_status rlt2_destroy(rlt2_ctx* ctx);
 
+/* Bounds-checked build only (compiled with -DRLT2_BOUNDS_CHECK): the number of
+ * kernel indices found outside their array since the library was loaded (each
+ * is replaced by 0, never dereferenced); -1 in the normal build, -2 if a
+ * counter cannot be read. */
+long long rlt2_debug_bounds_violations(void);
+
 /* Batched LAPs, one warp per LAP (the tiled-LAP idea of Section 3.2: many
  * small LAPs solved in one launch).
  *  batch, m : number of LAPs and their size, 1 <= m <= 32

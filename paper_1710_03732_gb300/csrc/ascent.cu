@@ -228,9 +228,25 @@ __global__ void k_child_yx(int np, int f, int l, const double* __restrict__ Dp, 
   }
 }
 
+RLT2_DEFINE_OOB_QUERY(oob_ascent)
+
 }  // namespace rlt2
 
 using namespace rlt2;
+
+extern "C" long long rlt2_debug_bounds_violations(void) {
+#ifdef RLT2_BOUNDS_CHECK
+  unsigned long long total = 0;
+  for (auto query : {oob_lap, oob_ascent, oob_nodes, oob_fused}) {
+    const unsigned long long v = query();
+    if (v == ~0ull) return -2;
+    total += v;
+  }
+  return (long long)total;
+#else
+  return -1;
+#endif
+}
 
 // ------------------------------------------------------------------ context ---
 struct rlt2_ctx {

@@ -102,13 +102,13 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 4) k_move_lap_z(MoveZA
     if (q >= nlap) break;
     const long long tb = (long long)q * per + grp;
     const bool have = tb < a.batch;
-    const long long t = have ? (long long)pa.order[tb] : 0;
+    const long long t = have ? RLT2_IDX((long long)pa.order[tb], a.batch) : 0;
     if (have && moving && gl == 0) {
       // tile t = ((i n + p) (n-1) + j') (n-1) + q': wait for facility pair {i, j}
       const int i = (int)(t / ((long long)n * n1 * n1));
       const int jj = (int)((t / n1) % n1);
       const int j = jj + (jj >= i);
-      const volatile unsigned long long* cnt = pair_done + (i < j ? i * n + j : j * n + i);
+      const volatile unsigned long long* cnt = pair_done + RLT2_IDX(i < j ? i * n + j : j * n + i, n * n);
       int spins = 0;
       while (*cnt < target) {
         if (++spins > kPipeSpinLimit) {
@@ -191,6 +191,8 @@ static void build_pipe_order(int n, std::vector<int>& order) {
   order.resize((size_t)T);
   for (long long t = 0; t < T; ++t) order[(size_t)t] = key[(size_t)t].second;
 }
+
+RLT2_DEFINE_OOB_QUERY(oob_fused)
 
 static std::mutex g_pipe_mu;
 

@@ -199,8 +199,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap_nodes(NodeLapArg
         else hi = mid - 1;
       }
       k = lo;
-      li = t - s_prefix[k];
       it = a.items[k];
+      li = RLT2_IDX(t - s_prefix[k], it.count);
       if (*it.skip) have = false;
     }
     const int m = have ? it.m : 0;
@@ -302,6 +302,8 @@ cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s) {
   kern<<<grid, wpb * 32, smem, s>>>(a);
   return cudaGetLastError();
 }
+
+RLT2_DEFINE_OOB_QUERY(oob_lap)
 
 }  // namespace rlt2
 

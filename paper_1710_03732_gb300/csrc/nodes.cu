@@ -209,6 +209,8 @@ cudaError_t enqueue_wave_iteration(const Wave& w, const WaveDev& d, int dual_mod
 }
 
 }  // namespace
+
+RLT2_DEFINE_OOB_QUERY(oob_nodes)
 }  // namespace rlt2
 
 using namespace rlt2;

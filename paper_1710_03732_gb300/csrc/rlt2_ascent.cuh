@@ -69,12 +69,12 @@ __device__ __forceinline__ void move_y_range(const MoveYArgs& a, long long start
     }
   }
   for (long long t = start; t < a.T; t += stride) {
-    const int ip = (int)(t / (n1 * n1));
+    const int ip = RLT2_IDX((int)(t / (n1 * n1)), n * n);
     const int rem = (int)(t - (long long)ip * n1 * n1);
     const int jj = rem / n1, qq = rem - jj * n1;
     const int i = ip / n, p = ip - i * n;
     const int j = jj + (jj >= i), q = qq + (qq >= p);
-    const long long tp = ((long long)(j * n + q) * n1 + (i - (i > j))) * n1 + (p - (p > q));
+    const long long tp = RLT2_IDX(((long long)(j * n + q) * n1 + (i - (i > j))) * n1 + (p - (p > q)), a.T);
     const double py = a.piy[t];
     // half-Z scheme: the z pools of an upper tile take the y slack left after the y move
     const double pyz = a.half ? dadd_(dsub_(py, dmul_(a.phi_y, py)), dmul_(a.phi_y, a.piy[tp])) : py;
@@ -203,8 +203,9 @@ __device__ __forceinline__ void move_z_half_block(const MoveZArgs& a, int blk) {
       const int b = kUp[u];
       const int f0 = F3[kOrd[b][0]], f1 = F3[kOrd[b][1]], f2 = F3[kOrd[b][2]];
       const int l0 = L3[kOrd[b][0]], l1 = L3[kOrd[b][1]], l2 = L3[kOrd[b][2]];
-      const long long t = ((long long)(f0 * n + l0) * n1 + (f1 - (f1 > f0))) * n1 + (l1 - (l1 > l0));
-      const int kr = f2 - (f2 > f0) - (f2 > f1), cc = l2 - (l2 > l0) - (l2 > l1);
+      const long long t = RLT2_IDX(((long long)(f0 * n + l0) * n1 + (f1 - (f1 > f0))) * n1 + (l1 - (l1 > l0)),
+                                        (long long)n * n * n1 * n1);
+      const int kr = RLT2_IDX(f2 - (f2 > f0) - (f2 > f1), m), cc = RLT2_IDX(l2 - (l2 > l0) - (l2 > l1), m);
       idx[u] = t * mm + kr * m + cc;
       Dv[u] = a.Dhat[idx[u]];
       const double pz = dsub_(dsub_(Dv[u], __ldg(a.xi + t * m + kr)), __ldg(a.psi + t * m + cc));
@@ -261,8 +262,9 @@ __device__ __forceinline__ void move_z_block(const MoveZArgs& a, int blk, int fi
       for (int b = 0; b < 6; ++b) {
         const int f0 = F3[kOrd[b][0]], f1 = F3[kOrd[b][1]], f2 = F3[kOrd[b][2]];
         const int l0 = L3[kOrd[b][0]], l1 = L3[kOrd[b][1]], l2 = L3[kOrd[b][2]];
-        const long long t = ((long long)(f0 * n + l0) * n1 + (f1 - (f1 > f0))) * n1 + (l1 - (l1 > l0));
-        const int kr = f2 - (f2 > f0) - (f2 > f1), cc = l2 - (l2 > l0) - (l2 > l1);
+        const long long t = RLT2_IDX(((long long)(f0 * n + l0) * n1 + (f1 - (f1 > f0))) * n1 + (l1 - (l1 > l0)),
+                                        (long long)n * n * n1 * n1);
+        const int kr = RLT2_IDX(f2 - (f2 > f0) - (f2 > f1), m), cc = RLT2_IDX(l2 - (l2 > l0) - (l2 > l1), m);
         idx[b] = t * mm + kr * m + cc;
         Dv[b] = a.Dhat[idx[b]];
         s[b] = dsub_(dsub_(Dv[b], ldv<RO>(a.xi + t * m + kr)), ldv<RO>(a.psi + t * m + cc));
@@ -278,8 +280,9 @@ __device__ __forceinline__ void move_z_block(const MoveZArgs& a, int blk, int fi
     for (int b = 0; b < 6; ++b) {
       const int f0 = F3[kOrd[b][0]], f1 = F3[kOrd[b][1]], f2 = F3[kOrd[b][2]];
       const int l0 = L3[kOrd[b][0]], l1 = L3[kOrd[b][1]], l2 = L3[kOrd[b][2]];
-      const long long t = ((long long)(f0 * n + l0) * n1 + (f1 - (f1 > f0))) * n1 + (l1 - (l1 > l0));
-      const int kr = f2 - (f2 > f0) - (f2 > f1), cc = l2 - (l2 > l0) - (l2 > l1);
+      const long long t = RLT2_IDX(((long long)(f0 * n + l0) * n1 + (f1 - (f1 > f0))) * n1 + (l1 - (l1 > l0)),
+                                        (long long)n * n * n1 * n1);
+      const int kr = RLT2_IDX(f2 - (f2 > f0) - (f2 > f1), m), cc = RLT2_IDX(l2 - (l2 > l0) - (l2 > l1), m);
       idx[b] = t * mm + kr * m + cc;
       const double Dv = a.Dhat[idx[b]];
       const double pz = dsub_(dsub_(Dv, ldv<RO>(a.xi + t * m + kr)), ldv<RO>(a.psi + t * m + cc));
@@ -354,8 +357,9 @@ __device__ __forceinline__ void phase2_block(const Phase2Args& a, int blk) {
     for (int b = 0; b < 6; ++b) {
       const int f0 = F3[kOrd[b][0]], f1 = F3[kOrd[b][1]], f2 = F3[kOrd[b][2]];
       const int l0 = L3[kOrd[b][0]], l1 = L3[kOrd[b][1]], l2 = L3[kOrd[b][2]];
-      const long long t = ((long long)(f0 * n + l0) * n1 + (f1 - (f1 > f0))) * n1 + (l1 - (l1 > l0));
-      const int kr = f2 - (f2 > f0) - (f2 > f1), cc = l2 - (l2 > l0) - (l2 > l1);
+      const long long t = RLT2_IDX(((long long)(f0 * n + l0) * n1 + (f1 - (f1 > f0))) * n1 + (l1 - (l1 > l0)),
+                                        (long long)n * n * n1 * n1);
+      const int kr = RLT2_IDX(f2 - (f2 > f0) - (f2 > f1), m), cc = RLT2_IDX(l2 - (l2 > l0) - (l2 > l1), m);
       idx[b] = t * mm + kr * m + cc;
       Dv[b] = a.Dhat[idx[b]];
       const double xv = __ldg(a.xi + t * m + kr), pv = __ldg(a.psi + t * m + cc);
@@ -412,7 +416,7 @@ __device__ __forceinline__ void finalize_block(const FinArgs& a) {
   double part = 0.0;
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e - i * n;
-    const int si = a.xperm[i], sj = a.xperm[j];
+    const int si = RLT2_IDX(a.xperm[i], n), sj = RLT2_IDX(a.xperm[j], n);
     part += (i == j) ? a.bqap[i * n + si] : a.Fr[i * n + j] * a.Dr[si * n + sj];
   }
   red[tid] = part;
@@ -427,7 +431,7 @@ __device__ __forceinline__ void finalize_block(const FinArgs& a) {
     const double tol = a.feas_tol * fmax(1.0, fabs(lb));
     for (int e = tid; e < n * n1; e += blockDim.x) {
       const int i = e / n1, jj = e - i * n1, j = jj + (jj >= i);
-      const int si = a.xperm[i], sj = a.xperm[j];
+      const int si = RLT2_IDX(a.xperm[i], n), sj = RLT2_IDX(a.xperm[j], n);
       const long long t = ((long long)(i * n + si) * n1 + jj) * n1 + (sj - (sj > si));
       if (fabs(a.piy[t]) > tol) bad = 1;
     }
@@ -440,7 +444,7 @@ __device__ __forceinline__ void finalize_block(const FinArgs& a) {
       int k = kk;
       k += (k >= lo);
       k += (k >= hi);
-      const int si = a.xperm[i], sj = a.xperm[j], sk = a.xperm[k];
+      const int si = RLT2_IDX(a.xperm[i], n), sj = RLT2_IDX(a.xperm[j], n), sk = RLT2_IDX(a.xperm[k], n);
       const long long t = ((long long)(i * n + si) * n1 + jj) * n1 + (sj - (sj > si));
       const int rc = sk - (sk > si) - (sk > sj);
       const double pz = dsub_(dsub_(a.Dhat[t * m * m + (long long)kk * m + rc], a.xi[t * m + kk]), a.psi[t * m + rc]);

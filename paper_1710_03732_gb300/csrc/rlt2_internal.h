@@ -8,6 +8,40 @@
 
 namespace rlt2 {
 
+// Bounds-checked build (-DRLT2_BOUNDS_CHECK, `build.build(checked=True)`): the
+// indices the kernels compute pass through RLT2_IDX(i, n), which counts an
+// index outside [0, n) in a per-file device counter and uses 0 instead, so a
+// bad index is reported (rlt2_debug_bounds_violations) and never dereferenced.
+// In the normal build RLT2_IDX(i, n) is i.
+#ifdef RLT2_BOUNDS_CHECK
+static __device__ unsigned long long g_oob_count;
+template <typename I, typename N>
+__device__ __forceinline__ I checked_index(I i, N n) {
+  if ((unsigned long long)(long long)i < (unsigned long long)(long long)n) return i;
+  atomicAdd(&g_oob_count, 1ull);
+  return I(0);
+}
+#define RLT2_IDX(i, n) ::rlt2::checked_index((i), (n))
+#else
+#define RLT2_IDX(i, n) (i)
+#endif
+// Host: this file's counter (defined once per translation unit by
+// RLT2_DEFINE_OOB_QUERY; 0 in the normal build, ~0 if it cannot be read).
+#ifdef RLT2_BOUNDS_CHECK
+#define RLT2_DEFINE_OOB_QUERY(name)                                                  \
+  unsigned long long name() {                                                        \
+    unsigned long long v = 0;                                                        \
+    return cudaMemcpyFromSymbol(&v, g_oob_count, sizeof v) == cudaSuccess ? v : ~0ull; \
+  }
+#else
+#define RLT2_DEFINE_OOB_QUERY(name) \
+  unsigned long long name() { return 0; }
+#endif
+unsigned long long oob_lap();
+unsigned long long oob_ascent();
+unsigned long long oob_nodes();
+unsigned long long oob_fused();
+
 struct MoveZArgs;
 struct DevScalars;
 

@@ -62,6 +62,8 @@
 
 #include <cuda_runtime.h>
 
+#include "rlt2_internal.h"
+
 namespace rlt2 {
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -263,7 +265,7 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
       const int r = r0 < 0 ? 0 : r0;
       const T ur = __shfl_sync(kFull, u, gb + r);
       if (relaxing && !scanned) {
-        const T nd = A::add(dm, A::sub(A::sub(cs[r * ld + gl], ur), v));
+        const T nd = A::add(dm, A::sub(A::sub(cs[RLT2_IDX(r, m) * ld + gl], ur), v));
         if (A::kExact ? nd < d : A::key(nd) < dk) {
           d = nd;
           if constexpr (!A::kExact) dk = A::key(nd);
@@ -289,12 +291,12 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
     }
     const int mc = (cv && r2c >= 0) ? r2c : 0;
     const T vm = __shfl_sync(kFull, v, gb + mc);
-    if (act && cv && r2c >= 0) u = A::sub(cs[gl * ld + r2c], vm);
+    if (act && cv && r2c >= 0) u = A::sub(cs[gl * ld + RLT2_IDX(r2c, m)], vm);
   }
 
   // optimum: pairwise tree over P = next power of two >= m rows (empty rows add
   // nothing), lane i adding lane i + h for h = P/2, ..., 1
-  const T xr = cv ? cs[gl * ld + r2c] : T(0);
+  const T xr = cv ? cs[gl * ld + RLT2_IDX(r2c, m)] : T(0);
   int P = 1;
   while (P < m) P <<= 1;
   const int PM = (G == 32) ? P : (int)__reduce_max_sync(kFull, (unsigned)P);
@@ -341,8 +343,8 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
     const T vs0 = __shfl_sync(kFull, v, gb + (s0 < 0 ? 0 : s0));
     T dist = T(0);
     if (cv && gl != 0) {
-      if constexpr (PRE) dist = cs[gl * ld + s0];
-      else dist = A::sub(A::sub(cs[gl * ld + s0], u), vs0);
+      if constexpr (PRE) dist = cs[gl * ld + RLT2_IDX(s0, m)];
+      else dist = A::sub(A::sub(cs[gl * ld + RLT2_IDX(s0, m)], u), vs0);
     }
     bool done = !cv || gl == 0;
     unsigned long long dk = A::key(dist);  // cached key of dist (rounded form only)
@@ -356,8 +358,8 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
       if constexpr (!PRE) vs = __shfl_sync(kFull, v, gb + (s < 0 ? 0 : s));
       if (stepping && !done) {
         T w;
-        if constexpr (PRE) w = cs[gl * ld + s];
-        else w = A::sub(A::sub(cs[gl * ld + s], u), vs);
+        if constexpr (PRE) w = cs[gl * ld + RLT2_IDX(s, m)];
+        else w = A::sub(A::sub(cs[gl * ld + RLT2_IDX(s, m)], u), vs);
         const T nd = A::add(dr, w);
         if (A::kExact ? nd < dist : A::key(nd) < dk) {
           dist = nd;

@@ -55,7 +55,8 @@ EXPORTS = ["rlt2_params_default", "rlt2_create", "rlt2_iterate", "rlt2_iterate_a
            "rlt2_mlp_set_weights", "rlt2_mlp_add_samples", "rlt2_mlp_samples", "rlt2_mlp_clear_samples",
            "rlt2_mlp_grad", "rlt2_mlp_fit", "rlt2_mlp_set_gate", "rlt2_mlp_predict", "rlt2_set_mlp",
            "rlt2_export_xstate", "rlt2_import_xstate", "rlt2_set_sa", "rlt2_create_child", "rlt2_bnb_options_default",
-           "rlt2_bnb_solve", "rlt2_mlp_check_wait_timeout", "rlt2_strerror", "rlt2_last_error"]
+           "rlt2_bnb_solve", "rlt2_mlp_check_wait_timeout", "rlt2_debug_bounds_violations", "rlt2_strerror",
+           "rlt2_last_error"]
 
 
 def lib():
@@ -114,8 +115,11 @@ def lib():
     L.rlt2_strerror.restype = ctypes.c_char_p
     L.rlt2_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("rlt2_params_default", "rlt2_bnb_options_default", "rlt2_strerror", "rlt2_last_error"):
+        if name not in ("rlt2_params_default", "rlt2_bnb_options_default", "rlt2_strerror", "rlt2_last_error",
+                        "rlt2_debug_bounds_violations"):
             getattr(L, name).restype = ctypes.c_int
+    L.rlt2_debug_bounds_violations.argtypes = []
+    L.rlt2_debug_bounds_violations.restype = ctypes.c_longlong
     _lib = L
     return L
 
@@ -313,6 +317,11 @@ def rlt2_bnb_solve(F, D, B=None, prm: Optional[rlt2_params] = None, opts: Option
                                 perm.ctypes.data_as(_ip), ctypes.byref(rlb), st, _stream(stream)), "rlt2_bnb_solve")
     keys = ["bounded", "branched", "enumerated", "iterations", "max_depth", "proven", "warm", "cold"]
     return best.value, perm, rlb.value, dict(zip(keys, list(st)))
+
+
+def rlt2_debug_bounds_violations() -> int:
+    """Indices the bounds-checked library caught out of range (-1: normal build)."""
+    return int(lib().rlt2_debug_bounds_violations())
 
 
 def rlt2_destroy(ctx: int):
