@@ -57,3 +57,23 @@ def test_single_process_is_identity():
     import bench
     assert bench.rank_max(12.5, None, "cpu") == 12.5
     assert bench.whole_job_rate(1, 300, 600.0) == pytest.approx(500.0)
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` (the CPU oracle, no GPU) prints one JSON line
+    with the contract's keys; a 3 s budget keeps it to a few oracle iterations."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RLT2_REF_BUDGET_S="3")
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "3"], capture_output=True, text=True, timeout=600, env=env, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
