@@ -86,6 +86,9 @@ def lib():
                                     ctypes.c_int])
         L.or_stage_z_upper.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _lp, _lp]
         L.or_redistribute_half.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.or_redistribute_half_form.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.or_redistribute_z_form.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp,
+                                             _dp, ctypes.c_int]
         L.or_iterate_half.argtypes = ([ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
                                        _dp, _dp, _dp, _dp, _dp, _dp, _ip, _dp, _dp, _lp])
         L.or_child_state.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, ctypes.c_double, _dp,
@@ -439,6 +442,24 @@ def redistribute_z_v(n, prm, Dhat, xi, psi, piy, pix, variant=0, sa=None, thread
     lib().or_redistribute_z_v(n, _d(_f64(prm)), variant, _d(None if sa is None else _f64(sa)), _d(out),
                               _d(_f64(xi)), _d(_f64(psi)), _d(_f64(piy)), _d(_f64(pix)), threads)
     return out
+
+
+def redistribute_z_form(n, prm, Dhat, xi, psi, piy, pix, form, variant=0, sa=None, threads=1):
+    """The z move with the branch chosen by form: 0 as the iteration picks it
+    (regrouped where phi are equal), 1 the general branch (Eq. 2.20 term by term)."""
+    out = _f64(Dhat).copy()
+    lib().or_redistribute_z_form(n, _d(_f64(prm)), variant, _d(None if sa is None else _f64(sa)), int(form), _d(out),
+                                 _d(_f64(xi)), _d(_f64(psi)), _d(_f64(piy)), _d(_f64(pix)), threads)
+    return out
+
+
+def redistribute_half_form(n, prm, Dhat, Chat, xi, psi, piy, pix, form):
+    """The half-Z scheme's move (z and y) with form 0 (regrouped member update)
+    or 1 (the plain sum); returns (D^', C^')."""
+    D, C = _f64(Dhat).copy(), _f64(Chat).copy()
+    lib().or_redistribute_half_form(n, _d(_f64(prm)), int(form), _d(D), _d(C), _d(_f64(xi)), _d(_f64(psi)),
+                                    _d(_f64(piy)), _d(_f64(pix)))
+    return D, C
 
 
 def phase2_z(n, Dhat, xi, psi, tol=1e-9, threads=1):

@@ -7,8 +7,10 @@
  * restatement of the method in FP64.  It is used by the test-suite, by the
  * package smoke check and by the benchmark's CPU-baseline leg; nothing on the
  * product path links, loads or calls it.  It shares no code with the CUDA
- * library.  Build flags: -O2 -ffp-contract=off (no fused multiply-add, so
- * every + and * below is one IEEE round-to-nearest operation).
+ * library.  Build flags: -O2 -ffp-contract=off: the compiler contracts
+ * nothing, so every + and * below is one IEEE round-to-nearest operation and
+ * a fused multiply-add happens only where the code calls C99 fma() (the z
+ * move's regrouped forms, which the paper's formulas leave the order of).
  *
  * Notation follows the paper (Section 2.3):
  *   n facilities/locations, b (n x n), C_ijpq = f_ij d_pq (RLT1, Eq. 2.1),
@@ -508,9 +510,13 @@ static inline long long zidx(int n, int i, int j, int k, int p, int q, int r) {
  * D^'(a) = fma(-kz, pi_z(a), pi_z(a)) [- sa(ip)] + inflow, i.e. (1-kz) pi_z
  * + Omega of Eq. 3.5 (the y and x parts of the pool leave the y and x costs).
  * sa (nullable, n*n): the Type 4 amount per (first facility, first location)
- * (Section 2.3, rule 4), added to every pool and, in F, taken from the z cost. */
-void or_redistribute_z_v(int n, const double* prm, int variant, const double* sa, double* Dhat, const double* xi,
-                         const double* psi, const double* piy, const double* pix, int nthreads) {
+ * (Section 2.3, rule 4), added to every pool and, in F, taken from the z cost.
+ * form 0 picks the regrouped branches where they apply (equal phi; equal phi
+ * with kz = 1 in S); form 1 always takes the general branch, which adds the
+ * five partner terms one at a time exactly as Eq. 2.20 lists them and is the
+ * plain definition the regrouped branches are tested against. */
+void or_redistribute_z_form(int n, const double* prm, int variant, const double* sa, int form, double* Dhat,
+                            const double* xi, const double* psi, const double* piy, const double* pix, int nthreads) {
   double kz = prm[0], cy = prm[1] / (double)(n - 2), cx = prm[2] / ((double)(n - 1) * (double)(n - 2));
   const double* phi = prm + 4;
   /* members of a class as position orders of the triple (i,j,k)/(p,q,r):
@@ -530,7 +536,7 @@ void or_redistribute_z_v(int n, const double* prm, int variant, const double* sa
     for (int b = 0; b < 6; b++) gives[a][b] = 0.0;
     for (int l = 0; l < 5; l++) gives[a][pmap[a][l]] = phi[l];
   }
-  int uniform = phi[0] == phi[1] && phi[0] == phi[2] && phi[0] == phi[3] && phi[0] == phi[4];
+  int uniform = form == 0 && phi[0] == phi[1] && phi[0] == phi[2] && phi[0] == phi[3] && phi[0] == phi[4];
   int folded = variant == 0 && uniform && kz == 1.0;
   double c1 = -(1.0 + phi[0]);
   int ntrip = 0;
@@ -616,6 +622,11 @@ void or_redistribute_z_v(int n, const double* prm, int variant, const double* sa
       }
   }
   free(trip);
+}
+
+void or_redistribute_z_v(int n, const double* prm, int variant, const double* sa, double* Dhat, const double* xi,
+                         const double* psi, const double* piy, const double* pix, int nthreads) {
+  or_redistribute_z_form(n, prm, variant, sa, 0, Dhat, xi, psi, piy, pix, nthreads);
 }
 
 void or_redistribute_z(int n, const double* prm, double* Dhat, const double* xi, const double* psi, const double* piy,
@@ -895,8 +906,11 @@ void or_stage_z_upper(int n, int dual_mode, const double* Dhat, const double* u0
   if (nrelax) *nrelax = relax_tot;
 }
 
-void or_redistribute_half(int n, const double* prm, double* Dhat, double* Chat, const double* xi, const double* psi,
-                          const double* piy, const double* pix) {
+/* form 0: the regrouped member update (D + S/2) - (3/2) s; form 1: the plain
+ * definition (D - s) + s_b/2 + s_c/2, the two other upper members' pools added
+ * one at a time in member order (the reference the regrouping is tested against). */
+void or_redistribute_half_form(int n, const double* prm, int form, double* Dhat, double* Chat, const double* xi,
+                               const double* psi, const double* piy, const double* pix) {
   double kz = prm[0], cy = prm[1] / (double)(n - 2), cx = prm[2] / ((double)(n - 1) * (double)(n - 2));
   double phi_y = prm[3], cxy = prm[2] / (double)(n - 1);
   for (int i = 0; i < n; i++)
@@ -923,6 +937,15 @@ void or_redistribute_half(int n, const double* prm, double* Dhat, double* Chat, 
                 idx[u] = zidx(n, a, b, c, x, y, w);
                 D[u] = Dhat[idx[u]];
               }
+              if (form == 1) {
+                for (int u = 0; u < 3; u++) {
+                  double acc = D[u] - s[u];
+                  for (int w = 0; w < 3; w++)
+                    if (w != u) acc = acc + 0.5 * s[w];
+                  Dhat[idx[u]] = acc;
+                }
+                continue;
+              }
               double S = (s[0] + s[1]) + s[2];
               /* D - s + (S - s)/2, regrouped as (D + S/2) - (3/2) s */
               for (int u = 0; u < 3; u++) Dhat[idx[u]] = fma(-1.5, s[u], fma(0.5, S, D[u]));
@@ -948,6 +971,11 @@ void or_redistribute_half(int n, const double* prm, double* Dhat, double* Chat, 
     }
   memcpy(Chat, out, sizeof(double) * T);
   free(out);
+}
+
+void or_redistribute_half(int n, const double* prm, double* Dhat, double* Chat, const double* xi, const double* psi,
+                          const double* piy, const double* pix) {
+  or_redistribute_half_form(n, prm, 0, Dhat, Chat, xi, psi, piy, pix);
 }
 
 /* One iteration of the half-Z scheme (solve, then the ascent step in place).

@@ -1,7 +1,8 @@
 """Builds the CUDA library ``librlt2.so`` in-tree for sm_103a (GB300).
 
-Two translation units are compiled in parallel with nvcc and linked with the
-static CUDA runtime; the result lands next to this file.  No CMake, no torch
+The CUDA sources listed in SOURCES are compiled in parallel with nvcc (one
+object each) and linked with the static CUDA runtime; the result lands next to
+this file.  No CMake, no torch
 extension machinery: the library exposes only the C ABI of include/rlt2.h.
 """
 from __future__ import annotations

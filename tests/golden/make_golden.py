@@ -23,7 +23,8 @@ def write(name, inst, iters, dual_mode):
     with open(path, "w") as f:
         f.write(f"# workload: {inst.name}: {inst.recipe}\n")
         f.write(f"# preset: {PRESET}; dual_mode={dual_mode}; S1 iterations={iters}\n")
-        f.write("# source: CPU oracle (oracle/rlt2_oracle.c), FP64, no FMA contraction\n")
+        f.write("# source: CPU oracle (oracle/rlt2_oracle.c), FP64, compiled without FMA contraction "
+                "(fused multiply-adds only where the oracle calls fma)\n")
         for v in lbs:
             f.write(repr(float(v)) + "\n")
     print("wrote", path)
