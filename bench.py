@@ -158,8 +158,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_baseline(inst, iters: int, budget_s: float):
-    """The CPU oracle as it stands, all host cores (OpenMP over LAPs and z classes)."""
+def oracle_step(O, st, prm, out, warm: bool, threads: int):
+    """One oracle iteration; with warm, every LAP starts from the previous
+    iteration's row duals (Z, Y and X), the start the GPU's `value` uses."""
+    w = warm and out is not None
+    return O.iterate(st, prm, 1, threads=threads, u0z=out.xi.copy() if w else None,
+                     u0y=out.gamma.copy() if w else None, u0x=out.alpha.copy() if w else None)
+
+
+def cpu_oracle_baseline(inst, iters: int, budget_s: float, warm: bool = True):
+    """The CPU oracle as it stands, all host cores (OpenMP over LAPs and z
+    classes), warm (previous duals, like `value`) or cold (like `plain_cold`)."""
     import oracle as O
     threads = max(1, O.max_threads() or 1)
     st = O.setup(inst.F, inst.D, inst.B)
@@ -167,8 +176,9 @@ def cpu_oracle_baseline(inst, iters: int, budget_s: float):
     t0 = time.perf_counter()
     done = 0
     lbs = []
+    out = None
     while done < iters:
-        out = O.iterate(st, prm, 1, threads=threads)
+        out = oracle_step(O, st, prm, out, warm, threads)
         lbs.append(st.const + out.lb)
         done += 1
         if time.perf_counter() - t0 > budget_s:
@@ -186,9 +196,10 @@ def cpu_oracle_detail():
     prm = O.params_array()
     inst20 = I.config(CFG)
     st = O.setup(inst20.F, inst20.D, inst20.B)
+    out = oracle_step(O, st, prm, None, True, threads)  # the first (cold) solve, untimed
     t0 = time.perf_counter()
     for _ in range(2):
-        O.iterate(st, prm, 1, threads=1)
+        out = oracle_step(O, st, prm, out, True, 1)
     one = 2 / (time.perf_counter() - t0)
     del st
     inst30 = I.config(5)
@@ -198,7 +209,9 @@ def cpu_oracle_detail():
     s30 = time.perf_counter() - t0
     del st
     return {"n20_one_core_iters_per_s": one, "n30_all_cores_s_per_iter": s30, "cores": threads,
-            "cpu": cpu_model(), "note": "CPU oracle, first iterations, setup excluded"}
+            "cpu": cpu_model(),
+            "note": "CPU oracle, setup excluded: n = 20 iterations 2-3 warm-started from the previous duals "
+                    "on one core; n = 30 the first (cold) iteration on all cores"}
 
 
 def cpu_model() -> str:
@@ -223,12 +236,13 @@ def run_reference(args):
     threads = max(1, O.max_threads() or 1)
     st = O.setup(inst.F, inst.D, inst.B)
     prm = O.params_array()
+    out = None  # warm starts from the previous iteration's duals, as the GPU arm's `value`
     for _ in range(args.warmup):
-        O.iterate(st, prm, 1, threads=threads)
+        out = oracle_step(O, st, prm, out, True, threads)
     t0 = time.perf_counter()
     steps = 0
     while steps < args.steps:
-        O.iterate(st, prm, 1, threads=threads)
+        out = oracle_step(O, st, prm, out, True, threads)
         steps += 1
         if time.perf_counter() - t0 > budget:
             break
@@ -240,8 +254,9 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": 20, "iterations": steps, "l2": "inputs larger than L2"},
         "cpu_baseline": {"value": value, "unit": "iters/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{steps} consecutive oracle iterations after {args.warmup} warm-up "
-                                   f"(capped at {budget:.0f} s); CPU: {cpu_model()}"},
+                         "sample": f"{steps} consecutive oracle iterations after {args.warmup} warm-up, every "
+                                   f"LAP warm-started from the previous iteration's duals as in the GPU arm's "
+                                   f"value (capped at {budget:.0f} s); CPU: {cpu_model()}"},
         "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -514,11 +529,16 @@ def main():
     rank, world, local = env_rank()
     inst = I.config(CFG)
     cpu = None
+    cpu_cold = None
     cpu_detail = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        it, dt, threads, _ = cpu_oracle_baseline(inst, 40, 15.0)
+        it, dt, threads, _ = cpu_oracle_baseline(inst, 40, 15.0, warm=True)
         cpu = {"value": it / dt, "unit": "iters/s", "cores": threads, "kind": "oracle",
-               "sample": f"first {it} iterations of the same n=20 workload, all host cores ({cpu_model()})"}
+               "sample": f"first {it} iterations of the same n=20 workload, every LAP warm-started from the "
+                         f"previous iteration's duals (the start of `value`), all host cores ({cpu_model()})"}
+        itc, dtc, _, _ = cpu_oracle_baseline(inst, 20, 8.0, warm=False)
+        cpu_cold = {"value": itc / dtc, "unit": "iters/s", "cores": threads, "kind": "oracle",
+                    "sample": f"first {itc} iterations, cold LAPs (the start of `plain_cold`), all host cores"}
         cpu_detail = cpu_oracle_detail()
 
     import torch
@@ -528,6 +548,12 @@ def main():
         B.build()
     R.lib()
     torch.cuda.set_device(local)
+    # roofline denominators measured on this device in this run (instruction
+    # throughputs of the pipes the two hot kernels are bound by)
+    rates = R.rlt2_probe_rates()
+    int64_peak = rates["iadd64"]
+    # the z move's FP64 mix per entry: 2 + 5/6 add/sub, 2 fused multiply-adds
+    fp64_move_peak = (4 + 5.0 / 6.0) / ((2 + 5.0 / 6.0) / rates["dadd"] + 2.0 / rates["dfma"])
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -634,7 +660,7 @@ def main():
                        "z_stage_only_warm": T / (avg_lz * 1e-3)},
         "plain_cold": {"value": whole_job_rate(world, steps, cold_ms), "unit": "iters/s",
                        "ms_per_step": cold_ms / steps, "lb_last": cold["lb"],
-                       "z_aug_per_lap": cold["stats"][1] / (steps * T)},
+                       "z_aug_per_lap": cold["stats"][1] / (steps * T), "cpu_oracle_cold": cpu_cold},
         "warm": {"lb_last": warm["lb"], "z_aug_per_lap": warm["stats"][1] / (steps * T),
                  "same_bound_as_cold": bool(warm["lb"] == cold["lb"]),
                  "same_bound_as_cold_rel": abs(warm["lb"] - cold["lb"]) / abs(cold["lb"])},
@@ -645,12 +671,13 @@ def main():
             "cold_last_50": cold["windows"][-1][1] / cold["windows"][-1][0]},
         "kernels_ms_per_iteration": {k: v[0] / steps for k, v in warm["kt"].items()},
         "kernel_launches_per_iteration": {k: v[1] / steps for k, v in warm["kt"].items()},
-        "roofline": {"bound": "alu", "kernel": "lap_z", "achieved": ach_lz, "peak": INT64_PEAK_GOPS,
-                     "unit": INT64_UNIT, "frac": ach_lz / INT64_PEAK_GOPS, "traffic": traffic,
+        "roofline": {"bound": "alu", "kernel": "lap_z", "achieved": ach_lz, "peak": int64_peak,
+                     "unit": INT64_UNIT, "frac": ach_lz / int64_peak, "traffic": traffic,
                      "algorithmic_ops_per_launch": fl_lz, "avg_launch_ms": avg_lz,
                      "arithmetic": "exact 64-bit fixed point (canonical duals, dual_mode 1)",
-                     "peak_source": "derived: 128 int32 add lanes/clk/SM (measured 127.2) / 2 per 64-bit add "
-                                    "x 152 SMs x 2.07 GHz (add.s64 measured 63.8 lanes/clk/SM)",
+                     "peak_source": "measured in this run: add.s64 lane throughput of the device "
+                                    "(rlt2_probe_rates, CUDA events); nominal 64 lanes/clk/SM x 152 x 2.07 GHz = "
+                                    f"{INT64_PEAK_GOPS:.0f}",
                      "limiter": "the ALU pipe's compares, selects and warp reductions of the sequential "
                                 "Dijkstra steps (ncu: ALU pipe about 70 % busy), not the additions"},
         "pipelined": {"cold": whole_job_rate(world, steps, pcold_ms), "warm": whole_job_rate(world, steps, pwarm_ms),
@@ -660,10 +687,14 @@ def main():
                            "ms_per_step": f64_ms / steps, "lb_last": f64["lb"],
                            "lb_rel_diff_vs_fixed_point": abs(f64["lb"] - warm["lb"]) / abs(warm["lb"]),
                            "lap_z_ms": avg_lz64,
-                           "roofline_lap_z": {"bound": "alu", "achieved": ach_lz64, "peak": FP64_PEAK_GOPS,
-                                              "unit": FP64_UNIT, "frac": ach_lz64 / FP64_PEAK_GOPS}},
-        "roofline_move_z": {"bound": "alu", "achieved": mz_ops / (mz_ms * 1e-3) / 1e9, "peak": FP64_PEAK_GOPS,
-                            "unit": FP64_UNIT, "frac": mz_ops / (mz_ms * 1e-3) / 1e9 / FP64_PEAK_GOPS,
+                           "roofline_lap_z": {"bound": "alu", "achieved": ach_lz64, "peak": rates["dadd"],
+                                              "unit": FP64_UNIT, "frac": ach_lz64 / rates["dadd"],
+                                              "peak_source": "measured add.rn.f64 lane throughput"}},
+        "roofline_move_z": {"bound": "alu", "achieved": mz_ops / (mz_ms * 1e-3) / 1e9, "peak": fp64_move_peak,
+                            "unit": FP64_UNIT, "frac": mz_ops / (mz_ms * 1e-3) / 1e9 / fp64_move_peak,
+                            "peak_source": "measured in this run: the kernel's FP64 mix (2 5/6 add/sub, 2 fma per "
+                                           "entry) at the probed add.rn.f64 and fma.rn.f64 lane rates",
+                            "frac_of_nominal": mz_ops / (mz_ms * 1e-3) / 1e9 / FP64_PEAK_GOPS,
                             "hbm_gbs": mz_bytes / (mz_ms * 1e-3) / 1e9,
                             "hbm_frac_of_measured": (mz_bytes / (mz_ms * 1e-3) / 1e9 / hbm) if hbm else None,
                             "avg_launch_ms": mz_ms},
@@ -672,6 +703,7 @@ def main():
         "e2e": {"value": whole_job_rate(world, got, e2e_s * 1000.0), "unit": "iters/s",
                 "h2d_bytes_per_step": 3 * 20 * 20 * 8 / steps, "d2h_bytes_per_step": 8,
                 "note": "rlt2_create from host F,D,B + rlt2_iterate(K) with host bound history + destroy"},
+        "measured_rates_gops": {k: v for k, v in rates.items() if k != "sm_clock_ghz"},
         "gpu_launches": int(launches),
         "gpu_kernel_ms_total": total_kernel_ms,
         "clocks": clk,

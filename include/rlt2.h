@@ -276,6 +276,30 @@ rlt2_status rlt2_kernel_times(rlt2_ctx* ctx, double* ms, long long* count, int n
 
 rlt2_status rlt2_destroy(rlt2_ctx* ctx);
 
+/* Measured instruction throughputs of the current device, the denominators of
+ * the hot kernels' rooflines (no counterpart in the paper: the z move is bound
+ * by the FP64 pipe, the fixed-point LAPs by the integer ALU pipe, and GB300's
+ * data sheet gives no per-instruction rates).  Each probe keeps 8 independent
+ * accumulators per thread over a grid of resident warps; the best of three
+ * timed launches (CUDA events on `stream`) after a warm-up is reported.
+ *  rates        : host, 5 doubles, in G lane-operations per second:
+ *                 [0] add.rn.f64, [1] fma.rn.f64, [2] add.s64, [3] add.s32,
+ *                 [4] the integer-pipe binary64 addition (rlt2_fp64_add_emulated)
+ *  sm_clock_ghz : host (nullable): the device's rated SM clock
+ * Allocates and frees two small buffers; synchronises `stream`.  Errors:
+ * EINVAL (rates NULL), ECUDA. */
+rlt2_status rlt2_probe_rates(double* rates, double* sm_clock_ghz, void* stream);
+
+/* The integer-pipe binary64 addition the z move uses for part of its exactly
+ * rounded additions (no counterpart in the paper), exposed so that tests can
+ * hold it to the FP64 pipe bit for bit: sum[i] = a[i] + b[i] and diff[i] =
+ * a[i] - b[i], round to nearest, ties to even, computed with integer
+ * operations only.  count >= 0; a, b, sum, diff: device arrays of count
+ * doubles (finite inputs; an overflowing result is infinity).  Asynchronous
+ * on `stream`.  Errors: EINVAL, ECUDA. */
+rlt2_status rlt2_fp64_add_emulated(long long count, const double* a, const double* b, double* sum, double* diff,
+                                   void* stream);
+
 /* Bounds-checked build only (compiled with -DRLT2_BOUNDS_CHECK): the number of
  * kernel indices found outside their array since the library was loaded (each
  * is replaced by 0, never dereferenced); -1 in the normal build, -2 if a
@@ -332,6 +356,20 @@ typedef struct rlt2_mlp rlt2_mlp;
  * not run out, EINVAL for a network whose width is not 256, ECUDA otherwise. */
 rlt2_status rlt2_mlp_check_wait_timeout(rlt2_mlp* mlp);
 
+/* Failure-detection check of the pipelined launch (rlt2_params.pipeline = 1;
+ * no counterpart in the paper): enqueues one iteration whose Z-LAP warps wait
+ * for facility-pair counts that the z move never reaches, with the polls
+ * capped at 2^12 (a few milliseconds) instead of 2^22.  The first wait to give
+ * up stops the ascent (the same path as a real timeout), the launch skips its
+ * remaining LAPs and ends, and the device stays usable.  Needs a context
+ * created with pipeline = 1 and warm 0 or 1 that has run at least one
+ * iteration (so that a move is pending), else RLT2_EINVAL.  Returns
+ * RLT2_ETIMEOUT when the timeout was detected and reported (the expected
+ * outcome), RLT2_OK if no wait gave up.  Afterwards the context is stopped
+ * (rlt2_iterate makes no progress and returns RLT2_ETIMEOUT) and holds the
+ * state of an incomplete step: destroy it.  Synchronises the context's stream. */
+rlt2_status rlt2_pipeline_check_wait_timeout(rlt2_ctx* ctx);
+
 rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D, const double* B, int n_nodes,
                              const int* partials, const rlt2_params* p, rlt2_mlp* mlp, int iters, size_t mem_budget,
                              double* lb_out, double* lb_hist, int* iters_out, long long* stats_out, void* stream);
@@ -387,8 +425,15 @@ rlt2_status rlt2_bnb_solve(int n, const double* F, const double* D, const double
  *             larger n returns RLT2_EINVAL with a message naming the limit
  *  F, D     : device, n*n flow and distance matrices (finite; not checked)
  *  B        : device, n*n fixed costs, or NULL for B = 0
- *  p        : host parameters (NULL = defaults), as for rlt2_create
- *  iters    : 1..65536 iterations of the same S1 dual ascent as rlt2_iterate
+ *  p        : host parameters (NULL = defaults), as for rlt2_create; the
+ *             S and F variants (variant 0, 1), the two-phase Z solve and warm
+ *             starts 0 and 1 run exactly as on a context.  Rejected with
+ *             RLT2_EINVAL: the half-Z scheme (half_z) and the learned start
+ *             (warm = 2), which need a context.  Not available on this path
+ *             (a context's set-up calls): the Type 4 draws (rlt2_set_sa); the
+ *             pipelined launch is ignored (pipeline = 1 runs unpipelined, with
+ *             the same results)
+ *  iters    : 1..65536 iterations of the dual ascent, as rlt2_iterate runs them
  *  lb_hist  : device, iters doubles: bound of each iteration (NaN after a stop)
  *  stream   : cudaStream_t the work is enqueued on; the call returns without
  *             waiting for it
@@ -399,7 +444,9 @@ rlt2_status rlt2_bnb_solve(int n, const double* F, const double* D, const double
  * current; make that first call before any stream capture.  Every call reuses
  * the same array and starts by clearing what must start at zero, so calls that
  * overlap on the GPU (different streams, or different host threads on one
- * device) race and give undefined results: serialise them. */
+ * device) race and give undefined results: serialise them.  The array's
+ * address is cached per device, so the library must not be used across a
+ * cudaDeviceReset. */
 rlt2_status rlt2_iterate_noalloc(int n, const double* F, const double* D, const double* B, const rlt2_params* p,
                                  int iters, double* lb_hist, void* stream);
 

@@ -904,7 +904,7 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   z.skip = done;
   if ((e = rec(2, 0)) != cudaSuccess) return e;
   if (pipelined) {
-    if ((e = launch_move_lap_z(mz, z, *v.pplan, v.pipe, v.sc, s)) != cudaSuccess) return e;
+    if ((e = launch_move_lap_z(mz, z, *v.pplan, v.pipe, v.sc, s, v.pipe_check != 0)) != cudaSuccess) return e;
   } else if ((e = launch_lap(z, s)) != cudaSuccess) {
     return e;
   }
@@ -977,6 +977,32 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
 
 static cudaError_t enqueue_iteration_ctx(rlt2_ctx* c, cudaStream_t s, int ev_base, int* launched = nullptr) {
   return enqueue_iteration(view_of(c), s, ev_base < 0 ? nullptr : c->ev.data() + ev_base, launched);
+}
+
+// Failure detection of the pipelined launch without a fault: one iteration
+// whose Z-LAP warps wait for pair counts the move never reaches, with the
+// polls capped low; the first wait to give up stops the context (reason 4)
+// and the remaining LAPs of the launch are skipped.
+extern "C" rlt2_status rlt2_pipeline_check_wait_timeout(rlt2_ctx* c) {
+  if (!c || c->prm.pipeline != 1 || !c->pplan || !c->pipe || c->prm.warm == 2 || c->enqueued < 1) {
+    set_error("rlt2_pipeline_check_wait_timeout: needs a context with pipeline = 1 (warm 0 or 1) that has "
+              "run at least one iteration");
+    return RLT2_EINVAL;
+  }
+  IterView v = view_of(c);
+  v.pipe_check = 1;
+  cudaError_t e = enqueue_iteration(v, c->stream, nullptr, nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "rlt2_pipeline_check_wait_timeout");
+  c->enqueued += 1;
+  DevScalars h;
+  CK(cudaMemcpyAsync(&h, c->sc, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->iter_host = h.iter;
+  if (h.reason == 4) {
+    set_error("rlt2_pipeline_check_wait_timeout: the pipelined wait gave up as intended; the context is stopped");
+    return RLT2_ETIMEOUT;
+  }
+  return RLT2_OK;
 }
 
 static rlt2_status build_graph(rlt2_ctx* c) {

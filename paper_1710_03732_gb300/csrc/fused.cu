@@ -41,6 +41,8 @@ namespace rlt2 {
 // Polls of a pair counter before a LAP warp gives up (about a second with the
 // back-off below); a move block takes microseconds, so only a fault gets here.
 constexpr int kPipeSpinLimit = 1 << 22;
+// The same limit in the failure-detection check, whose waits can never end.
+constexpr int kPipeCheckSpinLimit = 1 << 12;
 // Warps per block that run the move first (of kMaxWarpsPerBlock): 12 per SM
 // keep the FP64 pipe busy through the move's load latencies, the other 20 run
 // the integer LAPs (n = 20: 1, 2, 3, 4 tried, 3 fastest).
@@ -109,29 +111,34 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 4) k_move_lap_z(MoveZA
       const int jj = (int)((t / n1) % n1);
       const int j = jj + (jj >= i);
       const volatile unsigned long long* cnt = pair_done + RLT2_IDX(i < j ? i * n + j : j * n + i, n * n);
+      const volatile int* stop = &sc->done;
       int spins = 0;
-      while (*cnt < target) {
-        if (++spins > kPipeSpinLimit) {
+      while (*cnt < target + pa.extra) {
+        if (++spins > pa.spin_limit) {
           sc->reason = 4;  // reported as RLT2_ETIMEOUT; the step's results are not used
           sc->done = 1;
           break;
         }
+        if (*stop) break;  // another warp gave up: this launch's LAPs are void
         __nanosleep(200);
       }
     }
     __syncwarp();
     __threadfence();
-    const int L = stage_tile<G, FX, true>(tile, ld, m, gl, have ? a.A + t * mm : nullptr, nullptr);
+    // after a wait gave up (sc->done is set only then during this launch) the
+    // remaining LAPs are skipped, so the launch drains its queue and ends
+    const bool live = have && !*(const volatile int*)&sc->done;
+    const int L = stage_tile<G, FX, true>(tile, ld, m, gl, live ? a.A + t * mm : nullptr, nullptr);
     T u0 = T(0);
-    if (warm && have && gl < m) u0 = start_dual<FX>(a.u0[t * m + gl], L);
+    if (warm && live && gl < m) u0 = start_dual<FX>(a.u0[t * m + gl], L);
     __syncwarp();
     const WarpLapResult<T> R =
-        group_lap<G, true, A>(tile, ld, have ? m : 0, lane, warm, u0, a.dual_mode, scr, uv + grp * G);
-    if (have && gl < m) {
+        group_lap<G, true, A>(tile, ld, live ? m : 0, lane, warm, u0, a.dual_mode, scr, uv + grp * G);
+    if (live && gl < m) {
       a.u[t * m + gl] = out_value<FX>(R.u, L);
       a.v[t * m + gl] = out_value<FX>(R.v, L);
     }
-    if (have && gl == 0) {
+    if (live && gl == 0) {
       a.value[t] = out_value<FX>(R.value, L);
       aug_acc += R.naug;
       relax_acc += R.nrelax;
@@ -245,7 +252,7 @@ const PipePlan* prepare_pipe(int n, cudaError_t* err) {
 }
 
 cudaError_t launch_move_lap_z(const MoveZArgs& mz, const LapArgs& a, const PipePlan& plan, unsigned long long* ctr,
-                              DevScalars* sc, cudaStream_t s) {
+                              DevScalars* sc, cudaStream_t s, bool check) {
   if (a.m < 1 || a.m > 32 || mz.n != a.m + 2 || plan.n != mz.n || mz.half || a.map || a.Badd || a.pi || a.r2c ||
       !a.u || !a.v || !ctr || !sc)
     return cudaErrorInvalidValue;
@@ -255,6 +262,8 @@ cudaError_t launch_move_lap_z(const MoveZArgs& mz, const LapArgs& a, const PipeP
   pa.nmove = plan.nmove;
   pa.ctr = ctr;
   pa.sc = sc;
+  pa.spin_limit = check ? kPipeCheckSpinLimit : kPipeSpinLimit;
+  pa.extra = check ? 1ull : 0ull;
   const PipeKernel kern = pipe_kernel(G, a.dual_mode == 1);
   kern<<<plan.grid, kMaxWarpsPerBlock * 32, warp_smem_bytes(a.m, G) * kMaxWarpsPerBlock, s>>>(mz, a, pa);
   return cudaGetLastError();

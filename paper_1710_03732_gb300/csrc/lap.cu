@@ -11,6 +11,79 @@ namespace rlt2 {
 
 int default_group(int m) { return m <= 8 ? 8 : (m <= 16 ? 16 : 32); }
 
+// The fixed-point Z stage with prefetching (a.prefetch): each group's next tile
+// and start duals are copied into shared memory by cp.async while the current
+// LAP is solved, so the tile's HBM latency is off the warp's path.  The copy
+// of tile k+1 is issued as soon as the column reduction of tile k has
+// converted its raw entries (group_lap's hook); the grid exponent of a tile is
+// the largest exponent field of its raw entries, as in stage_tile.  Results
+// are those of the staged form bit for bit.
+template <int G>
+__device__ __forceinline__ void k_lap_prefetching(const LapArgs& a, unsigned char* base, int lane, bool warm,
+                                                  long long first, long long stride) {
+  using A = ArithFx;
+  using T = long long;
+  constexpr int per = 32 / G;
+  const int grp = lane / G, gl = lane & (G - 1);
+  const int m = a.m, ld = tile_ld(m), mm = m * m;
+  T* tile = reinterpret_cast<T*>(base) + (size_t)grp * m * ld;
+  T* uv = reinterpret_cast<T*>(base) + (size_t)per * m * ld;  // [0..31] u, [32..63] v
+  int* scr = reinterpret_cast<int*>(uv + 64) + grp * G;
+  double* raw = reinterpret_cast<double*>(base + warp_smem_bytes(m, G)) + (size_t)grp * raw_group_doubles(m);
+  unsigned long long aug_acc = 0, relax_acc = 0;
+  // copies of group grp's tile of the step starting at LAP t0 (nothing past the batch)
+  auto issue = [&](long long t0) {
+    const long long tb = t0 + grp;
+    if (tb < a.batch) {
+      const long long t = a.map ? (long long)a.map[tb] : tb;
+      const double* src = a.A + t * mm;
+      for (int e = gl; e < mm; e += G) cp_async8(raw + e, src + e);
+      if (warm && gl < m) cp_async8(raw + mm + gl, a.u0 + t * m + gl);
+    }
+    cp_async_commit();
+  };
+  issue(first);
+  for (long long t0 = first; t0 < a.batch; t0 += stride) {
+    const long long tb = t0 + grp;
+    const bool have = tb < a.batch;
+    const long long t = (have && a.map) ? (long long)a.map[tb] : tb;
+    cp_async_wait_all();
+    __syncwarp();
+    unsigned eb = 0;
+    if (have)
+      for (int e = gl; e < mm; e += G) eb = max(eb, fx_expfield_hi(raw + e));
+    if constexpr (G == 32) {
+      eb = __reduce_max_sync(kFull, eb);
+    } else {
+#pragma unroll
+      for (int off = G / 2; off > 0; off >>= 1) eb = max(eb, __shfl_xor_sync(kFull, eb, off));
+    }
+    const int L = fx_grid(eb);
+    T u0 = T(0);
+    if (warm && have && gl < m) u0 = start_dual<true>(raw[mm + gl], L);
+    const long long next = t0 + stride;
+    const WarpLapResult<T> R = group_lap<G, true, A>(tile, ld, have ? m : 0, lane, warm, u0, a.dual_mode, scr,
+                                                     uv + grp * G, raw, L, [&]() { issue(next); });
+    if (have && gl < m) {
+      if (a.u) a.u[t * m + gl] = out_value<true>(R.u, L);
+      if (a.v) a.v[t * m + gl] = out_value<true>(R.v, L);
+      if (a.r2c) a.r2c[t * m + gl] = R.r2c;
+    }
+    if (have && gl == 0) {
+      a.value[t] = out_value<true>(R.value, L);
+      if (a.naug) a.naug[t] = R.naug;
+      aug_acc += R.naug;
+      relax_acc += R.nrelax;
+    }
+    __syncwarp();
+  }
+  cp_async_wait_all();  // nothing may be in flight when the warp leaves
+  if (a.stats && gl == 0 && (aug_acc | relax_acc)) {
+    atomicAdd(a.stats + 0, aug_acc);
+    atomicAdd(a.stats + 1, relax_acc);
+  }
+}
+
 // Grid-stride over LAPs, 32/G LAPs per warp per step.  FX selects the exact
 // fixed-point arithmetic (canonical duals), else FP64.
 template <int G, bool PRE, bool FX>
@@ -19,6 +92,16 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap(LapArgs a) {
   using A = typename std::conditional<FX, ArithFx, ArithF64>::type;
   using T = typename A::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if constexpr (FX && PRE) {
+    if (a.prefetch) {
+      const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+      const bool warm = a.u0 != nullptr && (a.warm_gate == nullptr || *a.warm_gate != 0);
+      const long long nwarps = (long long)gridDim.x * wpb;
+      k_lap_prefetching<G>(a, smem_raw + (size_t)wib * warp_smem_bytes_async(a.m, G), lane, warm,
+                           ((long long)blockIdx.x * wpb + wib) * (32 / G), nwarps * (32 / G));
+      return;
+    }
+  }
   constexpr int per = 32 / G;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
@@ -80,12 +163,33 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap(LapArgs a) {
   }
 }
 
-// blocks per SM for (m, G, warps per block), 0 = not configured
-// Launch configuration (occupancy per size, shared-memory attributes), set once
-// per (size, group, warps) under g_cfg_mu: contexts may be created and used
-// from different host threads.
+// Launch configuration (SM count, occupancy per size, shared-memory
+// attributes), kept per device and set once per (device, size, group, warps)
+// under g_cfg_mu: contexts may be created and used from different host threads
+// and on different devices.  Like every per-device cache of the library it is
+// not valid across a cudaDeviceReset.
 static std::mutex g_cfg_mu;
-static int g_occ[33][3][2];
+constexpr int kMaxCfgDevices = 64;
+struct LapDevCfg {
+  int sms = 0;                 // multiprocessors of the device
+  int occ[33][3][2] = {};      // blocks per SM for (m, G, warps per block), 0 = not configured
+  int occ_nodes[33][3][2] = {};
+  bool attr[3] = {};           // dynamic shared-memory attribute set (k_lap, per G)
+  bool attr_nodes[3] = {};     // the same for k_lap_nodes
+};
+static LapDevCfg g_devcfg[kMaxCfgDevices];
+
+// The current device's entry, its SM count read on first use (g_cfg_mu held).
+static cudaError_t current_cfg(LapDevCfg** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxCfgDevices) return cudaErrorInvalidDevice;
+  LapDevCfg& c = g_devcfg[dev];
+  if (!c.sms && (e = cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  *out = &c;
+  return cudaSuccess;
+}
 
 static int gidx(int G) { return G == 8 ? 0 : (G == 16 ? 1 : 2); }
 
@@ -102,21 +206,24 @@ static LapKernel lap_kernel(int G, bool pre, bool fx) {
 }
 
 // Occupancy of the slowest of the four forms, so that one grid size serves all.
-static cudaError_t prepare_one(int G, int m, int wpb) {
-  int& slot = g_occ[m][gidx(G)][wpb == 4 ? 0 : 1];
+static cudaError_t prepare_one(LapDevCfg& cfg, int G, int m, int wpb) {
+  int& slot = cfg.occ[m][gidx(G)][wpb == 4 ? 0 : 1];
   if (slot > 0) return cudaSuccess;
-  static bool attr_set[3] = {false, false, false};
+  bool* attr_set = cfg.attr;
   cudaError_t e;
-  const int cap = (int)(warp_smem_bytes(32, 32) * kMaxWarpsPerBlock);
+  const int cap = (int)(warp_smem_bytes_async(32, 32) * kMaxWarpsPerBlock);
   int occ = 1 << 20;
   for (int k = 0; k < 4; ++k) {
-    const LapKernel kern = lap_kernel(G, (k & 1) != 0, (k & 2) != 0);
+    const bool pre = (k & 1) != 0, fx = (k & 2) != 0;
+    const LapKernel kern = lap_kernel(G, pre, fx);
     if (!attr_set[gidx(G)]) {
       if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess)
         return e;
     }
     int o = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, wpb * 32, warp_smem_bytes(m, G) * wpb);
+    // the prefetching form (fixed point, no reduced-cost output) needs more shared memory
+    const size_t per_warp = (pre && fx) ? warp_smem_bytes_async(m, G) : warp_smem_bytes(m, G);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, wpb * 32, per_warp * wpb);
     if (e != cudaSuccess) return e;
     occ = o < occ ? o : occ;
   }
@@ -125,36 +232,41 @@ static cudaError_t prepare_one(int G, int m, int wpb) {
   return cudaSuccess;
 }
 
-static int g_sms = 0;
-
-cudaError_t prepare_lap(int m, int group, int warps_per_block) {
+// Configures (once per device) the launch of an m-column LAP; *cap (nullable)
+// receives the resident block count of that launch on the current device.
+static cudaError_t prepare_cap(int m, int group, int warps_per_block, long long* cap) {
   if (m < 1 || m > 32) return cudaErrorInvalidValue;
   const int G = group ? group : default_group(m);
   const int wpb = warps_per_block ? warps_per_block : kMaxWarpsPerBlock;
   if (G < m || (G != 8 && G != 16 && G != 32) || (wpb != 4 && wpb != 8)) return cudaErrorInvalidValue;
   std::lock_guard<std::mutex> lock(g_cfg_mu);
-  cudaError_t e;
-  if (!g_sms) {
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  }
-  return prepare_one(G, m, wpb);
+  LapDevCfg* cfg = nullptr;
+  cudaError_t e = current_cfg(&cfg);
+  if (e != cudaSuccess) return e;
+  if ((e = prepare_one(*cfg, G, m, wpb)) != cudaSuccess) return e;
+  if (cap) *cap = (long long)cfg->sms * cfg->occ[m][gidx(G)][wpb == 4 ? 0 : 1];
+  return cudaSuccess;
+}
+
+cudaError_t prepare_lap(int m, int group, int warps_per_block) {
+  return prepare_cap(m, group, warps_per_block, nullptr);
 }
 
 cudaError_t launch_lap(const LapArgs& a, cudaStream_t s) {
   if (a.batch <= 0) return cudaSuccess;
   const int G = a.group ? a.group : default_group(a.m);
   const int wpb = a.warps_per_block ? a.warps_per_block : kMaxWarpsPerBlock;
-  cudaError_t e = prepare_lap(a.m, G, wpb);
+  long long cap = 0;
+  cudaError_t e = prepare_cap(a.m, G, wpb, &cap);
   if (e != cudaSuccess) return e;
-  const size_t smem = warp_smem_bytes(a.m, G) * wpb;
+  LapArgs b = a;
+  b.prefetch = (a.dual_mode == 1 && a.pi == nullptr && a.Badd == nullptr) ? 1 : 0;
+  const size_t smem = (b.prefetch ? warp_smem_bytes_async(a.m, G) : warp_smem_bytes(a.m, G)) * wpb;
   const long long per_block = (long long)wpb * (32 / G);
   const long long need = (a.batch + per_block - 1) / per_block;
-  const long long cap = (long long)g_sms * g_occ[a.m][gidx(G)][wpb == 4 ? 0 : 1];
   const int grid = (int)(need < cap ? need : cap);
   const LapKernel kern = lap_kernel(G, a.pi == nullptr, a.dual_mode == 1);
-  kern<<<grid, wpb * 32, smem, s>>>(a);
+  kern<<<grid, wpb * 32, smem, s>>>(b);
   return cudaGetLastError();
 }
 
@@ -253,8 +365,6 @@ static NodeLapKernel node_lap_kernel(int G, bool pre, bool fx) {
   return G == 8 ? node_lap_kernel<8>(pre, fx) : (G == 16 ? node_lap_kernel<16>(pre, fx) : node_lap_kernel<32>(pre, fx));
 }
 
-static int g_occ_nodes[33][3][2];
-
 cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s) {
   if (a.total <= 0) return cudaSuccess;
   if (a.max_m < 1 || a.max_m > 32 || a.nnodes < 1 || a.nnodes > kMaxWaveNodes) return cudaErrorInvalidValue;
@@ -265,15 +375,12 @@ cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s) {
   const size_t smem = pre + warp_smem_bytes(a.max_m, G) * wpb;
   cudaError_t e;
   std::unique_lock<std::mutex> lock(g_cfg_mu);
-  if (!g_sms) {
-    int dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  }
-  static bool attr_set[3] = {false, false, false};
+  LapDevCfg* cfg = nullptr;
+  if ((e = current_cfg(&cfg)) != cudaSuccess) return e;
+  bool* attr_set = cfg->attr_nodes;
   const size_t cap_smem = (((size_t)(kMaxWaveNodes + 1) * sizeof(long long)) + 255) / 256 * 256 +
                           warp_smem_bytes(32, 32) * kMaxWarpsPerBlock;
-  int& occ = g_occ_nodes[a.max_m][gidx(G)][wpb == 4 ? 0 : 1];
+  int& occ = cfg->occ_nodes[a.max_m][gidx(G)][wpb == 4 ? 0 : 1];
   // occupancy of the slowest of the four forms, computed once per size (the
   // prefix table's share of shared memory varies with the node count; a grid
   // above the resident count only queues blocks, which never wait on others)
@@ -293,7 +400,7 @@ cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s) {
     attr_set[gidx(G)] = true;
     occ = lo < 1 ? 1 : lo;
   }
-  const long long cap = (long long)g_sms * occ;
+  const long long cap = (long long)cfg->sms * occ;
   lock.unlock();
   const long long per_block = (long long)wpb * (32 / G);
   const long long need = (a.total + per_block - 1) / per_block;

@@ -87,7 +87,9 @@ __global__ void k_noalloc_init(int n, int* fac, int* loc, int* trips, int ntrip,
 }
 
 // Device address of the workspace on the current device, looked up once per
-// device (the first call on a device does it, with that device current).
+// device (the first call on a device does it, with that device current).  A
+// cudaDeviceReset unloads the module, so the cached address (like the LAP
+// launch set-up) is not valid across a reset: do not use the library after one.
 cudaError_t scratch_for_current_device(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -125,6 +127,11 @@ extern "C" rlt2_status rlt2_iterate_noalloc(int n, const double* F, const double
   if (p) prm = *p;
   if (!params_valid(prm) || prm.half_z) {
     set_error("rlt2_iterate_noalloc: parameters out of range (the half-Z scheme needs a context)");
+    return RLT2_EINVAL;
+  }
+  if (prm.warm == 2) {
+    // the learned start needs a network (rlt2_set_mlp) and its prediction buffer
+    set_error("rlt2_iterate_noalloc: warm = 2 (learned start) needs a context with rlt2_set_mlp; use warm 0 or 1");
     return RLT2_EINVAL;
   }
   double* base = nullptr;

@@ -65,6 +65,8 @@ struct LapArgs {
   int group;                 // lanes per LAP (8, 16 or 32); 0 = smallest that fits m
   int warps_per_block;       // 4 or 8; 0 = 8
   const int* map;            // nullable: LAP b works on slot map[b] of every array (a subset of tiles)
+  int prefetch;              // set by launch_lap: the fixed-point form without Badd and pi stages
+                             // the next tile by cp.async while it solves the current one
 };
 
 // The LAPs of one stage of one branch-and-bound node.
@@ -124,9 +126,14 @@ struct PipeArgs {
   long long nmove;
   unsigned long long* ctr;   // [0] move head, [1] warps done, [2] LAP head, [4 + a*n + b] blocks done for pair a < b
   DevScalars* sc;            // stop flags (a wait that gives up sets done, reason 4)
+  int spin_limit;            // polls of a pair counter before a LAP warp gives up
+  unsigned long long extra;  // added to the pair target: 0, or 1 in the failure-detection check
 };
+// check: the failure-detection form (rlt2_pipeline_check_wait_timeout): the
+// pair targets are raised by one, so no wait can be satisfied, and the polls
+// are capped low so that the first wait gives up within a few milliseconds.
 cudaError_t launch_move_lap_z(const MoveZArgs& mz, const LapArgs& z, const PipePlan& plan, unsigned long long* ctr,
-                              DevScalars* sc, cudaStream_t s);
+                              DevScalars* sc, cudaStream_t s, bool check = false);
 
 // Lanes per LAP the launcher would pick for size m (8, 16 or 32).
 int default_group(int m);
@@ -169,6 +176,7 @@ struct IterView {
   long long Tz;     // number of Z-LAPs solved (T, or T/2 with the half scheme)
   const PipePlan* pplan;   // nullable: pipelined z move + Z-LAPs (see PipePlan)
   unsigned long long* pipe;  // their queues and pair counters (4 + n*n)
+  int pipe_check;            // 1: the pipelined launch in its failure-detection form
   const double* bqap;     // nullable: QAP linear costs for upper bounds (default bprime)
   const double* cst_qap;  // nullable: QAP constant for upper bounds (default d_cst)
   int *xperm, *ubperm, *trips;

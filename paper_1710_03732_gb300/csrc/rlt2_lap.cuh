@@ -133,6 +133,33 @@ __device__ __forceinline__ long long fx_floor(double x, int L, int lim) {
   return (b < 0 ? -mant : mant) >> sh;
 }
 
+// fx_floor for an entry of the tile whose grid is L: its exponent is at most
+// the tile's largest, so |x| < 2^(L + 48) and the clamp of fx_floor cannot
+// apply; the result is the same.
+__device__ __forceinline__ long long fx_floor_entry(double x, int L) {
+  const long long b = __double_as_longlong(x);
+  const int eb = (int)((b >> 52) & 0x7ff);
+  const long long mant = (b & 0xFFFFFFFFFFFFFll) | (eb ? (1ll << 52) : 0ll);
+  const int sh = min(L + 1075 - (eb ? eb : 1), 63);  // >= 5
+  return (b < 0 ? -mant : mant) >> sh;
+}
+
+// Biased exponent field from the high word of a double in shared memory.
+__device__ __forceinline__ unsigned fx_expfield_hi(const double* p) {
+  return (reinterpret_cast<const unsigned*>(p)[1] >> 20) & 0x7ffu;
+}
+
+// Asynchronous global -> shared copies of 8 bytes (cp.async, no registers held
+// while in flight), committed as one group per call site and awaited with
+// cp_async_wait_all (the copies of this thread; a __syncwarp then makes the
+// group's copies visible to its lanes).
+__device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // q * 2^L rounded to the nearest double (L >= -1069 by construction of fx_grid).
 __device__ __forceinline__ double fx_to_double(long long q, int L) {
   const double p2 = L >= -1022 ? __longlong_as_double((long long)(L + 1023) << 52)
@@ -180,6 +207,12 @@ __device__ __forceinline__ unsigned group_bits(unsigned ball, int gb) {
   else return (ball >> gb) & ((1u << G) - 1u);
 }
 
+// Called by group_lap once the column reduction has read the staged raw tile
+// (all lanes, after a __syncwarp): the caller may then reuse the raw buffer.
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
 // Solve one LAP per group of G lanes (32/G LAPs per warp) in lockstep: every
 // intrinsic is executed by all 32 lanes with the full mask and all loops are
 // warp-uniform (they run while any group still has work; idle groups only
@@ -191,10 +224,17 @@ __device__ __forceinline__ unsigned group_bits(unsigned ball, int gb) {
 // PRE: the caller does not need the tile afterwards, so the canonical pass may
 // replace it by its reduced costs first (uvs: 64 values of group staging).
 // A: ArithF64 or ArithFx (the tile and u0 already on the grid).
-template <int G, bool PRE, typename A>
+// raw (fixed point only, nullable): the group's tile as m*m doubles, row-major
+// and unconverted, in shared memory; the column reduction then converts each
+// entry onto the grid 2^L as it reads it (lanes = columns) and stores it into
+// cs, and calls hook() once raw is no longer needed.  Without raw, cs already
+// holds the converted tile.
+template <int G, bool PRE, typename A, typename Hook = NoHook>
 __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T* __restrict__ cs, int ld, int m,
                                                                   int lane, bool warm, typename A::T u0,
-                                                                  int dual_mode, int* scr, typename A::T* uvs) {
+                                                                  int dual_mode, int* scr, typename A::T* uvs,
+                                                                  const double* raw = nullptr, int L = 0,
+                                                                  const Hook& hook = Hook()) {
   using T = typename A::T;
   const int gl = lane & (G - 1);
   const int gb = lane - gl;
@@ -205,19 +245,42 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
   T v = T(0);
   int naug = 0, nrelax = 0;
 
-  // column reduction with the argmin row
+  // column reduction with the argmin row (fixed point: the start duals are
+  // broadcast from shared memory, one load instead of two shuffles per row)
   unsigned long long bestk = ~0ull;
   int arg = -1;
+  if constexpr (A::kExact) {
+    if (warm) uvs[gl] = u;
+    __syncwarp();
+  }
   for (int r = 0; r < M; ++r) {
-    const T ur = __shfl_sync(kFull, u, gb + r);
+    T ur;
+    if constexpr (A::kExact) ur = warm ? uvs[r] : T(0);
+    else ur = __shfl_sync(kFull, u, gb + r);
     if (cv && r < m) {
-      const T c = cs[r * ld + gl];
+      T c;
+      if constexpr (A::kExact) {
+        if (raw) {
+          c = fx_floor_entry(raw[r * m + gl], L);
+          cs[r * ld + gl] = c;
+        } else {
+          c = cs[r * ld + gl];
+        }
+      } else {
+        c = cs[r * ld + gl];
+      }
       const T x = warm ? A::sub(c, ur) : c;  // c - 0 == c exactly
       if (arg < 0 || (A::kExact ? x < v : A::key(x) < bestk)) {
         if constexpr (!A::kExact) bestk = A::key(x);
         arg = r;
         v = x;
       }
+    }
+  }
+  if constexpr (A::kExact) {
+    if (raw) {
+      __syncwarp();  // every lane's reads of raw are done
+      hook();
     }
   }
   // greedy: the lowest column among those sharing an argmin row takes it
@@ -394,6 +457,12 @@ __host__ __device__ inline int tile_ld(int m) { return m | 1; }  // odd stride: 
 // Shared memory per warp: 32/G tiles, u/v staging (64 doubles) and 32 ints.
 __host__ __device__ inline size_t warp_smem_bytes(int m, int G) {
   return (size_t)(32 / G) * m * tile_ld(m) * sizeof(double) + 64 * sizeof(double) + 32 * sizeof(int);
+}
+// The prefetching form adds, per group, the next tile (m*m doubles, as stored)
+// and its start duals (m doubles), rounded to 16 bytes.
+__host__ __device__ inline size_t raw_group_doubles(int m) { return ((size_t)m * m + m + 1) & ~size_t(1); }
+__host__ __device__ inline size_t warp_smem_bytes_async(int m, int G) {
+  return warp_smem_bytes(m, G) + (size_t)(32 / G) * raw_group_doubles(m) * sizeof(double);
 }
 
 // Stages one group's tile (plus an optional addend) into shared memory, the

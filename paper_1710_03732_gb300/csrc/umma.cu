@@ -251,23 +251,28 @@ cudaError_t umma_mlp_forward(const bf16* X, long long rows, const bf16* W1, cons
                              const float* b2, const float* w3, const float* b3, float* out, int* err,
                              cudaStream_t s, bool withhold_commit) {
   if (rows <= 0) return cudaSuccess;
-  static std::mutex mu;  // one-time launch configuration, from any host thread
-  static int sms = 0;
-  static bool attr = false;
+  // launch configuration, once per device, from any host thread (not valid
+  // across a cudaDeviceReset, like every per-device cache of the library)
+  static std::mutex mu;
+  constexpr int kDevs = 64;
+  static int sms_of[kDevs];
+  static bool attr_of[kDevs];
   cudaError_t e;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if (dev < 0 || dev >= kDevs) return cudaErrorInvalidDevice;
   {
     std::lock_guard<std::mutex> lock(mu);
-    if (!sms) {
-      int dev = 0;
-      if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-      if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    }
-    if (!attr) {
+    if (!sms_of[dev] &&
+        (e = cudaDeviceGetAttribute(&sms_of[dev], cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return e;
+    if (!attr_of[dev]) {
       if ((e = cudaFuncSetAttribute(k_umma_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem)) !=
           cudaSuccess)
         return e;
-      attr = true;
+      attr_of[dev] = true;
     }
+    sms = sms_of[dev];
   }
   const long long tiles = (rows + kRowsPerTile - 1) / kRowsPerTile;
   const int grid = (int)(tiles < sms ? tiles : sms);

@@ -55,7 +55,8 @@ EXPORTS = ["rlt2_params_default", "rlt2_create", "rlt2_iterate", "rlt2_iterate_a
            "rlt2_mlp_set_weights", "rlt2_mlp_add_samples", "rlt2_mlp_samples", "rlt2_mlp_clear_samples",
            "rlt2_mlp_grad", "rlt2_mlp_fit", "rlt2_mlp_set_gate", "rlt2_mlp_predict", "rlt2_set_mlp",
            "rlt2_export_xstate", "rlt2_import_xstate", "rlt2_set_sa", "rlt2_create_child", "rlt2_bnb_options_default",
-           "rlt2_bnb_solve", "rlt2_mlp_check_wait_timeout", "rlt2_debug_bounds_violations", "rlt2_strerror",
+           "rlt2_bnb_solve", "rlt2_mlp_check_wait_timeout", "rlt2_pipeline_check_wait_timeout",
+           "rlt2_debug_bounds_violations", "rlt2_probe_rates", "rlt2_fp64_add_emulated", "rlt2_strerror",
            "rlt2_last_error"]
 
 
@@ -110,6 +111,9 @@ def lib():
     L.rlt2_mlp_predict.argtypes = [_vp, ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp]
     L.rlt2_mlp_set_gate.argtypes = [_vp, ctypes.c_double]
     L.rlt2_mlp_check_wait_timeout.argtypes = [_vp]
+    L.rlt2_pipeline_check_wait_timeout.argtypes = [_vp]
+    L.rlt2_probe_rates.argtypes = [_dp, _dp, _vp]
+    L.rlt2_fp64_add_emulated.argtypes = [ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp]
     L.rlt2_set_mlp.argtypes = [_vp, _vp]
     L.rlt2_strerror.argtypes = [ctypes.c_int]
     L.rlt2_strerror.restype = ctypes.c_char_p
@@ -322,6 +326,30 @@ def rlt2_bnb_solve(F, D, B=None, prm: Optional[rlt2_params] = None, opts: Option
 def rlt2_debug_bounds_violations() -> int:
     """Indices the bounds-checked library caught out of range (-1: normal build)."""
     return int(lib().rlt2_debug_bounds_violations())
+
+
+def rlt2_pipeline_check_wait_timeout(ctx: int) -> int:
+    """Runs the pipelined launch's failure-detection check on ctx; returns the
+    status (RLT2_ETIMEOUT is the expected outcome) without raising for it."""
+    st = lib().rlt2_pipeline_check_wait_timeout(ctx)
+    if st not in (RLT2_OK, RLT2_ETIMEOUT):
+        _check(st, "rlt2_pipeline_check_wait_timeout")
+    return st
+
+
+def rlt2_probe_rates(stream=None) -> dict:
+    """Measured lane-operation rates of the current device (G ops/s) and its
+    rated SM clock (GHz)."""
+    r = np.zeros(5)
+    clk = ctypes.c_double()
+    _check(lib().rlt2_probe_rates(_host_d(r), ctypes.byref(clk), _stream(stream)), "rlt2_probe_rates")
+    return {"dadd": r[0], "dfma": r[1], "iadd64": r[2], "iadd32": r[3], "emu_add": r[4], "sm_clock_ghz": clk.value}
+
+
+def rlt2_fp64_add_emulated(a, b, total, diff, stream=None):
+    """a + b and a - b by the integer-pipe binary64 addition (CUDA float64 tensors)."""
+    _check(lib().rlt2_fp64_add_emulated(int(a.numel()), _ptr(a), _ptr(b), _ptr(total), _ptr(diff), _stream(stream)),
+           "rlt2_fp64_add_emulated")
 
 
 def rlt2_destroy(ctx: int):

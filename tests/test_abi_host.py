@@ -22,7 +22,7 @@ def L():
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "rlt2.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(rlt2_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(rlt2_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_expected_api():

@@ -119,3 +119,30 @@ def test_pipeline_parameter_checked(R):
     inst = I.config(1)
     with pytest.raises(R.Rlt2Error):
         R.Context(inst.F, inst.D, inst.B, prm=R.params(pipeline=2))
+
+
+def test_pipeline_wait_times_out_without_a_fault(R):
+    """Failure detection of the pipelined launch: in its check form the LAP
+    warps wait for pair counts the move never reaches, with the polls capped
+    low; the wait gives up, the step reports RLT2_ETIMEOUT through the host,
+    the launch ends, and the same device then runs a fresh pipelined ascent
+    with the two-launch sequence's results."""
+    inst = I.config(2)
+    with R.Context(inst.F, inst.D, inst.B, prm=R.params(feas_tol=0.0, warm=1, pipeline=1)) as ctx:
+        with pytest.raises(R.Rlt2Error) as e:  # no move pending before the first solve
+            R._check(R.lib().rlt2_pipeline_check_wait_timeout(ctx.ctx), "check")
+        assert e.value.status == R.RLT2_EINVAL
+        _, done = ctx.iterate(3)
+        assert done == 3
+        assert R.rlt2_pipeline_check_wait_timeout(ctx.ctx) == R.RLT2_ETIMEOUT
+        assert "gave up" in R.lib().rlt2_last_error().decode()
+        with pytest.raises(R.Rlt2Error) as e:  # the context is stopped and keeps reporting it
+            ctx.iterate(2)
+        assert e.value.status == R.RLT2_ETIMEOUT
+    with R.Context(inst.F, inst.D, inst.B, prm=R.params(feas_tol=0.0, warm=1, pipeline=0)) as ctx:
+        with pytest.raises(R.Rlt2Error) as e:
+            R._check(R.lib().rlt2_pipeline_check_wait_timeout(ctx.ctx), "check")
+        assert e.value.status == R.RLT2_EINVAL
+    a = _run(R, inst, 12, None, warm=1, pipeline=1)
+    b = _run(R, inst, 12, None, warm=1, pipeline=0)
+    assert a[1] == b[1] == 12 and np.array_equal(a[0], b[0]) and np.array_equal(a[2], b[2])

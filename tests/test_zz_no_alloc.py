@@ -85,3 +85,15 @@ def test_noalloc_rejects_the_half_z_scheme(R):
     out = torch.empty(3, dtype=torch.float64, device="cuda")
     with pytest.raises(R.Rlt2Error):
         R.rlt2_iterate_noalloc(F, D, out, prm=R.half_z_params())
+
+
+def test_noalloc_rejects_the_learned_start(R):
+    """warm = 2 needs a network set on a context; the no-allocation path has
+    none, so it must refuse instead of running a cold start."""
+    inst = I.config(1)
+    F = torch.from_numpy(inst.F).cuda()
+    D = torch.from_numpy(inst.D).cuda()
+    out = torch.empty(3, dtype=torch.float64, device="cuda")
+    with pytest.raises(R.Rlt2Error) as e:
+        R.rlt2_iterate_noalloc(F, D, out, prm=R.params(warm=2))
+    assert e.value.status == R.RLT2_EINVAL and "learned start" in str(e.value)
