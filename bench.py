@@ -380,8 +380,12 @@ def run_bnb_hard():
     R.lib()
     inst = I.grid_instance("n20_grid4x5", 4, 5, 9, 0.5, 12, 1)
     res = {"workload": "QAP n=20, D = Manhattan 4x5 grid, F symmetric 0..9 at density 0.5 (seed 12), B = 0"}
-    for wd, tag in ((64, "warm"), (-1, "cold")):
-        opts = R.bnb_options(iters_root=300, iters_node=60, warm_depth=wd, time_limit_s=600.0)
+    runs = ((64, 1, "warm"), (64, 0, "warm_one_at_a_time"), (-1, 1, "cold"))
+    if os.environ.get("RLT2_BNB_RUNS"):
+        runs = tuple(r for r in runs if r[2] in os.environ["RLT2_BNB_RUNS"].split(","))
+    for wd, batch, tag in runs:
+        # batch: the children of a branched node bounded together (rlt2_iterate_many)
+        opts = R.bnb_options(iters_root=300, iters_node=60, warm_depth=wd, time_limit_s=600.0, batch_children=batch)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         best, perm, rlb, st = R.rlt2_bnb_solve(inst.F, inst.D, inst.B, prm=R.params(warm=1, stall_window=25),
@@ -434,7 +438,8 @@ def extra_workloads(R, torch):
         if warm == 2 and mlp is None:
             continue
         prm = R.params(feas_tol=0.0, warm=warm)
-        R.rlt2_bound_nodes(inst.F, inst.D, inst.partials[:4], 6, prm=prm, mlp=mlp)  # tuning + warm-up
+        # warm-up that also tunes the Z-stage shape of every size present (the table is kept)
+        R.rlt2_bound_nodes(inst.F, inst.D, inst.partials, 6, prm=prm, mlp=mlp)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         lb, _, its, st = R.rlt2_bound_nodes(inst.F, inst.D, inst.partials, iters, prm=prm, mlp=mlp)
@@ -443,6 +448,7 @@ def extra_workloads(R, torch):
         c4[["cold", "warm", "learned"][warm]] = {"node_iters_per_s": float(its.sum() / dt), "seconds": dt,
                                                  "z_aug": int(st["z_aug"]), "lb_sum": float(lb.sum()),
                                                  "z_lanes_per_lap": int(st["group"]), "z_warps_per_block": int(st["wpb"])}
+    c4["z_shape_per_size"] = R.rlt2_node_tuning()
     out["config4_nodes"] = c4
     # config 5: n = 30
     inst = I.config(5)
@@ -476,10 +482,40 @@ def extra_workloads(R, torch):
             with R.Context(inst.F, inst.D, inst.B, prm=R.params(feas_tol=0.0, warm=warm)) as ctx:
                 if warm == 2:
                     ctx.set_mlp(mlp)
-                lbs, _ = ctx.iterate(20)
-                lw[["cold", "warm", "learned"][warm]] = {"z_aug": int(ctx.stats()[1]), "lb_last": float(lbs[-1])}
+                ctx.iterate(4)
+                s0 = ctx.stats()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                lbs, _ = ctx.iterate(16)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                lw[["cold", "warm", "learned"][warm]] = {"z_aug": int(ctx.stats()[1] - s0[1]), "lb_last": float(lbs[-1]),
+                                                         "ms_per_iteration": 1e3 * dt / 16}
+                if warm == 2:
+                    # inference alone on this state's tiles (CUDA events): the network's cost per iteration
+                    T, m = ctx.T, ctx.n - 2
+                    D = torch.empty(ctx.E, dtype=torch.float64, device="cuda")
+                    xi = torch.empty(T * m, dtype=torch.float64, device="cuda")
+                    R.rlt2_export_state(ctx.ctx, Dhat=D, on_device=1)
+                    R.rlt2_duals(ctx.ctx, xi=xi, on_device=1)
+                    u0 = torch.empty(T, m, dtype=torch.float64, device="cuda")
+                    mlp.predict(D.view(T, m, m), u0, xi.view(T, m))
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for _ in range(5):
+                        mlp.predict(D.view(T, m, m), u0, xi.view(T, m))
+                    e1.record()
+                    torch.cuda.synchronize()
+                    lw["learned"]["inference_ms_per_iteration"] = e0.elapsed_time(e1) / 5
+                    del D, xi, u0
         lw["learned_saves_vs_cold"] = 1.0 - lw["learned"]["z_aug"] / lw["cold"]["z_aug"]
         lw["warm_saves_vs_cold"] = 1.0 - lw["warm"]["z_aug"] / lw["cold"]["z_aug"]
+        # break-even: the inference time per iteration below which the learned
+        # start would match the other start's iteration time (negative: it loses
+        # even with free inference)
+        solve = lw["learned"]["ms_per_iteration"] - lw["learned"]["inference_ms_per_iteration"]
+        lw["break_even_inference_ms"] = {"vs_cold": lw["cold"]["ms_per_iteration"] - solve,
+                                         "vs_previous_duals": lw["warm"]["ms_per_iteration"] - solve}
         out["learned_warm_start_n20"] = lw
         mlp.close()
     return out

@@ -196,6 +196,24 @@ rlt2_status rlt2_create_child(rlt2_ctx* parent, int facility, int location, cons
  * Synchronises the context's stream before returning. */
 rlt2_status rlt2_iterate(rlt2_ctx* ctx, int iters, double* lb_hist, int* done);
 
+/* Up to `iters` iterations of several contexts' ascents in lockstep: every
+ * stage of an iteration is one launch over all of them (the batched node
+ * kernels of rlt2_bound_nodes, Z-LAPs launched per size with the tuned shapes
+ * of rlt2_node_tuning), so many small ascents, such as the children of a
+ * branch-and-bound node, share the GPU instead of taking turns.  Each context
+ * follows exactly the trajectory rlt2_iterate would give it and stops on its
+ * own rules; the call returns once every context has stopped (checked between
+ * chunks of 8, 16, 32, ... iterations) or after `iters` iterations.
+ *  ctxs  : count distinct contexts, 1 <= count <= 1024, all on the current
+ *          device, sharing dual_mode, warm (0 or 1) and two_phase; the
+ *          half-Z scheme and Type 4 draws are not supported (EINVAL)
+ *  done  : host, count ints (nullable): iterations each context ran
+ * Work runs on ctxs[0]'s stream after every context's stream is synchronised;
+ * the call synchronises before returning.  The contexts' augmentation and
+ * relaxation counters (rlt2_stats) do not count these iterations.  Calls from
+ * several host threads are serialised.  Errors: EINVAL, ECUDA. */
+rlt2_status rlt2_iterate_many(rlt2_ctx* const* ctxs, int count, int iters, int* done);
+
 /* Enqueue `iters` iterations without synchronising or reading anything back
  * (for timing and for callers that overlap work).  The bounds can be read
  * later with rlt2_bound. */
@@ -341,7 +359,8 @@ rlt2_status rlt2_lap_batched(int batch, int m, const double* cost, const double*
  *  iters_out  : host, n_nodes ints (nullable): iterations each node ran
  *  stats_out  : host, 5 long longs (nullable): {waves, Z augmentations,
  *               Z relaxations, lanes per Z-LAP, warps per block} where the
- *               last two are the autotuned Z-stage launch shape
+ *               last two are the autotuned Z-stage launch shape of the
+ *               largest Z-LAP size (rlt2_node_tuning lists every size)
  *  stream     : cudaStream_t; the call synchronises it before returning
  * Errors: EINVAL (bad input), EADMIT (a node alone exceeds mem_budget),
  * ENOMEM, ECUDA.  Device memory is allocated for the call and freed on return. */
@@ -374,6 +393,18 @@ rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D, const doub
                              const int* partials, const rlt2_params* p, rlt2_mlp* mlp, int iters, size_t mem_budget,
                              double* lb_out, double* lb_hist, int* iters_out, long long* stats_out, void* stream);
 
+/* The Z-stage launch shapes rlt2_bound_nodes has tuned in this process (no
+ * counterpart in the paper).  Within a wave the Z-LAPs are launched per size
+ * (adjacent sizes with the same shape share a launch); the shape of each size,
+ * lanes per LAP (8, 16, 32) and warps per block (4, 8), is chosen the first
+ * time that size occurs by timing the candidates on live iterations, and kept
+ * for the life of the process.  cap: capacity of the output arrays; m, group,
+ * wpb: host, cap ints (Z-LAP size, lanes per LAP, warps per block), ms: host,
+ * cap doubles (nullable; the chosen shape's Z-stage time for that size when it
+ * was tuned, milliseconds), sorted by size; *count: the number of sizes in the
+ * table (may exceed cap).  Errors: EINVAL. */
+rlt2_status rlt2_node_tuning(int cap, int* m, int* group, int* wpb, double* ms, int* count);
+
 /* Branch and bound to optimality (Section 4) on one GPU, every node bounded by
  * RLT2-DA.  Facilities are placed in a fixed order (order_rule 1: index order;
  * 2: largest total interaction first, then largest interaction with those
@@ -401,6 +432,9 @@ typedef struct rlt2_bnb_options {
   double abs_tol;       /* fathom when LB >= UB - abs_tol; < 0 (default): 1 - 1e-6 when F, D, B are
                            integral (the optimum is then an integer), else 1e-9 max(1, |UB|) */
   double max_state_bytes; /* device memory for kept parent contexts; 0 (default): half the free memory */
+  int batch_children;   /* 1 (default): the children of a branched node are bounded together in lockstep
+                           launches (rlt2_iterate_many); 0: one after the other (rlt2_iterate).  The
+                           half-Z scheme and the learned start always bound one after the other */
 } rlt2_bnb_options;
 void rlt2_bnb_options_default(rlt2_bnb_options* o);
 

@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -254,7 +255,8 @@ struct rlt2_ctx {
   long long T = 0, E = 0;
   rlt2_params prm{};
   cudaStream_t stream = nullptr;
-  cudaStream_t cap_stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // created when the first graph is captured
+  char* arena = nullptr;              // every fixed-size buffer, one pool allocation
   std::vector<int> fac, loc;  // free facilities / locations (host)
   std::vector<int> fixf, fixl;
   double* d_cst = nullptr;
@@ -287,24 +289,57 @@ struct rlt2_ctx {
   unsigned long long* pipe = nullptr;  // its queue head, exit count and pair counters
 };
 
+// Device memory of contexts.  A branch and bound creates and destroys a
+// context per node, and cudaMalloc / cudaFree (which waits for the whole
+// device) cost about a millisecond per node for the twenty-odd buffers; so a
+// context takes all its fixed-size buffers as one arena from a stream-ordered
+// memory pool of the library (one per device), allocated and freed in order on
+// the context's stream.  The pool keeps up to a quarter of the device's memory
+// cached for reuse after contexts are destroyed.
+static std::mutex g_pool_mu;
+constexpr int kPoolDevices = 64;
+static cudaMemPool_t g_pool[kPoolDevices];
+
+static cudaError_t ctx_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kPoolDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess) return e;
+    size_t fr = 0, tot = 0;
+    if ((e = cudaMemGetInfo(&fr, &tot)) != cudaSuccess) return e;
+    unsigned long long keep = tot / 4;
+    if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) return e;
+    g_pool[dev] = pool;
+  }
+  *out = g_pool[dev];
+  return cudaSuccess;
+}
+
+// Bytes the pool holds but no context uses (available to the next context).
+static size_t ctx_pool_idle(cudaMemPool_t pool) {
+  unsigned long long reserved = 0, used = 0;
+  if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) != cudaSuccess ||
+      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess)
+    return 0;
+  return reserved > used ? (size_t)(reserved - used) : 0;
+}
+
 static void ctx_free(rlt2_ctx* c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (auto e : c->ev) cudaEventDestroy(e);
-  void* ptrs[] = {c->d_cst, c->Fr,    c->Dr,   c->bprime, c->Chat, c->Dhat,  c->Theta, c->xi,
-                  c->psi,   c->Delta, c->gamma, c->delta, c->alpha, c->beta, c->pix,   c->piy,
-                  c->tterm, c->xval,  c->ring, c->xperm,  c->ubperm, c->trips, c->sc};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
-  if (c->xcost && c->xcost != c->bprime) cudaFree(c->xcost);
-  if (c->saterm) cudaFree(c->saterm);
+  if (c->arena) cudaFreeAsync(c->arena, c->stream);
   if (c->sa_buf) cudaFree(c->sa_buf);
-  if (c->zmap) cudaFree(c->zmap);
-  if (c->bqap && c->bqap != c->bprime) cudaFree(c->bqap);
-  if (c->d_cst_qap && c->d_cst_qap != c->d_cst) cudaFree(c->d_cst_qap);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->u0buf) cudaFree(c->u0buf);
-  if (c->pipe) cudaFree(c->pipe);
   delete c;
 }
 
@@ -426,6 +461,18 @@ static cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
 }
 
+// Sub-arrays of a context's arena, each 256-byte aligned; with base == nullptr
+// it only counts, so sizing and carving cannot disagree.
+struct CtxCarver {
+  char* base;
+  size_t used = 0;
+  template <class T>
+  void take(T** p, size_t count) {
+    *p = base ? reinterpret_cast<T*>(base + used) : nullptr;
+    used += (sizeof(T) * (count ? count : 1) + 255) & ~size_t(255);
+  }
+};
+
 // Device buffers of a context whose sizes (n, m, T, E, ntrip) and parameters
 // are set: memory admission, allocation, the capture stream, cleared D^, duals
 // and Theta, fresh scalars, the facility triples and (half-Z scheme) the tile
@@ -439,11 +486,14 @@ static rlt2_status ctx_alloc(rlt2_ctx* c, bool own_qap) {
                                   2 * (size_t)nr * nr * nr + kRing) +
                 sizeof(int) * (size_t)(c->ntrip + nr + (prm.half_z ? c->T / 2 : 0)) + (64u << 20);
   size_t fr = 0, tot = 0;
-  cudaError_t e = cudaMemGetInfo(&fr, &tot);
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = ctx_pool(&pool);
+  if (e == cudaSuccess) e = cudaMemGetInfo(&fr, &tot);
   if (e != cudaSuccess) {
     delete c;
     return cuda_fail(e, "cudaMemGetInfo");
   }
+  fr += ctx_pool_idle(pool);
   if (need > fr) {
     delete c;
     set_error("rlt2_create: not enough free device memory");
@@ -456,12 +506,10 @@ static rlt2_status ctx_alloc(rlt2_ctx* c, bool own_qap) {
     ctx_free(c);
     return st;
   };
-#define AL(ptr, cnt)                                      \
-  do {                                                    \
-    cudaError_t e2 = dalloc(&(ptr), (cnt));               \
-    if (e2 != cudaSuccess) return fail(e2, "cudaMalloc"); \
-  } while (0)
   const size_t T = c->T, m = c->m, n2 = (size_t)nr * nr;
+  // the arena: sized by a counting pass, then allocated once and carved
+  auto carve = [&](CtxCarver& cv) {
+#define AL(ptr, cnt) cv.take(&(ptr), (cnt))
   AL(c->d_cst, 1);
   AL(c->Fr, n2);
   AL(c->Dr, n2);
@@ -492,18 +540,27 @@ static rlt2_status ctx_alloc(rlt2_ctx* c, bool own_qap) {
     AL(c->bqap, n2);
     AL(c->d_cst_qap, 1);
   }
+  if (prm.pipeline && !prm.half_z) AL(c->pipe, 4 + n2);
+#undef AL
+  };
+  {
+    CtxCarver count{nullptr};
+    carve(count);
+    if ((e = cudaMallocFromPoolAsync((void**)&c->arena, count.used, pool, c->stream)) != cudaSuccess) {
+      c->arena = nullptr;
+      return fail(e, "context arena");
+    }
+    CtxCarver cv{c->arena};
+    carve(cv);
+  }
   if (prm.pipeline && !prm.half_z) {
-    AL(c->pipe, 4 + n2);
     cudaError_t e2 = cudaSuccess;
     c->pplan = prepare_pipe(nr, &e2);
     if (!c->pplan) return fail(e2, "pipelined move and Z-LAP plan");
   }
-#undef AL
   if (!c->xcost) c->xcost = c->bprime;  // S variant: the X-LAP reads b' itself
   if (!c->bqap) c->bqap = c->bprime;
   if (!c->d_cst_qap) c->d_cst_qap = c->d_cst;
-  if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
-    return fail(e, "cudaStreamCreate");
   std::vector<int> trips;
   trips.reserve(c->ntrip);
   for (int i = 0; i < nr; ++i)
@@ -1007,6 +1064,7 @@ extern "C" rlt2_status rlt2_pipeline_check_wait_timeout(rlt2_ctx* c) {
 
 static rlt2_status build_graph(rlt2_ctx* c) {
   if (c->graph) return RLT2_OK;
+  if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = enqueue_iteration_ctx(c, c->cap_stream, -1);
@@ -1070,6 +1128,56 @@ static rlt2_status enqueue_many(rlt2_ctx* c, int iters) {
   if (st != RLT2_OK) return st;
   for (int it = 0; it < iters; ++it) CK(cudaGraphLaunch(c->graph, c->stream));
   c->enqueued += iters;
+  return RLT2_OK;
+}
+
+extern "C" rlt2_status rlt2_iterate_many(rlt2_ctx* const* ctxs, int count, int iters, int* done) {
+  if (!ctxs || count < 1 || count > kMaxWaveNodes || iters < 0) {
+    set_error("rlt2_iterate_many: need 1 <= count <= 1024 contexts and iters >= 0");
+    return RLT2_EINVAL;
+  }
+  const rlt2_ctx* c0 = ctxs[0];
+  for (int k = 0; k < count; ++k) {
+    const rlt2_ctx* c = ctxs[k];
+    if (!c) {
+      set_error("rlt2_iterate_many: a context is NULL");
+      return RLT2_EINVAL;
+    }
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == c) {
+        set_error("rlt2_iterate_many: a context appears twice");
+        return RLT2_EINVAL;
+      }
+    if (c->prm.dual_mode != c0->prm.dual_mode || c->prm.warm != c0->prm.warm ||
+        c->prm.two_phase != c0->prm.two_phase) {
+      set_error("rlt2_iterate_many: the contexts must share dual_mode, warm and two_phase");
+      return RLT2_EINVAL;
+    }
+    if (c->prm.half_z || c->prm.warm == 2 || c->sa_count > 0) {
+      set_error("rlt2_iterate_many: the half-Z scheme, the learned start and Type 4 draws need rlt2_iterate");
+      return RLT2_EINVAL;
+    }
+  }
+  // the contexts' own streams first (their earlier work), then everything on the first one's
+  for (int k = 0; k < count; ++k) CK(cudaStreamSynchronize(ctxs[k]->stream));
+  std::vector<IterView> views;
+  std::vector<int> before(count);
+  views.reserve(count);
+  for (int k = 0; k < count; ++k) {
+    views.push_back(view_of(ctxs[k]));
+    before[k] = ctxs[k]->iter_host;
+  }
+  int ran = 0;
+  const cudaError_t e = iterate_views(views.data(), count, c0->prm, iters, c0->stream, &ran);
+  if (e != cudaSuccess) return cuda_fail(e, "rlt2_iterate_many");
+  for (int k = 0; k < count; ++k) {
+    rlt2_ctx* c = ctxs[k];
+    int it = 0;
+    CK(cudaMemcpy(&it, &c->sc->iter, sizeof(int), cudaMemcpyDeviceToHost));
+    c->enqueued += ran;
+    c->iter_host = it;
+    if (done) done[k] = it - before[k];
+  }
   return RLT2_OK;
 }
 

@@ -102,6 +102,7 @@ extern "C" void rlt2_bnb_options_default(rlt2_bnb_options* o) {
   o->ub0 = 0.0;
   o->abs_tol = -1.0;
   o->max_state_bytes = 0.0;
+  o->batch_children = 1;
 }
 
 extern "C" rlt2_status rlt2_bnb_solve(int n, const double* F, const double* D, const double* B, const rlt2_params* p,
@@ -116,7 +117,7 @@ extern "C" rlt2_status rlt2_bnb_solve(int n, const double* F, const double* D, c
   if (opt) o = *opt;
   if (o.order_rule < 1 || o.order_rule > 3 || o.iters_root < 1 || o.iters_node < 1 || o.max_states < 0 ||
       o.max_nodes < 0 || !std::isfinite(o.time_limit_s) || !std::isfinite(o.ub0) || !std::isfinite(o.abs_tol) ||
-      !(o.max_state_bytes >= 0.0)) {
+      !(o.max_state_bytes >= 0.0) || (o.batch_children != 0 && o.batch_children != 1)) {
     rlt2::set_error("rlt2_bnb_solve: options out of range");
     return RLT2_EINVAL;
   }
@@ -168,21 +169,27 @@ extern "C" rlt2_status rlt2_bnb_solve(int n, const double* F, const double* D, c
     }
     return q;
   };
-  // bound one node context: iterate, read the bound and its X-LAP primal
-  auto bound = [&](rlt2_ctx* c, int iters, double* lb_out) -> rlt2_status {
-    int done = 0;
-    rlt2_status s = rlt2_iterate(c, iters, nullptr, &done);
-    if (s != RLT2_OK) return s;
+  // a bounded node context: read its bound and offer its X-LAP primal
+  auto harvest = [&](rlt2_ctx* c, int done, double* lb_out) -> rlt2_status {
     double lb = 0.0, blb = 0.0, ub = 0.0;
     int its = 0;
     std::vector<int> up(n);
-    if ((s = rlt2_bound(c, &lb, &blb, &ub, nullptr, up.data(), &its)) != RLT2_OK) return s;
+    rlt2_status s = rlt2_bound(c, &lb, &blb, &ub, nullptr, up.data(), &its);
+    if (s != RLT2_OK) return s;
     ++bounded;
     iterations += done;
     if (std::isfinite(ub)) offer(qap_value(n, F, D, B, up), up);
     *lb_out = blb;
     return RLT2_OK;
   };
+  // bound one node context: iterate, read the bound and its X-LAP primal
+  auto bound = [&](rlt2_ctx* c, int iters, double* lb_out) -> rlt2_status {
+    int done = 0;
+    rlt2_status s = rlt2_iterate(c, iters, nullptr, &done);
+    if (s != RLT2_OK) return s;
+    return harvest(c, done, lb_out);
+  };
+  const bool batched = o.batch_children == 1 && !prm.half_z && prm.warm != 2;
   // nodes with at most two free facilities: enumerate their completions
   auto enumerate = [&](const std::vector<int>& part) {
     std::vector<int> ff, fl;
@@ -248,12 +255,31 @@ extern "C" rlt2_status rlt2_bnb_solve(int n, const double* F, const double* D, c
     for (int i = 0; i < n; ++i)
       if (nd->partial[i] >= 0) used[nd->partial[i]] = 1;
     ++branched;
+    const int depth = nd->depth + 1;
+    max_depth = std::max(max_depth, depth);
+    // a bounded child: fathomed, or pushed on the heap (its context kept for
+    // its own children within the depth and memory limits)
+    auto place = [&](rlt2_ctx* c, const std::vector<int>& part, double lb) {
+      if (fathomed(lb)) {
+        rlt2_destroy(c);
+        return;
+      }
+      Node* ch = new Node{lb, depth, part, nullptr, seq++};
+      if (depth <= o.warm_depth && kept < o.max_states && kept_bytes + ctx_bytes(n - depth) <= state_budget) {
+        ch->state = c;
+        ++kept;
+        kept_bytes += ctx_bytes(n - depth);
+      } else {
+        rlt2_destroy(c);
+      }
+      heap.push(ch);
+    };
+    std::vector<rlt2_ctx*> kids;  // batched: created first, then bounded together
+    std::vector<std::vector<int>> kparts;
     for (int loc = 0; loc < n && st == RLT2_OK; ++loc) {
       if (used[loc]) continue;
       std::vector<int> part = nd->partial;
       part[fac] = loc;
-      const int depth = nd->depth + 1;
-      max_depth = std::max(max_depth, depth);
       if (n - depth <= 2) {
         enumerate(part);
         continue;
@@ -268,24 +294,28 @@ extern "C" rlt2_status rlt2_bnb_solve(int n, const double* F, const double* D, c
         ++cold;
       }
       if (st != RLT2_OK) break;
+      if (batched) {
+        kids.push_back(c);
+        kparts.push_back(part);
+        continue;
+      }
+      // one at a time: each child is bounded before the next is created
       double lb = -INFINITY;
       if ((st = bound(c, o.iters_node, &lb)) != RLT2_OK) {
         rlt2_destroy(c);
         break;
       }
-      if (fathomed(lb)) {
-        rlt2_destroy(c);
-        continue;
+      place(c, part, lb);
+    }
+    if (!kids.empty()) {
+      std::vector<int> done(kids.size(), 0);
+      std::vector<double> klb(kids.size(), -INFINITY);
+      if (st == RLT2_OK) st = rlt2_iterate_many(kids.data(), (int)kids.size(), o.iters_node, done.data());
+      for (size_t k = 0; k < kids.size() && st == RLT2_OK; ++k) st = harvest(kids[k], done[k], &klb[k]);
+      for (size_t k = 0; k < kids.size(); ++k) {
+        if (st != RLT2_OK) rlt2_destroy(kids[k]);
+        else place(kids[k], kparts[k], klb[k]);
       }
-      Node* ch = new Node{lb, depth, part, nullptr, seq++};
-      if (depth <= o.warm_depth && kept < o.max_states && kept_bytes + ctx_bytes(n - depth) <= state_budget) {
-        ch->state = c;
-        ++kept;
-        kept_bytes += ctx_bytes(n - depth);
-      } else {
-        rlt2_destroy(c);
-      }
-      heap.push(ch);
     }
     if (nd->state) {
       rlt2_destroy(nd->state);

@@ -274,6 +274,111 @@ cudaError_t launch_lap(const LapArgs& a, cudaStream_t s) {
 // Batched branch-and-bound nodes: one persistent launch per stage over the LAPs
 // of every node of a wave.  Warps pull 32/G LAPs at a time from a device queue
 // (atomic head, no waiting), so nodes of uneven size share the GPU.
+// The queue-fed node form of k_lap_prefetching (fixed point, Z stages): a
+// warp claims its next queue slot before it solves the current one and copies
+// that slot's tiles and start duals into shared memory by cp.async (issued by
+// group_lap's hook once the current raw tiles are converted).  The raw buffers
+// are sized for the largest LAP of the stage.  Results are those of the staged
+// form bit for bit (each LAP is independent of which warp solves it).
+template <int G>
+__device__ __forceinline__ void k_lap_nodes_prefetching(const NodeLapArgs& a, const long long* s_prefix,
+                                                        unsigned char* base, int lane) {
+  using A = ArithFx;
+  using T = long long;
+  constexpr int per = 32 / G;
+  const int grp = lane / G, gl = lane & (G - 1);
+  const int MM = a.max_m;
+  T* tile = reinterpret_cast<T*>(base) + (size_t)grp * MM * tile_ld(MM);
+  T* uv = reinterpret_cast<T*>(base) + (size_t)per * MM * tile_ld(MM);
+  int* scr = reinterpret_cast<int*>(uv + 64) + grp * G;
+  double* raw = reinterpret_cast<double*>(base + warp_smem_bytes(MM, G)) + (size_t)grp * raw_group_doubles(MM);
+  unsigned long long aug_acc = 0, relax_acc = 0;
+  // the queue slot's LAP of this group: node k, LAP li of that node (have = false past the end or for a
+  // stopped node)
+  struct Slot {
+    bool have, warm;
+    int k;
+    long long li;
+  };
+  auto lookup = [&](unsigned long long b0) {
+    Slot sl{false, false, 0, 0};
+    const long long t = (long long)b0 + grp;
+    if (b0 < (unsigned long long)a.total && t < a.total) {
+      int lo = 0, hi = a.nnodes - 1;
+      while (lo < hi) {  // largest k with prefix[k] <= t
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_prefix[mid] <= t) lo = mid;
+        else hi = mid - 1;
+      }
+      sl.k = lo;
+      const NodeLapItem& it = a.items[lo];
+      sl.li = RLT2_IDX(t - s_prefix[lo], it.count);
+      sl.have = *it.skip == 0;
+      sl.warm = sl.have && it.u0 != nullptr && (it.warm_gate == nullptr || *it.warm_gate != 0);
+    }
+    return sl;
+  };
+  auto grab = [&]() {
+    unsigned long long b0 = 0;
+    if (lane == 0) b0 = atomicAdd(a.head, (unsigned long long)per);
+    return __shfl_sync(kFull, b0, 0);
+  };
+  auto issue = [&](const Slot& sl) {
+    if (sl.have) {
+      const NodeLapItem& it = a.items[sl.k];
+      const int m = it.m, mm = m * m;
+      const double* src = it.A + sl.li * mm;
+      for (int e = gl; e < mm; e += G) cp_async8(raw + e, src + e);
+      if (sl.warm && gl < m) cp_async8(raw + mm + gl, it.u0 + sl.li * m + gl);
+    }
+    cp_async_commit();
+  };
+  unsigned long long b0 = grab();
+  Slot cur = lookup(b0);
+  issue(cur);
+  while (b0 < (unsigned long long)a.total) {
+    const unsigned long long b1 = grab();
+    const Slot nxt = lookup(b1);
+    cp_async_wait_all();
+    __syncwarp();
+    const int m = cur.have ? a.items[cur.k].m : 0;
+    const int mm = m * m;
+    unsigned eb = 0;
+    for (int e = gl; e < mm; e += G) eb = max(eb, fx_expfield_hi(raw + e));
+    if constexpr (G == 32) {
+      eb = __reduce_max_sync(kFull, eb);
+    } else {
+#pragma unroll
+      for (int off = G / 2; off > 0; off >>= 1) eb = max(eb, __shfl_xor_sync(kFull, eb, off));
+    }
+    const int L = fx_grid(eb);
+    const T u0 = (cur.warm && gl < m) ? start_dual<true>(raw[mm + gl], L) : T(0);
+    const WarpLapResult<T> R = group_lap<G, true, A>(tile, tile_ld(m), m, lane, cur.warm, u0, a.dual_mode, scr,
+                                                     uv + grp * G, raw, L, [&]() { issue(nxt); });
+    if (cur.have) {
+      const NodeLapItem& it = a.items[cur.k];
+      if (gl < m) {
+        if (it.u) it.u[cur.li * m + gl] = out_value<true>(R.u, L);
+        if (it.v) it.v[cur.li * m + gl] = out_value<true>(R.v, L);
+        if (it.r2c) it.r2c[cur.li * m + gl] = R.r2c;
+      }
+      if (gl == 0) {
+        it.value[cur.li] = out_value<true>(R.value, L);
+        aug_acc += R.naug;
+        relax_acc += R.nrelax;
+      }
+    }
+    __syncwarp();
+    b0 = b1;
+    cur = nxt;
+  }
+  cp_async_wait_all();  // nothing may be in flight when the warp leaves
+  if (a.stats && gl == 0 && (aug_acc | relax_acc)) {
+    atomicAdd(a.stats + 0, aug_acc);
+    atomicAdd(a.stats + 1, relax_acc);
+  }
+}
+
 template <int G, bool PRE, bool FX>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap_nodes(NodeLapArgs a) {
   using A = typename std::conditional<FX, ArithFx, ArithF64>::type;
@@ -283,6 +388,15 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap_nodes(NodeLapArg
   long long* s_prefix = reinterpret_cast<long long*>(smem_raw);
   for (int i = threadIdx.x; i <= a.nnodes; i += blockDim.x) s_prefix[i] = a.prefix[i];
   __syncthreads();
+  if constexpr (PRE && FX) {
+    if (a.prefetch) {
+      const size_t pre = (((size_t)(a.nnodes + 1) * sizeof(long long)) + 255) & ~size_t(255);
+      k_lap_nodes_prefetching<G>(a, s_prefix,
+                                 smem_raw + pre + (size_t)(threadIdx.x >> 5) * warp_smem_bytes_async(a.max_m, G),
+                                 threadIdx.x & 31);
+      return;
+    }
+  }
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int grp = lane / G, gl = lane & (G - 1);
@@ -372,14 +486,17 @@ cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s) {
   const int wpb = a.warps_per_block ? a.warps_per_block : kMaxWarpsPerBlock;
   if (G < a.max_m || (wpb != 4 && wpb != 8)) return cudaErrorInvalidValue;
   const size_t pre = (((size_t)(a.nnodes + 1) * sizeof(long long)) + 255) & ~size_t(255);
-  const size_t smem = pre + warp_smem_bytes(a.max_m, G) * wpb;
+  NodeLapArgs b = a;
+  b.prefetch = (a.pre && a.dual_mode == 1) ? 1 : 0;
+  const size_t per_warp = b.prefetch ? warp_smem_bytes_async(a.max_m, G) : warp_smem_bytes(a.max_m, G);
+  const size_t smem = pre + per_warp * wpb;
   cudaError_t e;
   std::unique_lock<std::mutex> lock(g_cfg_mu);
   LapDevCfg* cfg = nullptr;
   if ((e = current_cfg(&cfg)) != cudaSuccess) return e;
   bool* attr_set = cfg->attr_nodes;
   const size_t cap_smem = (((size_t)(kMaxWaveNodes + 1) * sizeof(long long)) + 255) / 256 * 256 +
-                          warp_smem_bytes(32, 32) * kMaxWarpsPerBlock;
+                          warp_smem_bytes_async(32, 32) * kMaxWarpsPerBlock;
   int& occ = cfg->occ_nodes[a.max_m][gidx(G)][wpb == 4 ? 0 : 1];
   // occupancy of the slowest of the four forms, computed once per size (the
   // prefix table's share of shared memory varies with the node count; a grid
@@ -387,14 +504,17 @@ cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s) {
   if (!occ) {
     int lo = 1 << 20;
     for (int k = 0; k < 4; ++k) {
-      const NodeLapKernel kern = node_lap_kernel(G, (k & 1) != 0, (k & 2) != 0);
+      const bool kpre = (k & 1) != 0, kfx = (k & 2) != 0;
+      const NodeLapKernel kern = node_lap_kernel(G, kpre, kfx);
       if (!attr_set[gidx(G)]) {
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap_smem)) !=
             cudaSuccess)
           return e;
       }
       int o = 0;
-      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, wpb * 32, smem)) != cudaSuccess) return e;
+      const size_t ksmem =
+          pre + (kpre && kfx ? warp_smem_bytes_async(a.max_m, G) : warp_smem_bytes(a.max_m, G)) * wpb;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, wpb * 32, ksmem)) != cudaSuccess) return e;
       lo = o < lo ? o : lo;
     }
     attr_set[gidx(G)] = true;
@@ -406,7 +526,7 @@ cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s) {
   const long long need = (a.total + per_block - 1) / per_block;
   const int grid = (int)(need < cap ? need : cap);
   const NodeLapKernel kern = node_lap_kernel(G, a.pre, a.dual_mode == 1);
-  kern<<<grid, wpb * 32, smem, s>>>(a);
+  kern<<<grid, wpb * 32, smem, s>>>(b);
   return cudaGetLastError();
 }
 

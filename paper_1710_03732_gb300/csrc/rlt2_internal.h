@@ -99,7 +99,10 @@ struct NodeLapArgs {
   unsigned long long* head;
   unsigned long long* stats;  // device [2]: augmentations, relaxations (nullable)
   int group, warps_per_block;
-  bool pre;  // no node of the stage writes reduced costs (the tile may be reduced in place)
+  bool pre;  // no node of the stage writes reduced costs (the tile may be reduced in place);
+             // such stages (the Z stages) have no Badd either
+  int prefetch;  // set by launch_lap_nodes: fixed-point pre stages copy each warp's next
+                 // queue item into shared memory by cp.async while the current one is solved
 };
 cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s);
 
@@ -182,6 +185,15 @@ struct IterView {
   int *xperm, *ubperm, *trips;
   DevScalars* sc;
 };
+
+// Up to `iters` iterations of several ascents (one view each, nn <= 1024) in
+// lockstep, every stage one launch over all of them (the batched node kernels
+// of rlt2_bound_nodes); stops early once every view's ascent has stopped
+// (checked between chunks of 8, 16, ... iterations).  *ran: iterations
+// enqueued.  Synchronises s.  Not for the half-Z scheme, the learned start or
+// Type 4 draws; the views' augmentation counters are not updated.
+cudaError_t iterate_views(const IterView* views, int nn, const rlt2_params& prm, int iters, cudaStream_t s,
+                          int* ran);
 
 // Step A0 (setup kernels) and one iteration (seven to nine kernels) on a view.
 cudaError_t enqueue_setup(const IterView& v, int n_full, const double* dF, const double* dD, const double* dB,

@@ -34,7 +34,7 @@ class rlt2_bnb_options(ctypes.Structure):
     _fields_ = [("order_rule", ctypes.c_int), ("iters_root", ctypes.c_int), ("iters_node", ctypes.c_int),
                 ("warm_depth", ctypes.c_int), ("max_states", ctypes.c_int), ("max_nodes", ctypes.c_longlong),
                 ("time_limit_s", ctypes.c_double), ("ub0", ctypes.c_double), ("abs_tol", ctypes.c_double),
-                ("max_state_bytes", ctypes.c_double)]
+                ("max_state_bytes", ctypes.c_double), ("batch_children", ctypes.c_int)]
 
 
 class Rlt2Error(RuntimeError):
@@ -56,7 +56,8 @@ EXPORTS = ["rlt2_params_default", "rlt2_create", "rlt2_iterate", "rlt2_iterate_a
            "rlt2_mlp_grad", "rlt2_mlp_fit", "rlt2_mlp_set_gate", "rlt2_mlp_predict", "rlt2_set_mlp",
            "rlt2_export_xstate", "rlt2_import_xstate", "rlt2_set_sa", "rlt2_create_child", "rlt2_bnb_options_default",
            "rlt2_bnb_solve", "rlt2_mlp_check_wait_timeout", "rlt2_pipeline_check_wait_timeout",
-           "rlt2_debug_bounds_violations", "rlt2_probe_rates", "rlt2_fp64_add_emulated", "rlt2_strerror",
+           "rlt2_debug_bounds_violations", "rlt2_probe_rates", "rlt2_fp64_add_emulated", "rlt2_node_tuning", "rlt2_iterate_many",
+           "rlt2_strerror",
            "rlt2_last_error"]
 
 
@@ -113,6 +114,8 @@ def lib():
     L.rlt2_mlp_check_wait_timeout.argtypes = [_vp]
     L.rlt2_pipeline_check_wait_timeout.argtypes = [_vp]
     L.rlt2_probe_rates.argtypes = [_dp, _dp, _vp]
+    L.rlt2_node_tuning.argtypes = [ctypes.c_int, _ip, _ip, _ip, _dp, _ip]
+    L.rlt2_iterate_many.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, _ip]
     L.rlt2_fp64_add_emulated.argtypes = [ctypes.c_longlong, _vp, _vp, _vp, _vp, _vp]
     L.rlt2_set_mlp.argtypes = [_vp, _vp]
     L.rlt2_strerror.argtypes = [ctypes.c_int]
@@ -350,6 +353,30 @@ def rlt2_fp64_add_emulated(a, b, total, diff, stream=None):
     """a + b and a - b by the integer-pipe binary64 addition (CUDA float64 tensors)."""
     _check(lib().rlt2_fp64_add_emulated(int(a.numel()), _ptr(a), _ptr(b), _ptr(total), _ptr(diff), _stream(stream)),
            "rlt2_fp64_add_emulated")
+
+
+def rlt2_iterate_many(ctxs, iters: int) -> np.ndarray:
+    """Iterates several contexts (Context objects or handles) in lockstep
+    batched launches; returns the iterations each ran."""
+    handles = [c.ctx if isinstance(c, Context) else c for c in ctxs]
+    arr = (_vp * len(handles))(*handles)
+    done = np.zeros(len(handles), dtype=np.int32)
+    _check(lib().rlt2_iterate_many(arr, len(handles), iters, done.ctypes.data_as(_ip)), "rlt2_iterate_many")
+    return done
+
+
+def rlt2_node_tuning() -> list:
+    """The batched nodes' per-size Z-stage launch shapes tuned so far:
+    [{"m", "lanes_per_lap", "warps_per_block", "ms"}, ...] sorted by size."""
+    cap = 64
+    m, g, w = (np.zeros(cap, dtype=np.int32) for _ in range(3))
+    ms = np.zeros(cap)
+    cnt = ctypes.c_int()
+    _check(lib().rlt2_node_tuning(cap, m.ctypes.data_as(_ip), g.ctypes.data_as(_ip), w.ctypes.data_as(_ip),
+                                  _host_d(ms), ctypes.byref(cnt)), "rlt2_node_tuning")
+    k = min(cnt.value, cap)
+    return [{"m": int(m[i]), "lanes_per_lap": int(g[i]), "warps_per_block": int(w[i]), "ms": float(ms[i])}
+            for i in range(k)]
 
 
 def rlt2_destroy(ctx: int):

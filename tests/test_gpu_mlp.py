@@ -149,3 +149,32 @@ def test_inference_wait_timeout_is_detected(R):
     out, _, _ = O.mlp_forward(f, *net, bf16_acts=True)
     ref = prev[3] + (np.float32(out.astype(np.float32)) * np.float32(s)).astype(np.float64)
     assert np.allclose(u0[3], ref, rtol=2e-3, atol=2e-3 * abs(s))
+
+
+def test_trained_network_against_both_starts_on_held_out_grid(R):
+    """The shipped network (weights/warmstart_h256.npz, trained on n = 20..25
+    runs) on a held-out n = 22 grid (seed 99, never trained on), 12 iterations:
+    bounds identical for the cold, previous-dual and learned starts (the exact
+    Hungarian finishes every solve); the learned start needs fewer Z augmenting
+    searches than the cold Hungarian but more than the previous-dual start (the
+    method without the network): the network is a net loss against it."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1710_03732_gb300",
+                        "weights", "warmstart_h256.npz")
+    mlp = R.Mlp(256)
+    mlp.load(path)
+    inst = I.grid_instance("heldout_n22_2x11", 2, 11, 9, 0.5, 99, 0)
+    res = {}
+    for warm in (0, 1, 2):
+        with R.Context(inst.F, inst.D, inst.B, prm=R.params(feas_tol=0.0, warm=warm)) as ctx:
+            if warm == 2:
+                ctx.set_mlp(mlp)
+            lbs, done = ctx.iterate(12)
+            assert done == 12
+            res[warm] = (lbs, int(ctx.stats()[1]))
+    mlp.close()
+    assert np.max(np.abs(res[2][0] - res[0][0]) / np.abs(res[0][0])) <= 1e-9
+    assert np.array_equal(res[1][0], res[0][0])
+    cold, prev, learned = res[0][1], res[1][1], res[2][1]
+    assert learned < cold
+    assert learned > prev

@@ -107,8 +107,86 @@ def test_config4_batched_nodes(R):
     lb, hist, its, stats = R.rlt2_bound_nodes(inst.F, inst.D, parts, iters, B=inst.B, prm=prm)
     assert stats["waves"] == 1 and (its == iters).all()
     assert stats["group"] in (16, 32) and stats["wpb"] in (4, 8)
+    # every Z-LAP size present has its own tuned shape (lanes >= size)
+    table = {e["m"]: e for e in R.rlt2_node_tuning()}
+    for mz in {int((parts[k] < 0).sum()) - 2 for k in range(len(parts))}:
+        assert mz in table and table[mz]["lanes_per_lap"] >= mz and table[mz]["warps_per_block"] in (4, 8)
     assert np.all(np.diff(hist, axis=1) >= -1e-9 * np.abs(hist[:, :-1]))
     for k in (0, 17, 63):
         with R.Context(inst.F, inst.D, inst.B, partial=parts[k], prm=prm) as ctx:
             ref, _ = ctx.iterate(iters)
         assert np.array_equal(hist[k], ref)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_iterate_many_equals_single_contexts(R, mode):
+    """rlt2_iterate_many runs several contexts (different residual sizes, one
+    already advanced, another a child derived from a parent) in lockstep
+    batched launches; each ends exactly where rlt2_iterate alone takes it:
+    bounds, multiplier-adjusted costs and duals bit for bit."""
+    inst = I.random_instance(12, 4, with_b=True)
+    parts = _nodes(12, [1, 2, 3, 5, 7], 3)
+    prm = R.params(dual_mode=mode, feas_tol=0.0, warm=1)
+
+    def make():
+        cs = [R.Context(inst.F, inst.D, inst.B, partial=p, prm=prm) for p in parts]
+        cs[0].iterate(3)
+        root = R.Context(inst.F, inst.D, inst.B, prm=prm)
+        root.iterate(4)
+        cs.append(root.child(facility=2, location=5))
+        root.close()
+        return cs
+
+    many = make()
+    done = R.rlt2_iterate_many(many, 9)
+    assert (done == 9).all()
+    single = make()
+    for c in single:
+        _, d = c.iterate(9)
+        assert d == 9
+    for a, b in zip(many, single):
+        assert a.bound()[:3] == b.bound()[:3]
+        Da, Ca = a.export_state()
+        Db, Cb = b.export_state()
+        assert np.array_equal(Da, Db) and np.array_equal(Ca, Cb)
+        for k in ("xi", "psi", "gamma", "alpha"):
+            assert np.array_equal(a.duals()[k], b.duals()[k]), k
+        # and the next iterations continue identically on the single path
+        ha, _ = a.iterate(2)
+        hb, _ = b.iterate(2)
+        assert np.array_equal(ha, hb)
+    for c in many + single:
+        c.close()
+
+
+def test_iterate_many_stops_each_context_on_its_own(R):
+    """Contexts with a known upper bound stop on the min-gap rule at their own
+    iteration; the batch reports each one's count, equal to rlt2_iterate's, and
+    ends once all have stopped."""
+    inst = I.config(1)
+    opt, _ = O.qap_brute(inst.F, inst.D, inst.B)
+    parts = _nodes(8, [0, 1, 2, 3], 11)
+    prm = R.params(feas_tol=0.0, warm=1, ub=float(opt) * 1.02, min_gap=0.03)
+    many = [R.Context(inst.F, inst.D, inst.B, partial=p, prm=prm) for p in parts]
+    done = R.rlt2_iterate_many(many, 400)
+    for k, p in enumerate(parts):
+        with R.Context(inst.F, inst.D, inst.B, partial=p, prm=prm) as c:
+            _, d = c.iterate(400)
+            ref_best = c.bound()[1]
+        assert done[k] == d and many[k].bound()[1] == ref_best
+    assert done.max() < 400 and len(set(done.tolist())) > 1
+    for c in many:
+        c.close()
+
+
+def test_iterate_many_rejects_mixed_parameters(R):
+    inst = I.config(1)
+    a = R.Context(inst.F, inst.D, inst.B, prm=R.params(warm=1))
+    b = R.Context(inst.F, inst.D, inst.B, prm=R.params(warm=0))
+    with pytest.raises(R.Rlt2Error) as e:
+        R.rlt2_iterate_many([a, b], 3)
+    assert e.value.status == R.RLT2_EINVAL
+    with pytest.raises(R.Rlt2Error):
+        R.rlt2_iterate_many([a, a], 3)
+    a.close()
+    b.close()
