@@ -245,12 +245,13 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
   T v = T(0);
   int naug = 0, nrelax = 0;
 
-  // column reduction with the argmin row (fixed point: the start duals are
-  // broadcast from shared memory, one load instead of two shuffles per row)
+  // column reduction with the argmin row (fixed point: the row duals are
+  // broadcast from shared memory, one load instead of two shuffles per row;
+  // uvs holds the group's row duals until the canonical pass)
   unsigned long long bestk = ~0ull;
   int arg = -1;
   if constexpr (A::kExact) {
-    if (warm) uvs[gl] = u;
+    uvs[gl] = u;
     __syncwarp();
   }
   for (int r = 0; r < M; ++r) {
@@ -304,7 +305,9 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
       ++naug;
       nrelax += m;
     }
-    const T ui = __shfl_sync(kFull, u, gb + i);
+    T ui;
+    if constexpr (A::kExact) ui = uvs[i];
+    else ui = __shfl_sync(kFull, u, gb + i);
     T d = (act && cv) ? A::sub(A::sub(cs[i * ld + gl], ui), v) : T(0);
     unsigned long long dk = A::key(d);  // cached key of d (rounded form only)
     int pred = i;
@@ -312,7 +315,7 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
     const unsigned freecols = group_bits<G>(__ballot_sync(kFull, cv && c2r < 0), gb);
     bool searching = act;
     int sink = 0;
-    int step = 0;  // columns scanned so far in this search (one per step)
+    int step = 0;  // relaxing steps of this search (one column scanned per step)
     T dlast = T(0);
     while (__any_sync(kFull, searching)) {
       const int c = group_argmin<G>(scanned ? ~0ull : (A::kExact ? A::key(d) : dk), gb);
@@ -326,7 +329,9 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
       const bool relaxing = searching && !found;
       const int r0 = __shfl_sync(kFull, c2r, gb + c);
       const int r = r0 < 0 ? 0 : r0;
-      const T ur = __shfl_sync(kFull, u, gb + r);
+      T ur;
+      if constexpr (A::kExact) ur = uvs[RLT2_IDX(r, m > 0 ? m : 1)];
+      else ur = __shfl_sync(kFull, u, gb + r);
       if (relaxing && !scanned) {
         const T nd = A::add(dm, A::sub(A::sub(cs[RLT2_IDX(r, m) * ld + gl], ur), v));
         if (A::kExact ? nd < d : A::key(nd) < dk) {
@@ -335,9 +340,11 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
           pred = r;
         }
       }
-      if (relaxing) nrelax += m - (++step);  // the columns still unscanned were relaxed
+      if (relaxing) ++step;
       searching = relaxing;
     }
+    // the k-th relaxing step relaxed the m - k columns still unscanned
+    if (act) nrelax += step * m - (step * (step + 1)) / 2;
     if (act && cv && scanned) v = A::add(v, A::sub(d, dlast));
     // augment back to row i (groups walk their own chains in lockstep)
     bool walking = act;
@@ -355,6 +362,10 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
     const int mc = (cv && r2c >= 0) ? r2c : 0;
     const T vm = __shfl_sync(kFull, v, gb + mc);
     if (act && cv && r2c >= 0) u = A::sub(cs[gl * ld + RLT2_IDX(r2c, m)], vm);
+    if constexpr (A::kExact) {
+      uvs[gl] = u;
+      __syncwarp();
+    }
   }
 
   // optimum: pairwise tree over P = next power of two >= m rows (empty rows add
