@@ -18,7 +18,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "librlt2.so")
-SOURCES = ["lap.cu", "ascent.cu", "nodes.cu", "mlp.cu", "noalloc.cu", "bnb.cu", "umma.cu", "fused.cu", "probe.cu"]
+SOURCES = ["lap.cu", "ascent.cu", "nodes.cu", "mlp.cu", "noalloc.cu", "bnb.cu", "umma.cu", "umma_gemm.cu", "fused.cu",
+           "probe.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

@@ -10,10 +10,12 @@
 //
 // Network: 34 -> H -> H -> 1, ReLU, BF16 weights and activations, FP32
 // accumulation.  Inference of the H = 256 network runs on the 5th-generation
-// tensor cores (tcgen05.mma with TMEM accumulators, umma.cu); training and
-// other widths use a hand-written mma.sync (m16n8k16, BF16 -> FP32) GEMM with
-// ldmatrix fragment loads and a cp.async double-buffered shared-memory
-// pipeline, whose transposed-operand variants compute the backward pass.
+// tensor cores in one fused kernel (tcgen05.mma with TMEM accumulators,
+// umma.cu); the training GEMMs (forward layers, and the backward products
+// with transposed operands) of widths up to 256 run on a tcgen05 GEMM
+// (umma_gemm.cu); wider networks use a hand-written mma.sync (m16n8k16,
+// BF16 -> FP32) GEMM with ldmatrix fragment loads and a cp.async
+// double-buffered shared-memory pipeline.
 // Features are built without FP64 arithmetic (FP64 -> FP32 by truncating the
 // significand on the integer pipe) because FP64 is GB300's scarce resource.
 #include <cuda_bf16.h>
@@ -25,6 +27,7 @@
 #include <vector>
 
 #include "rlt2_internal.h"
+#include "rlt2_mlp_gemm.h"
 
 namespace rlt2 {
 namespace {
@@ -428,8 +431,35 @@ void param_ptrs(rlt2_mlp* m) {
   m->b3 = m->w3 + H;
 }
 
+// ta: A stored [K x M]; tb: B stored [N x K].  Widths up to 256 run on the
+// tcgen05 GEMM (umma_gemm.cu; err: its timeout flag), others on the mma.sync one.
 cudaError_t gemm(bool ta, bool tb, int epi, int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb,
-                 float* C, int ldc, bf16* Cb, const float* bias, const bf16* mask, int splits, cudaStream_t s) {
+                 float* C, int ldc, bf16* Cb, const float* bias, const bf16* mask, int splits, int* err,
+                 cudaStream_t s) {
+  const bool tc_case = (!ta && !tb && epi == 1) || (ta && !tb && epi == 0) || (!ta && tb && epi == 2);
+  if (err && tc_case && umma_gemm_supported(M, N, K)) {
+    UmmaGemmArgs u{};
+    u.M = M;
+    u.N = N;
+    u.K = K;
+    u.A = A;
+    u.lda = lda;
+    u.a_kmajor = !ta;
+    u.B = B;
+    u.ldb = ldb;
+    u.b_kmajor = tb;
+    u.epi = epi;
+    u.C = C;
+    u.ldc = ldc;
+    u.Cb = Cb;
+    u.bias = bias;
+    u.mask = mask;
+    u.err = err;
+    // a K split over the batch (weight gradients): chunks of 512 rows per CTA,
+    // so that the few 128-row blocks of the output still fill the GPU
+    const int tsplits = splits > 1 ? std::max(splits, std::min(64, K / 512)) : 1;
+    return umma_gemm(u, tsplits, s);
+  }
   const int kps = ((K / splits + BK - 1) / BK) * BK;
   dim3 grid(N / BN, M / BM, (K + kps - 1) / kps);
 #define RLT2_GEMM_CASE(TA_, TB_, EPI_)                                                                       \
@@ -450,9 +480,9 @@ cudaError_t forward(rlt2_mlp* m, const bf16* X, long long rows, float* out, cuda
   const int H = m->H;
   cudaError_t e;
   if ((e = gemm(false, false, 1, (int)rows, H, kInPad, X, kInPad, m->W1b, H, nullptr, H, m->H1, m->b1, nullptr, 1,
-                s)) != cudaSuccess)
+                m->err, s)) != cudaSuccess)
     return e;
-  if ((e = gemm(false, false, 1, (int)rows, H, H, m->H1, H, m->W2b, H, nullptr, H, m->H2, m->b2, nullptr, 1, s)) !=
+  if ((e = gemm(false, false, 1, (int)rows, H, H, m->H1, H, m->W2b, H, nullptr, H, m->H2, m->b2, nullptr, 1, m->err, s)) !=
       cudaSuccess)
     return e;
   k_out<<<(int)std::min<long long>(4096, (rows + 7) / 8), 256, 0, s>>>(rows, H, m->H2, m->w3, m->b3, out);
@@ -474,19 +504,21 @@ cudaError_t backward(rlt2_mlp* m, const bf16* X, const float* T, long long rows,
   k_loss<<<256, 256, 0, s>>>(rows, nvalid, m->out, T, m->dout, m->loss);
   k_dh2<<<4096, 256, 0, s>>>(rows, H, m->H2, m->dout, m->w3, m->dH2);
   const int gsplit = (int)std::max<long long>(1, std::min<long long>(256, rows / 1024));
-  k_colsum<<<gsplit, H, 0, s>>>(rows, H, m->H2, m->dout, gw3);
+  // column sums: 32 rows per block (latency-bound with fewer blocks), atomic adds
+  const int csplit = (int)std::max<long long>(1, std::min<long long>(4096, rows / 32));
+  k_colsum<<<csplit, H, 0, s>>>(rows, H, m->H2, m->dout, gw3);
   k_sum<<<64, 256, 0, s>>>(rows, m->dout, gb3);
-  if ((e = gemm(true, false, 0, H, H, (int)rows, m->H1, H, m->dH2, H, gW2, H, nullptr, nullptr, nullptr, gsplit, s)) !=
+  if ((e = gemm(true, false, 0, H, H, (int)rows, m->H1, H, m->dH2, H, gW2, H, nullptr, nullptr, nullptr, gsplit, m->err, s)) !=
       cudaSuccess)
     return e;
-  k_colsum<<<gsplit, H, 0, s>>>(rows, H, m->dH2, nullptr, gb2);
-  if ((e = gemm(false, true, 2, (int)rows, H, H, m->dH2, H, m->W2b, H, nullptr, H, m->dH1, nullptr, m->H1, 1, s)) !=
+  k_colsum<<<csplit, H, 0, s>>>(rows, H, m->dH2, nullptr, gb2);
+  if ((e = gemm(false, true, 2, (int)rows, H, H, m->dH2, H, m->W2b, H, nullptr, H, m->dH1, nullptr, m->H1, 1, m->err, s)) !=
       cudaSuccess)
     return e;
   if ((e = gemm(true, false, 0, kInPad, H, (int)rows, X, kInPad, m->dH1, H, gW1, H, nullptr, nullptr, nullptr, gsplit,
-                s)) != cudaSuccess)
+                m->err, s)) != cudaSuccess)
     return e;
-  k_colsum<<<gsplit, H, 0, s>>>(rows, H, m->dH1, nullptr, gb1);
+  k_colsum<<<csplit, H, 0, s>>>(rows, H, m->dH1, nullptr, gb1);
   return cudaGetLastError();
 }
 
@@ -705,6 +737,18 @@ extern "C" rlt2_status rlt2_mlp_clear_samples(rlt2_mlp* m) {
   return RLT2_OK;
 }
 
+// ETIMEOUT (and the flag cleared) if a tensor-core wait of the network's kernels
+// timed out since the flag was last cleared; the stream is synchronised.
+static rlt2_status tc_wait_status(rlt2_mlp* m, const char* where) {
+  int err = 0;
+  CKM(cudaStreamSynchronize(m->stream));
+  CKM(cudaMemcpy(&err, m->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!err) return RLT2_OK;
+  CKM(cudaMemset(m->err, 0, sizeof(int)));
+  set_error(std::string(where) + ": a tensor-core wait timed out");
+  return RLT2_ETIMEOUT;
+}
+
 // loss and gradients on the first `rows` samples (<= one chunk), no update
 extern "C" rlt2_status rlt2_mlp_grad(rlt2_mlp* m, long long rows, double* loss, float* gW1, float* gb1, float* gW2,
                                      float* gb2, float* gw3, float* gb3) {
@@ -726,6 +770,7 @@ extern "C" rlt2_status rlt2_mlp_grad(rlt2_mlp* m, long long rows, double* loss, 
   CKM(cudaMemcpyAsync(g.data(), m->grad, sizeof(float) * m->nparams, cudaMemcpyDeviceToHost, s));
   CKM(cudaMemcpyAsync(&l, m->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
   CKM(cudaStreamSynchronize(s));
+  if (rlt2_status ts = tc_wait_status(m, "rlt2_mlp_grad"); ts != RLT2_OK) return ts;
   if (loss) *loss = l;
   const float* p = g.data();
   if (gW1) memcpy(gW1, p, sizeof(float) * kIn * H);
@@ -777,6 +822,7 @@ extern "C" rlt2_status rlt2_mlp_fit(rlt2_mlp* m, int steps, int batch_rows, doub
     if (loss_hist) CKM(cudaMemcpyAsync(&losses[st], m->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
   }
   CKM(cudaStreamSynchronize(s));
+  if (rlt2_status ts = tc_wait_status(m, "rlt2_mlp_fit"); ts != RLT2_OK) return ts;
   if (loss_hist)
     for (int st = 0; st < steps; ++st) loss_hist[st] = losses[st];
   return RLT2_OK;
