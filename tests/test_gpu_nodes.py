@@ -190,3 +190,25 @@ def test_iterate_many_rejects_mixed_parameters(R):
         R.rlt2_iterate_many([a, a], 3)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("variant,two_phase", [(1, 0), (0, 1), (1, 1)])
+def test_iterate_many_runs_the_variants(R, variant, two_phase):
+    """The F variant and the two-phase Z solve through the batched engine:
+    raw duals, each context bit for bit where rlt2_iterate takes it."""
+    inst = I.random_instance(10, 23, with_b=True, asymmetric=True)
+    parts = _nodes(10, [0, 1, 2, 4], 5)
+    prm = R.params(dual_mode=0, feas_tol=0.0, warm=1, variant=variant, two_phase=two_phase)
+    many = [R.Context(inst.F, inst.D, inst.B, partial=p, prm=prm) for p in parts]
+    done = R.rlt2_iterate_many(many, 7)
+    assert (done == 7).all()
+    for k, p in enumerate(parts):
+        with R.Context(inst.F, inst.D, inst.B, partial=p, prm=prm) as c:
+            ref, _ = c.iterate(7)
+            Dr, Cr = c.export_state()
+            ref_best = c.bound()[1]
+        D, C = many[k].export_state()
+        assert np.array_equal(D, Dr) and np.array_equal(C, Cr)
+        assert many[k].bound()[1] == ref_best
+    for c in many:
+        c.close()

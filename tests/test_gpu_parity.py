@@ -167,6 +167,34 @@ def test_lap_fixed_point_scales(R, kind):
         assert np.allclose(v[b], o.v, rtol=0, atol=1e-9 * scale + 1e-320)
 
 
+def test_lap_fixed_point_wide_range_small_optimum(R):
+    """Tiles with a 1e12 dynamic range whose optimum is near 0: a permutation of
+    entries of size ~1 in a tile of entries up to 1e12.  The fixed-point grid
+    of such a tile is 2^L with L = E - 48 (2^E the first power of two above its
+    largest entry, here 2^-8), so the exact optimum of the rounded tile differs
+    from the FP64 optimum by less than m * 2^L; against the optimum itself that
+    is a relative error of up to ~1e-3 (recorded here, not hidden behind the
+    tile-scale tolerance).  Duals stay feasible for the given tile."""
+    rng = np.random.default_rng(77)
+    batch, m = 64, 18
+    c = rng.uniform(1e11, 1e12, size=(batch, m, m))
+    for b in range(batch):
+        perm = rng.permutation(m)
+        c[b, np.arange(m), perm] = rng.uniform(0.0, 2.0, m)
+    val, u, v = _fixed_point_solve(R, c)
+    worst = 0.0
+    for b in range(batch):
+        o = O.lap(c[b], canonical=True)
+        E = int(np.floor(np.log2(np.abs(c[b]).max()))) + 1
+        grid = 2.0 ** (E - 48)
+        assert abs(val[b] - o.value) <= m * grid
+        worst = max(worst, abs(val[b] - o.value) / abs(o.value))
+        assert (c[b] - u[b][:, None] - v[b][None, :]).min() >= -1e-14 * np.abs(c[b]).max() * m
+    # the recorded figure: relative error against the optimum itself
+    assert worst < 5e-3
+    print(f"fixed point, 1e12 dynamic range, optimum ~{np.mean(val):.2f}: worst relative error {worst:.2e}")
+
+
 def test_lap_batched_warm_start(R):
     rng = np.random.default_rng(5)
     batch, m = 500, 18
