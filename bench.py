@@ -309,6 +309,14 @@ def run_profile_case(args):
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": "16 nodes of config 4", "iterations": int(its.sum()), "stats": st}))
         return 0
+    if args.profile == "train":
+        mlp, rows = training_samples(R, torch)
+        hist = mlp.fit(args.warmup + args.steps, batch_rows=16384)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "training steps of the H = 256 network, 16,384 rows each",
+                          "samples": rows, "steps": args.warmup + args.steps, "loss_last": float(hist[-1])}))
+        mlp.close()
+        return 0
     inst = I.config(CFG)
     mlp = None
     warm = 1
@@ -323,6 +331,51 @@ def run_profile_case(args):
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": WORKLOAD, "warm": warm, "iterations": got, "lb_last": float(hist[got - 1])}))
     return 0
+
+
+def training_samples(R, torch, ntiles: int = 24000):
+    """An H = 256 network with (tile, canonical dual) samples of the n = 20
+    workload: 24,000 tiles of iteration 3 with the duals of iteration 2 as the
+    previous ones (432,000 rows)."""
+    inst = I.config(CFG)
+    mlp = R.Mlp(256, seed=5)
+    with R.Context(inst.F, inst.D, inst.B, prm=R.params(feas_tol=0.0)) as ctx:
+        T, m = ctx.T, ctx.n - 2
+        ctx.iterate(2)
+        prev = torch.empty(T * m, dtype=torch.float64, device="cuda")
+        R.rlt2_duals(ctx.ctx, xi=prev, on_device=1)
+        ctx.iterate(1)
+        D = torch.empty(ctx.E, dtype=torch.float64, device="cuda")
+        xi = torch.empty(T * m, dtype=torch.float64, device="cuda")
+        R.rlt2_export_state(ctx.ctx, Dhat=D, on_device=1)
+        R.rlt2_duals(ctx.ctx, xi=xi, on_device=1)
+        mlp.add_samples(D.view(T, m, m)[:ntiles].contiguous(), xi.view(T, m)[:ntiles].contiguous(),
+                        prev.view(T, m)[:ntiles].contiguous())
+        del D, xi, prev
+    return mlp, ntiles * 18
+
+
+def training_rate(R, torch):
+    """AdamW training steps of the H = 256 network (16,384 rows each; forward,
+    backward and update, the GEMMs on tcgen05), timed with CUDA events."""
+    mlp, rows = training_samples(R, torch)
+    H, B = 256, 16384
+    mlp.fit(5, batch_rows=B)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = 100
+    e0.record()
+    hist = mlp.fit(steps, batch_rows=B)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    gemm_flop = 2.0 * B * (64 * H + H * H) + 2.0 * B * (H * H + H * H + 64 * H)
+    mlp.close()
+    return {"workload": "AdamW steps of the 34-256-256-1 network, 16,384 rows each, samples from the n=20 workload",
+            "samples": rows, "ms_per_step": ms, "rows_per_s": B / (ms * 1e-3),
+            "gemm_tflops_whole_step": gemm_flop / (ms * 1e-3) / 1e12, "loss_last": float(hist[-1]),
+            "note": "the whole step (features gather, five GEMMs, loss, column sums, AdamW) timed; the "
+                    "per-GEMM rates are in the launch-list profile"}
 
 
 def variant_runs(R, torch, iters: int = 300):
@@ -474,6 +527,7 @@ def extra_workloads(R, torch):
     out["variants_n20"] = variant_runs(R, torch)
     # branch and bound to optimality (Section 4)
     out["branch_and_bound"] = bnb_runs(R, torch)
+    out["mlp_training"] = training_rate(R, torch)
     # learned start on the headline workload: augmenting searches, identical bounds
     if mlp is not None:
         inst = I.config(CFG)
@@ -549,7 +603,7 @@ def main():
     ap.add_argument("--bnb-hard", action="store_true",
                     help="only solve a Nugent-like n=20 QAP (4x5 grid, F 0..9 at density 0.5, seed 12) to proven "
                          "optimality with rlt2_bnb_solve and print its statistics (about two minutes)")
-    ap.add_argument("--profile", nargs="?", const="n20", choices=["n20", "nodes", "learned"],
+    ap.add_argument("--profile", nargs="?", const="n20", choices=["n20", "nodes", "learned", "train"],
                     help="only run a small case for ncu captures: n20 = warmup+steps iterations of the n=20 "
                          "workload (graph replay, warm start); nodes = 16 nodes of the n=22 grid QAP; "
                          "learned = n=20 with the learned warm start")
