@@ -317,6 +317,24 @@ def run_profile_case(args):
                           "samples": rows, "steps": args.warmup + args.steps, "loss_last": float(hist[-1])}))
         mlp.close()
         return 0
+    if args.profile == "gemm":
+        # the training GEMMs at the largest batch one call takes (2^18 rows):
+        # forward, loss and backward per call, no update
+        mlp, rows = training_samples(R, torch)
+        big = 1 << 18
+        for _ in range(args.warmup):
+            mlp.grad(big)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            mlp.grad(big)
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "gradients of the H = 256 network on 262,144 rows per call",
+                          "samples": rows, "calls": args.warmup + args.steps,
+                          "ms_per_call": e0.elapsed_time(e1) / max(1, args.steps)}))
+        mlp.close()
+        return 0
     inst = I.config(CFG)
     mlp = None
     warm = 1
@@ -603,10 +621,11 @@ def main():
     ap.add_argument("--bnb-hard", action="store_true",
                     help="only solve a Nugent-like n=20 QAP (4x5 grid, F 0..9 at density 0.5, seed 12) to proven "
                          "optimality with rlt2_bnb_solve and print its statistics (about two minutes)")
-    ap.add_argument("--profile", nargs="?", const="n20", choices=["n20", "nodes", "learned", "train"],
+    ap.add_argument("--profile", nargs="?", const="n20", choices=["n20", "nodes", "learned", "train", "gemm"],
                     help="only run a small case for ncu captures: n20 = warmup+steps iterations of the n=20 "
                          "workload (graph replay, warm start); nodes = 16 nodes of the n=22 grid QAP; "
-                         "learned = n=20 with the learned warm start")
+                         "learned = n=20 with the learned warm start; train = AdamW steps of the H=256 "
+                         "network (16,384 rows); gemm = its gradients on 262,144 rows per call")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

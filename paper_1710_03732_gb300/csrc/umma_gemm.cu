@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_umma_gemm(UmmaGemmArgs a) {
   const int kend = min(a.K, kbeg + a.kps);
   const int nk = kend > kbeg ? (kend - kbeg) / kBK : 0;
   const uint32_t id = idesc(NP);
-  uint32_t ph[kMaxSlots] = {0u, 0u, 0u};
+  uint32_t ph = 0u;  // bit sl: the phase of slot sl's barrier to wait for
   bool ok = true;
   int last = -1;  // slot of the last commit
   // the copies of chunk c into its slot (K-major operands directly, the
@@ -236,8 +236,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_umma_gemm(UmmaGemmArgs a) {
     // chunk kt + kSlots - 1 goes into the slot the MMAs of chunk kt - 1 read
     if (kt >= 1 && kt + kSlots - 1 < nk) {
       const int ps = (kt - 1) % kSlots;
-      const bool arrived = mbar_wait(smem_u32(bar + ps), ph[ps]);
-      ph[ps] ^= 1u;
+      const bool arrived = mbar_wait(smem_u32(bar + ps), (ph >> ps) & 1u);
+      ph ^= 1u << ps;
       if (__syncthreads_or(arrived ? 0 : 1)) {
         ok = false;
         break;
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_umma_gemm(UmmaGemmArgs a) {
   // the last commit covers every MMA issued before it (on a timeout: one more
   // bounded wait so that no MMA is in flight when the TMEM is released)
   if (last >= 0) {
-    const bool arrived = mbar_wait(smem_u32(bar + last), ph[last]);
+    const bool arrived = mbar_wait(smem_u32(bar + last), (ph >> last) & 1u);
     if (__syncthreads_or(arrived ? 0 : 1)) ok = false;
   }
   if (!ok) {
@@ -301,6 +301,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_umma_gemm(UmmaGemmArgs a) {
     for (int c0 = colh * half; c0 < (colh + 1) * half; c0 += 32) {
       uint32_t v[32];
       tmem_ld32(tmem + lane_off + (uint32_t)c0, v);
+      if constexpr (EPI == 2) {
+        // the ReLU mask of this lane's row (row rbase + lane) over the chunk's
+        // 32 columns, read as four 16-byte pieces and applied in registers;
+        // pieces past the last column (N is a multiple of 8) or rows past M read
+        // nothing
+        const int row = rbase + lane;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          uint4 w = make_uint4(0u, 0u, 0u, 0u);
+          if (row < a.M && c0 + 8 * q < cend)
+            w = __ldg(reinterpret_cast<const uint4*>(a.mask + (size_t)row * a.ldc + n0 + c0 + 8 * q));
+          const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int h = 0; h < 8; ++h) {
+            const uint32_t bits = (ws[h >> 1] >> ((h & 1) * 16)) & 0xFFFFu;
+            // a BF16 value is > 0 exactly when its bits lie in [0x0001, 0x7F80]
+            // (positive subnormals up to +inf; zeros, negatives and NaNs not)
+            const bool pos = bits - 1u < 0x7F80u;
+            if (!pos) v[8 * q + h] = 0u;
+          }
+        }
+      }
 #pragma unroll
       for (int j = 0; j < 32; ++j) scr[lane * 33 + j] = __uint_as_float(v[j]);
       __syncwarp();
@@ -309,13 +331,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_umma_gemm(UmmaGemmArgs a) {
       if (cl < cend) {
         float bias_c = 0.0f;
         if constexpr (EPI == 1) bias_c = a.bias[c];
-        // the mask of the 32 rows, loaded together (one latency, not 32)
-        bf16 mk[EPI == 2 ? 32 : 1];
-        if constexpr (EPI == 2) {
-#pragma unroll
-          for (int rr = 0; rr < 32; ++rr)
-            mk[rr] = rbase + rr < a.M ? a.mask[(size_t)(rbase + rr) * a.ldc + c] : __float2bfloat16_rn(0.0f);
-        }
 #pragma unroll 8
         for (int rr = 0; rr < 32; ++rr) {
           const int row = rbase + rr;
@@ -328,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_umma_gemm(UmmaGemmArgs a) {
           } else if constexpr (EPI == 1) {
             a.Cb[(size_t)row * a.ldc + c] = __float2bfloat16_rn(fmaxf(x + bias_c, 0.0f));
           } else {
-            a.Cb[(size_t)row * a.ldc + c] = __float2bfloat16_rn(__bfloat162float(mk[rr]) > 0.0f ? x : 0.0f);
+            a.Cb[(size_t)row * a.ldc + c] = __float2bfloat16_rn(x);  // masked above
           }
         }
       }
@@ -361,6 +376,8 @@ cudaError_t umma_gemm(UmmaGemmArgs a, int splits, cudaStream_t s) {
   if (!umma_gemm_supported(a.M, a.N, a.K) || !a.A || !a.B || !a.err || splits < 1) return cudaErrorInvalidValue;
   if (a.a_kmajor ? (a.lda < a.K || a.lda % 8) : (a.lda < a.M || a.lda % 8 || a.M % 8)) return cudaErrorInvalidValue;
   if (a.b_kmajor ? (a.ldb < a.K || a.ldb % 8) : (a.ldb < a.N || a.ldb % 8)) return cudaErrorInvalidValue;
+  // the masked epilogue reads the mask in 16-byte pieces
+  if (a.epi == 2 && (!a.mask || a.ldc % 8 || reinterpret_cast<uintptr_t>(a.mask) % 16)) return cudaErrorInvalidValue;
   GemmKernel kern = nullptr;
   if (a.a_kmajor && !a.b_kmajor && a.epi == 1) kern = k_umma_gemm<true, false, 1>;
   else if (!a.a_kmajor && !a.b_kmajor && a.epi == 0) kern = k_umma_gemm<false, false, 0>;
