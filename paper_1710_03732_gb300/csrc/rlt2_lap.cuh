@@ -250,6 +250,9 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
   // uvs holds the group's row duals until the canonical pass)
   unsigned long long bestk = ~0ull;
   int arg = -1;
+  // exact form: the running minimum starts above every |x| < 2^58, so the first
+  // row always takes it (the same result as testing arg < 0)
+  T vmin = A::kExact ? T(0x7fffffffffffffffll) : T(0);
   if constexpr (A::kExact) {
     uvs[gl] = u;
     __syncwarp();
@@ -271,12 +274,20 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
         c = cs[r * ld + gl];
       }
       const T x = warm ? A::sub(c, ur) : c;  // c - 0 == c exactly
-      if (arg < 0 || (A::kExact ? x < v : A::key(x) < bestk)) {
-        if constexpr (!A::kExact) bestk = A::key(x);
+      if constexpr (A::kExact) {
+        if (x < vmin) {
+          arg = r;
+          vmin = x;
+        }
+      } else if (arg < 0 || A::key(x) < bestk) {
+        bestk = A::key(x);
         arg = r;
         v = x;
       }
     }
+  }
+  if constexpr (A::kExact) {
+    if (cv) v = vmin;
   }
   if constexpr (A::kExact) {
     if (raw) {
@@ -296,8 +307,10 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
   int r2c = cv ? scr[gl] : -1;
   __syncwarp();
 
+  // at G = 32 the warp is one group, so every loop condition below is
+  // warp-uniform and needs no vote
   unsigned freerows = group_bits<G>(__ballot_sync(kFull, cv && r2c < 0), gb);
-  while (__any_sync(kFull, freerows != 0)) {
+  while (G == 32 ? freerows != 0 : __any_sync(kFull, freerows != 0)) {
     const bool act = freerows != 0;  // this group runs a search in this round
     const int i = act ? __ffs(freerows) - 1 : 0;
     if (act) {
@@ -312,22 +325,22 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
     unsigned long long dk = A::key(d);  // cached key of d (rounded form only)
     int pred = i;
     bool scanned = !(act && cv);
-    const unsigned freecols = group_bits<G>(__ballot_sync(kFull, cv && c2r < 0), gb);
     bool searching = act;
     int sink = 0;
-    int step = 0;  // relaxing steps of this search (one column scanned per step)
     T dlast = T(0);
-    while (__any_sync(kFull, searching)) {
+    while (G == 32 ? searching : __any_sync(kFull, searching)) {
       const int c = group_argmin<G>(scanned ? ~0ull : (A::kExact ? A::key(d) : dk), gb);
       const T dm = __shfl_sync(kFull, d, gb + c);
       if (searching && gl == c) scanned = true;
-      const bool found = searching && ((freecols >> c) & 1u);
+      // the matching does not change during a search, so column c is free
+      // exactly when it has no matched row
+      const int r0 = __shfl_sync(kFull, c2r, gb + c);
+      const bool found = searching && r0 < 0;
       if (found) {
         sink = c;
         dlast = dm;
       }
       const bool relaxing = searching && !found;
-      const int r0 = __shfl_sync(kFull, c2r, gb + c);
       const int r = r0 < 0 ? 0 : r0;
       T ur;
       if constexpr (A::kExact) ur = uvs[RLT2_IDX(r, m > 0 ? m : 1)];
@@ -340,16 +353,18 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
           pred = r;
         }
       }
-      if (relaxing) ++step;
       searching = relaxing;
     }
-    // the k-th relaxing step relaxed the m - k columns still unscanned
+    // every step scanned one column, the last one the sink: the relaxing
+    // steps are the scanned columns but one, and the k-th of them relaxed the
+    // m - k columns still unscanned
+    const int step = __popc(group_bits<G>(__ballot_sync(kFull, act && cv && scanned), gb)) - 1;
     if (act) nrelax += step * m - (step * (step + 1)) / 2;
     if (act && cv && scanned) v = A::add(v, A::sub(d, dlast));
     // augment back to row i (groups walk their own chains in lockstep)
     bool walking = act;
     int col = sink;
-    while (__any_sync(kFull, walking)) {
+    while (G == 32 ? walking : __any_sync(kFull, walking)) {
       const int r = __shfl_sync(kFull, pred, gb + col);
       const int nxt = __shfl_sync(kFull, r2c, gb + r);
       if (walking) {
@@ -385,13 +400,12 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
     // canonical duals: shortest paths from row 0 on reduced weights
     // pi(r, sigma(r')) = (c_{r,sigma(r')} - u_r) - v_{sigma(r')} >= 0
     const int s0 = __shfl_sync(kFull, r2c, gb);
-    if constexpr (PRE && A::kExact) {
-      // integer subtractions are cheap: each column's lane walks its column
-      uvs[gl] = u;
-      __syncwarp();
-      if (cv) {
-        for (int r = 0; r < m; ++r) cs[r * ld + gl] = A::sub(A::sub(cs[r * ld + gl], uvs[r]), v);
-      }
+    // exact form: a lane forms only the reduced costs of its own row that the
+    // pass reads (two integer subtractions each, with the column duals
+    // broadcast from shared memory) instead of the whole reduced tile first
+    constexpr bool kRed = PRE && !A::kExact;  // the reduced tile is formed first
+    if constexpr (A::kExact) {
+      uvs[32 + gl] = v;
       __syncwarp();
     } else if constexpr (PRE) {
       // an FP64 instruction costs the same with few lanes active, so the group's
@@ -414,10 +428,12 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
       }
       __syncwarp();
     }
-    const T vs0 = __shfl_sync(kFull, v, gb + (s0 < 0 ? 0 : s0));
+    T vs0 = T(0);
+    if constexpr (A::kExact) vs0 = uvs[32 + RLT2_IDX(s0 < 0 ? 0 : s0, m > 0 ? m : 1)];
+    else vs0 = __shfl_sync(kFull, v, gb + (s0 < 0 ? 0 : s0));
     T dist = T(0);
     if (cv && gl != 0) {
-      if constexpr (PRE) dist = cs[gl * ld + RLT2_IDX(s0, m)];
+      if constexpr (kRed) dist = cs[gl * ld + RLT2_IDX(s0, m)];
       else dist = A::sub(A::sub(cs[gl * ld + RLT2_IDX(s0, m)], u), vs0);
     }
     bool done = !cv || gl == 0;
@@ -429,10 +445,11 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
       if (stepping && gl == rs) done = true;
       const int s = __shfl_sync(kFull, r2c, gb + rs);
       T vs = T(0);
-      if constexpr (!PRE) vs = __shfl_sync(kFull, v, gb + (s < 0 ? 0 : s));
+      if constexpr (A::kExact) vs = uvs[32 + RLT2_IDX(s < 0 ? 0 : s, m > 0 ? m : 1)];
+      else if constexpr (!kRed) vs = __shfl_sync(kFull, v, gb + (s < 0 ? 0 : s));
       if (stepping && !done) {
         T w;
-        if constexpr (PRE) w = cs[gl * ld + RLT2_IDX(s, m)];
+        if constexpr (kRed) w = cs[gl * ld + RLT2_IDX(s, m)];
         else w = A::sub(A::sub(cs[gl * ld + RLT2_IDX(s, m)], u), vs);
         const T nd = A::add(dr, w);
         if (A::kExact ? nd < dist : A::key(nd) < dk) {
@@ -449,6 +466,7 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
     const T vcan = __shfl_sync(kFull, wrow, gb + rr);
     u = ucan;
     v = cv ? vcan : T(0);
+    if constexpr (A::kExact) __syncwarp();  // the reads of uvs are done before a caller reuses it
   }
   R.u = u;
   R.v = v;
