@@ -52,7 +52,8 @@
 //             relax only on strict '<'; stop at the first free column.
 //   duals     v_c = v_c + (d_c - d_sink) on scanned columns, augment, then
 //             u_r = c_{r,sigma(r)} - v_{sigma(r)} for every matched row
-//   value     sum_r c_{r,sigma(r)} as a pairwise tree (lane i += lane i+h, h = P/2..1)
+//   value     sum_r c_{r,sigma(r)} as a pairwise tree (lane i += lane i+h, h = P/2..1);
+//             exact in fixed point, where one LAP per warp sums by warp reductions
 //   canonical (dual_mode 1, 2) Dijkstra from row 0 over arcs r'->r with weight
 //             pi(r, sigma(r')) (>= 0), u^c_r = dist_r + (u_r - u_0),
 //             v^c_c = c_{sigma^-1(c),c} - u^c_{sigma^-1(c)}
@@ -386,15 +387,28 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
   // optimum: pairwise tree over P = next power of two >= m rows (empty rows add
   // nothing), lane i adding lane i + h for h = P/2, ..., 1
   const T xr = cv ? cs[gl * ld + RLT2_IDX(r2c, m)] : T(0);
-  int P = 1;
-  while (P < m) P <<= 1;
-  const int PM = (G == 32) ? P : (int)__reduce_max_sync(kFull, (unsigned)P);
-  T val = xr;
-  for (int h = PM >> 1; h >= 1; h >>= 1) {
-    const T o = __shfl_xor_sync(kFull, val, h);
-    if (h < P) val = A::add(val, o);
+  T val;
+  if constexpr (G == 32 && A::kExact) {
+    // exact sums do not depend on the order: the 64-bit entries as two
+    // non-negative 26-bit limbs and a signed top part, each summed over the
+    // warp by one 32-bit reduction (32 limbs < 2^31, no overflow)
+    const unsigned long long ux = (unsigned long long)xr;
+    const int l0 = (int)(ux & 0x3ffffffull), l1 = (int)((ux >> 26) & 0x3ffffffull);
+    const int l2 = (int)(xr >> 52);
+    const long long s0 = __reduce_add_sync(kFull, l0), s1 = __reduce_add_sync(kFull, l1);
+    const long long s2 = __reduce_add_sync(kFull, l2);
+    val = (T)(s2 * (1ll << 52) + s1 * (1ll << 26) + s0);
+  } else {
+    int P = 1;
+    while (P < m) P <<= 1;
+    const int PM = (G == 32) ? P : (int)__reduce_max_sync(kFull, (unsigned)P);
+    val = xr;
+    for (int h = PM >> 1; h >= 1; h >>= 1) {
+      const T o = __shfl_xor_sync(kFull, val, h);
+      if (h < P) val = A::add(val, o);
+    }
+    val = __shfl_sync(kFull, val, gb);
   }
-  val = __shfl_sync(kFull, val, gb);
 
   if (dual_mode != 0) {
     // canonical duals: shortest paths from row 0 on reduced weights
