@@ -334,7 +334,9 @@ long long rlt2_debug_bounds_violations(void);
  *  row_to_col: device, batch*m assignment (nullable)
  *  n_aug    : device, batch augmenting searches per LAP (nullable)
  *  dual_mode: 0 raw (FP64), 1 canonical (exact fixed point), 2 canonical
- *             (FP64), as in rlt2_params.  Asynchronous on `stream`. */
+ *             (FP64), as in rlt2_params.  Asynchronous on `stream`; dual_mode
+ *             1 takes 8 bytes of stream-ordered device memory for its work
+ *             queue (cudaMallocAsync, freed on `stream` after the launch). */
 rlt2_status rlt2_lap_batched(int batch, int m, const double* cost, const double* u0, double* value, double* u,
                              double* v, int* row_to_col, int* n_aug, int dual_mode, void* stream);
 

@@ -958,6 +958,7 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   z.v = v.psi;
   z.dual_mode = p.dual_mode;
   z.stats = v.sc->stats + 0;
+  z.head = &v.sc->lap_head;
   z.skip = done;
   if ((e = rec(2, 0)) != cudaSuccess) return e;
   if (pipelined) {

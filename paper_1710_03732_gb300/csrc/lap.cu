@@ -17,7 +17,10 @@ int default_group(int m) { return m <= 8 ? 8 : (m <= 16 ? 16 : 32); }
 // of tile k+1 is issued as soon as the column reduction of tile k has
 // converted its raw entries (group_lap's hook); the grid exponent of a tile is
 // the largest exponent field of its raw entries, as in stage_tile.  Results
-// are those of the staged form bit for bit.
+// are those of the staged form bit for bit.  With a.head set, warps claim
+// their next step of 32/G LAPs from that counter (zero at launch) when they
+// issue its copies, so that warps whose LAPs needed few searches take more of
+// them and all warps end together; otherwise they take a fixed grid stride.
 template <int G>
 __device__ __forceinline__ void k_lap_prefetching(const LapArgs& a, unsigned char* base, int lane, bool warm,
                                                   long long first, long long stride) {
@@ -42,8 +45,16 @@ __device__ __forceinline__ void k_lap_prefetching(const LapArgs& a, unsigned cha
     }
     cp_async_commit();
   };
-  issue(first);
-  for (long long t0 = first; t0 < a.batch; t0 += stride) {
+  // the first LAP of this warp's next step (every lane of the warp)
+  auto claim = [&](long long t_static) -> long long {
+    if (a.head == nullptr) return t_static;
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(a.head, (unsigned long long)per);
+    return (long long)__shfl_sync(kFull, b, 0);
+  };
+  long long t0 = claim(first);
+  issue(t0);
+  while (t0 < a.batch) {
     const long long tb = t0 + grp;
     const bool have = tb < a.batch;
     const long long t = (have && a.map) ? (long long)a.map[tb] : tb;
@@ -61,9 +72,12 @@ __device__ __forceinline__ void k_lap_prefetching(const LapArgs& a, unsigned cha
     const int L = fx_grid(eb);
     T u0 = T(0);
     if (warm && have && gl < m) u0 = start_dual<true>(raw[mm + gl], L);
-    const long long next = t0 + stride;
+    long long next = a.batch;  // claimed in the hook, which group_lap calls once (raw is set)
     const WarpLapResult<T> R = group_lap<G, true, A>(tile, ld, have ? m : 0, lane, warm, u0, a.dual_mode, scr,
-                                                     uv + grp * G, raw, L, [&]() { issue(next); });
+                                                     uv + grp * G, raw, L, [&]() {
+                                                       next = claim(t0 + stride);
+                                                       issue(next);
+                                                     });
     if (have && gl < m) {
       if (a.u) a.u[t * m + gl] = out_value<true>(R.u, L);
       if (a.v) a.v[t * m + gl] = out_value<true>(R.v, L);
@@ -76,6 +90,7 @@ __device__ __forceinline__ void k_lap_prefetching(const LapArgs& a, unsigned cha
       relax_acc += R.nrelax;
     }
     __syncwarp();
+    t0 = next;
   }
   cp_async_wait_all();  // nothing may be in flight when the warp leaves
   if (a.stats && gl == 0 && (aug_acc | relax_acc)) {
@@ -266,6 +281,8 @@ cudaError_t launch_lap(const LapArgs& a, cudaStream_t s) {
   const long long need = (a.batch + per_block - 1) / per_block;
   const int grid = (int)(need < cap ? need : cap);
   const LapKernel kern = lap_kernel(G, a.pi == nullptr, a.dual_mode == 1);
+  if (!b.prefetch) b.head = nullptr;
+  if (b.head && (e = cudaMemsetAsync(b.head, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
   kern<<<grid, wpb * 32, smem, s>>>(b);
   return cudaGetLastError();
 }
@@ -555,7 +572,20 @@ extern "C" rlt2_status rlt2_lap_batched(int batch, int m, const double* cost, co
   a.r2c = row_to_col;
   a.naug = n_aug;
   a.dual_mode = dual_mode;
-  cudaError_t e = launch_lap(a, (cudaStream_t)stream);
+  const cudaStream_t s = (cudaStream_t)stream;
+  // the fixed-point form's LAP queue: 8 stream-ordered bytes, freed after the launch
+  // (without them the warps take a fixed stride; the results are the same)
+  unsigned long long* head = nullptr;
+  if (dual_mode == 1 && cudaMallocAsync((void**)&head, sizeof(unsigned long long), s) != cudaSuccess) {
+    (void)cudaGetLastError();
+    head = nullptr;
+  }
+  a.head = head;
+  cudaError_t e = launch_lap(a, s);
+  if (head) {
+    const cudaError_t ef = cudaFreeAsync(head, s);
+    if (e == cudaSuccess) e = ef;
+  }
   if (e != cudaSuccess) return cuda_fail(e, "rlt2_lap_batched");
   return RLT2_OK;
 }

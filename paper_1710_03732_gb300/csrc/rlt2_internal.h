@@ -67,6 +67,8 @@ struct LapArgs {
   const int* map;            // nullable: LAP b works on slot map[b] of every array (a subset of tiles)
   int prefetch;              // set by launch_lap: the fixed-point form without Badd and pi stages
                              // the next tile by cp.async while it solves the current one
+  unsigned long long* head;  // nullable: device counter of the prefetching form's LAP queue
+                             // (launch_lap zeroes it on the stream before the launch)
 };
 
 // The LAPs of one stage of one branch-and-bound node.
@@ -158,6 +160,7 @@ struct DevScalars {
   int iter, done, have_snap, reason;
   int sa_on;       // the pending ascent step applies a Type 4 draw
   unsigned long long stats[6];  // Z aug, Z relax, Y aug, Y relax, X aug, X relax
+  unsigned long long lap_head;  // queue counter of the Z-stage LAP launch
   double best_hist[kStallRing];  // best bound after iteration it, at it % kStallRing
 };
 
