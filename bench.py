@@ -788,7 +788,11 @@ def main():
                                     "(rlt2_probe_rates, CUDA events); nominal 64 lanes/clk/SM x 152 x 2.07 GHz = "
                                     f"{INT64_PEAK_GOPS:.0f}",
                      "limiter": "the ALU pipe's compares, selects and warp reductions of the sequential "
-                                "Dijkstra steps (ncu: ALU pipe about 70 % busy), not the additions"},
+                                "Dijkstra steps and instruction issue (ncu: ALU pipe 78 %, issue 81 % busy), "
+                                "not the additions",
+                     # the survey's roofline for this kernel counts the same additions as FP64 ops
+                     # against the FP64 pipe: above 1 means faster than an FP64 solve could be
+                     "frac_of_fp64_add_peak": ach_lz / rates["dadd"]},
         "pipelined": {"cold": whole_job_rate(world, steps, pcold_ms), "warm": whole_job_rate(world, steps, pwarm_ms),
                       "unit": "iters/s", "same_bounds": bool(pcold["lb"] == cold["lb"] and pwarm["lb"] == warm["lb"]),
                       "note": "z move and next Z-LAPs in one persistent launch (rlt2_params.pipeline = 1)"},
