@@ -69,7 +69,9 @@ __device__ __forceinline__ void move_y_range(const MoveYArgs& a, long long start
     }
   }
   for (long long t = start; t < a.T; t += stride) {
-    const int ip = RLT2_IDX((int)(t / (n1 * n1)), n * n);
+    // T = n^2 (n-1)^2 < 2^20 for n <= 32: 32-bit divisions (a 64-bit one is a
+    // long subroutine)
+    const int ip = RLT2_IDX((int)((unsigned)t / (unsigned)(n1 * n1)), n * n);
     const int rem = (int)(t - (long long)ip * n1 * n1);
     const int jj = rem / n1, qq = rem - jj * n1;
     const int i = ip / n, p = ip - i * n;
@@ -106,8 +108,8 @@ __device__ __forceinline__ void move_y_range(const MoveYArgs& a, long long start
 // runs after move_y_range has written the tile terms.
 __device__ __forceinline__ void shift_psi_range(const MoveYArgs& a, long long start, long long stride) {
   const int m = a.n - 2;
-  const long long Tm = a.T * m;
-  for (long long e = start; e < Tm; e += stride) a.psi[e] = dsub_(a.psi[e], a.tterm[e / m]);
+  const long long Tm = a.T * m;  // < 2^25 for n <= 32: the tile by a 32-bit division
+  for (long long e = start; e < Tm; e += stride) a.psi[e] = dsub_(a.psi[e], a.tterm[(unsigned)e / (unsigned)m]);
 }
 
 // The six members of a class {(i,p),(j,q),(k,r)} are the position orders of the
