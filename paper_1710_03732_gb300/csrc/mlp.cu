@@ -313,12 +313,20 @@ __global__ void k_loss(long long rows, long long nvalid, const float* out, const
 }
 
 // dH2 = relu'(H2) * dout x w3 (BF16)
+// one thread per 8 consecutive elements of a row (16-byte loads and stores; H
+// a multiple of 8, rows * H / 8 < 2^31: 32-bit index arithmetic)
 __global__ void k_dh2(long long rows, int H, const bf16* H2, const float* dout, const float* w3, bf16* dH2) {
-  const long long tot = rows * H;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const long long r = e / H;
-    const int j = (int)(e - r * H);
-    dH2[e] = __float2bfloat16_rn(__bfloat162float(H2[e]) > 0.0f ? dout[r] * w3[j] : 0.0f);
+  const unsigned per = (unsigned)(H / 8), tot = (unsigned)(rows * per);
+  for (unsigned p = blockIdx.x * blockDim.x + threadIdx.x; p < tot; p += gridDim.x * blockDim.x) {
+    const unsigned r = p / per, j0 = (p - r * per) * 8;
+    const uint4 hv = *reinterpret_cast<const uint4*>(H2 + (size_t)p * 8);
+    const bf16* h = reinterpret_cast<const bf16*>(&hv);
+    const float d = dout[r];
+    uint4 ov;
+    bf16* o = reinterpret_cast<bf16*>(&ov);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) o[k] = __float2bfloat16_rn(__bfloat162float(h[k]) > 0.0f ? d * w3[j0 + k] : 0.0f);
+    *reinterpret_cast<uint4*>(dH2 + (size_t)p * 8) = ov;
   }
 }
 
@@ -380,14 +388,17 @@ __global__ void k_init_normal(int n, int valid_rows, int cols, float stdv, unsig
 }
 
 // gather a minibatch: rows idx = hash(seed, r) % nrows
+// one thread per 16-byte piece of a sampled row (8 pieces per row, the row's
+// hash computed once per piece instead of once per element)
 __global__ void k_gather(long long brows, long long nrows, unsigned long long seed, const bf16* X, const float* T,
                          bf16* Xb, float* Tb) {
-  const long long tot = brows * kInPad;
+  constexpr int kPieces = kInPad / 8;
+  const long long tot = brows * kPieces;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const long long r = e / kInPad;
-    const int k = (int)(e - r * kInPad);
+    const long long r = e / kPieces;
+    const int k = (int)(e - r * kPieces);
     const long long src = (long long)(smix(seed ^ (unsigned long long)r) % (unsigned long long)nrows);
-    Xb[e] = X[src * kInPad + k];
+    *reinterpret_cast<uint4*>(Xb + r * kInPad + k * 8) = *reinterpret_cast<const uint4*>(X + src * kInPad + k * 8);
     if (k == 0) Tb[r] = T[src];
   }
 }
