@@ -97,6 +97,33 @@ def test_gradients_match_oracle(R, H):
         assert err <= 1e-2, (name, err)
 
 
+def test_gradients_several_tiles_per_persistent_cta(R):
+    """The tall products run on persistent CTAs (one per SM, two per 128-row
+    tile at H = 256) that take several 128-row tiles each, alternating two TMEM
+    accumulators and two staging tiles: 41,400 rows (324 tiles, the last
+    ragged; four or more per CTA on a 152-SM GB300) against the FP64 oracle."""
+    rng = np.random.default_rng(77)
+    m, nt, H = 18, 2300, 256
+    tiles = _tiles(rng, nt, m)
+    prev = rng.normal(size=(nt, m))
+    tgt = rng.normal(size=(nt, m))
+    net = _random_weights(rng, H)
+    mlp = R.Mlp(H)
+    mlp.set_weights(*net)
+    mlp.add_samples(torch.from_numpy(tiles).cuda(), torch.from_numpy(tgt).cuda(), torch.from_numpy(prev).cuda())
+    X, T = mlp.samples()
+    rows = X.shape[0]
+    assert rows == nt * m and rows % 128 != 0 and rows // 128 >= 300
+    loss, *g = mlp.grad(rows)
+    oloss, *og = O.mlp_grads(X, *net, T.astype(np.float64), bf16_acts=True)
+    assert abs(loss - oloss) <= 1e-3 * abs(oloss)
+    for name, a, b in zip(["W1", "b1", "W2", "b2", "w3", "b3"], g, og):
+        a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+        err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        assert err <= 1e-2, (name, err)
+    mlp.close()
+
+
 def test_training_reduces_loss_and_augmentations(R):
     """Train on (tile, canonical dual) pairs harvested from an n=12 ascent, then
     warm-start another n=12 ascent: bounds identical to the cold run (canonical
