@@ -188,9 +188,27 @@ template <int G>
 __device__ __forceinline__ int group_argmin(unsigned long long key, int gb) {
   if constexpr (G == 32) {
     return warp_argmin(key);
+  } else if constexpr (G == 16) {
+    // two full-warp reductions of the high words, each with the other half's
+    // lanes at the maximum (no divergence, unlike a redux.sync on a half-warp
+    // mask), the low words only where a half has a tie on the high word
+    const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+    const bool g0 = gb == 0;
+    const unsigned m0 = __reduce_min_sync(kFull, g0 ? hi : 0xffffffffu);
+    const unsigned m1 = __reduce_min_sync(kFull, g0 ? 0xffffffffu : hi);
+    const unsigned mhi = g0 ? m0 : m1;
+    unsigned mine = (__ballot_sync(kFull, hi == mhi) >> gb) & 0xffffu;
+    if (__any_sync(kFull, (mine & (mine - 1u)) != 0u)) {
+      const bool cand = hi == mhi;
+      const unsigned l0 = __reduce_min_sync(kFull, (g0 && cand) ? lo : 0xffffffffu);
+      const unsigned l1 = __reduce_min_sync(kFull, (!g0 && cand) ? lo : 0xffffffffu);
+      const unsigned mlo = g0 ? l0 : l1;
+      mine = (__ballot_sync(kFull, cand && lo == mlo) >> gb) & 0xffffu;
+    }
+    return __ffs(mine) - 1;
   } else {
-    // xor butterfly (a half-warp redux.sync with the group's lane mask was
-    // slower here: 0.121 against 0.104 ms per iteration at n = 12)
+    // xor butterfly (a redux.sync on the group's own lane mask was slower
+    // here: 0.121 against 0.104 ms per iteration at n = 12)
     unsigned long long k = key;
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1) {
