@@ -189,8 +189,8 @@ def cpu_oracle_baseline(inst, iters: int, budget_s: float, warm: bool = True):
 
 def cpu_oracle_detail():
     """The oracle on one core at n = 20 (first 2 iterations) and on all cores at
-    n = 30 (first iteration, setup excluded): the survey's CPU timings, bounded to
-    about 20 s."""
+    n = 30 (first iteration, setup excluded): CPU timings of the method itself,
+    bounded to about 20 s."""
     import oracle as O
     threads = max(1, O.max_threads() or 1)
     prm = O.params_array()
@@ -789,8 +789,8 @@ def main():
                      "limiter": "the ALU pipe's compares, selects and warp reductions of the sequential "
                                 "Dijkstra steps and instruction issue (ncu: ALU pipe 78 %, issue 81 % busy), "
                                 "not the additions",
-                     # the survey's roofline for this kernel counts the same additions as FP64 ops
-                     # against the FP64 pipe: above 1 means faster than an FP64 solve could be
+                     # the same additions counted as FP64 ops against the FP64 pipe (the roofline of
+                     # an FP64 solve): above 1 means faster than an FP64 solve could be
                      "frac_of_fp64_add_peak": ach_lz / rates["dadd"]},
         "pipelined": {"cold": whole_job_rate(world, steps, pcold_ms), "warm": whole_job_rate(world, steps, pwarm_ms),
                       "unit": "iters/s", "same_bounds": bool(pcold["lb"] == cold["lb"] and pwarm["lb"] == warm["lb"]),
