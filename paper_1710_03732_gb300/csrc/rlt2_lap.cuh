@@ -330,7 +330,7 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
   // warp-uniform and needs no vote
   unsigned freerows = group_bits<G>(__ballot_sync(kFull, cv && r2c < 0), gb);
   while (G == 32 ? freerows != 0 : __any_sync(kFull, freerows != 0)) {
-    const bool act = freerows != 0;  // this group runs a search in this round
+    const bool act = freerows != 0;  // this group runs a search in this pass
     const int i = act ? __ffs(freerows) - 1 : 0;
     if (act) {
       freerows &= freerows - 1;
