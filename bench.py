@@ -263,12 +263,17 @@ def run_reference(args):
     return 0
 
 
-def timed_device_run(R, torch, inst, warm: int, steps: int, warmup: int, barrier, mode: int = 1, pipeline: int = 0):
+def timed_device_run(R, torch, inst, warm: int, steps: int, warmup: int, barrier, mode: int = 1, pipeline: int = 0,
+                     timing: bool = True):
+    """`steps` iterations after `warmup`, timed with CUDA events on the context's
+    stream every 50 iterations.  timing: also CUDA events around every kernel
+    launch (the per-kernel times; iterations are then launched kernel by kernel
+    instead of replayed as a graph, so the run itself is a little slower)."""
     prm = R.params(dual_mode=mode, warm=warm, feas_tol=0.0, pipeline=pipeline)
     ctx = R.Context(inst.F, inst.D, inst.B, prm=prm)
     ctx.iterate(warmup)
     s0 = ctx.stats()
-    ctx.set_timing(True)
+    ctx.set_timing(timing)
     barrier()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -673,8 +678,13 @@ def main():
             dist.barrier()
 
     with ClockSampler(local) as clocks:
-        cold = timed_device_run(R, torch, inst, 0, args.steps, args.warmup, barrier)
-        warm = timed_device_run(R, torch, inst, 1, args.steps, args.warmup, barrier)
+        # the headline runs: graph replay, no per-kernel events
+        cold = timed_device_run(R, torch, inst, 0, args.steps, args.warmup, barrier, timing=False)
+        warm = timed_device_run(R, torch, inst, 1, args.steps, args.warmup, barrier, timing=False)
+        # the same warm run again with CUDA events around every launch: the per-kernel
+        # times of the rooflines and the kernel breakdown
+        warm_k = timed_device_run(R, torch, inst, 1, args.steps, args.warmup, barrier)
+        warm["kt"] = warm_k["kt"]
         # the same ascent with the canonical duals computed in FP64 (dual_mode 2)
         f64 = timed_device_run(R, torch, inst, 1, args.steps, args.warmup, barrier, mode=2)
         # the z move and the next Z-LAPs as one launch (rlt2_params.pipeline)
@@ -699,6 +709,7 @@ def main():
         return rank_max(x, dist, "cuda")
 
     warm_ms = per_rank_max(warm["ms"])
+    warm_k_ms = per_rank_max(warm_k["ms"])
     cold_ms = per_rank_max(cold["ms"])
     f64_ms = per_rank_max(f64["ms"])
     pcold_ms = per_rank_max(pcold["ms"])
@@ -777,8 +788,12 @@ def main():
             "last_50": warm["windows"][-1][1] / warm["windows"][-1][0],
             "cold_first_50_after_warmup": cold["windows"][0][1] / cold["windows"][0][0],
             "cold_last_50": cold["windows"][-1][1] / cold["windows"][-1][0]},
-        "kernels_ms_per_iteration": {k: v[0] / steps for k, v in warm["kt"].items()},
-        "kernel_launches_per_iteration": {k: v[1] / steps for k, v in warm["kt"].items()},
+        "kernels_ms_per_iteration": {k: v[0] / steps for k, v in warm["kt"].items() if v[1] > 0},
+        "kernel_launches_per_iteration": {k: v[1] / steps for k, v in warm["kt"].items() if v[1] > 0},
+        "kernel_times_run": {"iters_per_s": whole_job_rate(world, steps, warm_k_ms),
+                             "note": "per-kernel times (and the rooflines) from a second run of the same warm "
+                                     "workload with CUDA events around every launch, launched kernel by kernel; "
+                                     "value and ms_per_step from graph replay without them"},
         "roofline_lap_z": {"bound": "alu", "kernel": "lap_z", "achieved": ach_lz, "peak": int64_peak,
                      "unit": INT64_UNIT, "frac": ach_lz / int64_peak, "traffic": traffic,
                      "algorithmic_ops_per_launch": fl_lz, "avg_launch_ms": avg_lz,
