@@ -377,6 +377,17 @@ typedef struct rlt2_mlp rlt2_mlp;
  * not run out, EINVAL for a network whose width is not 256, ECUDA otherwise. */
 rlt2_status rlt2_mlp_check_wait_timeout(rlt2_mlp* mlp);
 
+/* The same check for the training GEMM of the tall products (the persistent
+ * TMA / tcgen05 kernel: a producer, an MMA issuer and four epilogue warps):
+ * runs the second forward layer's product on 1,024 zero rows with no MMA
+ * issued and none committed, so the producer's and the epilogue's bounded
+ * waits run out; each role then stops the others, lets its started copies
+ * land and releases the TMEM, and the network's error flag is set.  Returns
+ * RLT2_ETIMEOUT when that was detected (flag cleared again), RLT2_OK if no
+ * wait ran out, EINVAL for a width other than 256, ECUDA otherwise.  The
+ * network's activation buffers are overwritten. */
+rlt2_status rlt2_mlp_check_gemm_wait_timeout(rlt2_mlp* mlp);
+
 /* Failure-detection check of the pipelined launch (rlt2_params.pipeline = 1;
  * no counterpart in the paper): enqueues one iteration whose Z-LAP warps wait
  * for facility-pair counts that the z move never reaches, with the polls

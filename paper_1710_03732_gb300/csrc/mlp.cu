@@ -865,6 +865,46 @@ extern "C" rlt2_status rlt2_mlp_check_wait_timeout(rlt2_mlp* m) {
   return RLT2_OK;
 }
 
+extern "C" rlt2_status rlt2_mlp_check_gemm_wait_timeout(rlt2_mlp* m) {
+  if (!m || m->H != 256) {
+    set_error("rlt2_mlp_check_gemm_wait_timeout: needs a network with H = 256");
+    return RLT2_EINVAL;
+  }
+  // the second forward layer's product on 1,024 zero rows (eight 128-row tiles,
+  // four K chunks each) with the MMAs withheld
+  constexpr int kRows = 1024;
+  const int H = m->H;
+  CKM(cudaMemsetAsync(m->err, 0, sizeof(int), m->stream));
+  CKM(cudaMemsetAsync(m->H1, 0, sizeof(bf16) * kRows * H, m->stream));
+  UmmaGemmArgs u{};
+  u.M = kRows;
+  u.N = H;
+  u.K = H;
+  u.A = m->H1;
+  u.lda = H;
+  u.a_kmajor = true;
+  u.B = m->W2b;
+  u.ldb = H;
+  u.b_kmajor = false;
+  u.epi = 1;
+  u.Cb = m->H2;
+  u.ldc = H;
+  u.bias = m->b2;
+  u.err = m->err;
+  u.withhold = 1;
+  CKM(umma_gemm(u, 1, m->stream));
+  CKM(cudaStreamSynchronize(m->stream));
+  int err = 0;
+  CKM(cudaMemcpy(&err, m->err, sizeof(int), cudaMemcpyDeviceToHost));
+  CKM(cudaMemsetAsync(m->err, 0, sizeof(int), m->stream));
+  CKM(cudaStreamSynchronize(m->stream));
+  if (err) {
+    set_error("rlt2_mlp_check_gemm_wait_timeout: the training GEMM's waits ran out (expected)");
+    return RLT2_ETIMEOUT;
+  }
+  return RLT2_OK;
+}
+
 extern "C" rlt2_status rlt2_mlp_predict(rlt2_mlp* m, long long ntiles, int mz, const double* tiles,
                                         const double* prev_u, double* u0) {
   if (!m || ntiles < 0 || mz < 1 || mz > 32 || (ntiles > 0 && (!tiles || !u0))) {

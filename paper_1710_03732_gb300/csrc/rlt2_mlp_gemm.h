@@ -24,6 +24,8 @@ struct UmmaGemmArgs {
   int* err;                  // set on a timed-out wait
   int kps;                   // K per split (set by umma_gemm)
   unsigned tmem_cols;        // TMEM columns allocated (set by umma_gemm)
+  int withhold;              // diagnostics (tall products): issue no MMA and no commit, so that
+                             // the bounded waits run out (failure detection without a fault)
 };
 
 // Shapes the kernel takes (the caller falls back to the mma.sync GEMM otherwise).

@@ -637,6 +637,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (a.withhold) continue;  // diagnostics: nothing issued, nothing committed
       const uint32_t aa = smem_u32(ring + (size_t)sl * kBM * kBK * 2);
       const uint32_t acc = tmem + (uint32_t)((i & 1) * kBN);
 #pragma unroll
@@ -660,7 +661,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                      : "memory");
     }
     // no MMA in flight when the TMEM is released (the last commit covers all)
-    if (g > 0) (void)mbar_wait(smem_u32(empty + (g - 1) % kS), (uint32_t)(((g - 1) / kS) & 1));
+    if (g > 0 && !a.withhold) (void)mbar_wait(smem_u32(empty + (g - 1) % kS), (uint32_t)(((g - 1) / kS) & 1));
   } else if (warp >= 4) {
     // epilogue warps: warp 4 + q drains TMEM lanes 32 q .. 32 q + 31 (rows of the tile) over all
     // columns into the staging tile j % 2, which thread 128 then stores by TMA (boxes of 64

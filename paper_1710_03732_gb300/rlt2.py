@@ -55,7 +55,8 @@ EXPORTS = ["rlt2_params_default", "rlt2_create", "rlt2_iterate", "rlt2_iterate_a
            "rlt2_mlp_set_weights", "rlt2_mlp_add_samples", "rlt2_mlp_samples", "rlt2_mlp_clear_samples",
            "rlt2_mlp_grad", "rlt2_mlp_fit", "rlt2_mlp_set_gate", "rlt2_mlp_predict", "rlt2_set_mlp",
            "rlt2_export_xstate", "rlt2_import_xstate", "rlt2_set_sa", "rlt2_create_child", "rlt2_bnb_options_default",
-           "rlt2_bnb_solve", "rlt2_mlp_check_wait_timeout", "rlt2_pipeline_check_wait_timeout",
+           "rlt2_bnb_solve", "rlt2_mlp_check_wait_timeout", "rlt2_mlp_check_gemm_wait_timeout",
+           "rlt2_pipeline_check_wait_timeout",
            "rlt2_debug_bounds_violations", "rlt2_probe_rates", "rlt2_fp64_add_emulated", "rlt2_node_tuning", "rlt2_iterate_many",
            "rlt2_strerror",
            "rlt2_last_error"]
@@ -112,6 +113,7 @@ def lib():
     L.rlt2_mlp_predict.argtypes = [_vp, ctypes.c_longlong, ctypes.c_int, _vp, _vp, _vp]
     L.rlt2_mlp_set_gate.argtypes = [_vp, ctypes.c_double]
     L.rlt2_mlp_check_wait_timeout.argtypes = [_vp]
+    L.rlt2_mlp_check_gemm_wait_timeout.argtypes = [_vp]
     L.rlt2_pipeline_check_wait_timeout.argtypes = [_vp]
     L.rlt2_probe_rates.argtypes = [_dp, _dp, _vp]
     L.rlt2_node_tuning.argtypes = [ctypes.c_int, _ip, _ip, _ip, _dp, _ip]

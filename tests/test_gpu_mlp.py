@@ -179,6 +179,32 @@ def test_inference_wait_timeout_is_detected(R):
     assert np.allclose(u0[3], ref, rtol=2e-3, atol=2e-3 * abs(s))
 
 
+def test_gemm_wait_timeout_is_detected(R):
+    """Failure detection without a fault for the persistent training GEMM: its
+    MMAs are withheld, the producer's and the epilogue's bounded waits run out,
+    ETIMEOUT reaches the host, and the device stays usable (gradients on the
+    next call still match the oracle)."""
+    mlp = R.Mlp(256)
+    st = R.lib().rlt2_mlp_check_gemm_wait_timeout(mlp.ptr)
+    assert st == R.RLT2_ETIMEOUT
+    rng = np.random.default_rng(21)
+    m, nt = 14, 150
+    tiles = _tiles(rng, nt, m)
+    prev = rng.normal(size=(nt, m))
+    tgt = rng.normal(size=(nt, m))
+    net = _random_weights(rng, 256)
+    mlp.set_weights(*net)
+    mlp.add_samples(torch.from_numpy(tiles).cuda(), torch.from_numpy(tgt).cuda(), torch.from_numpy(prev).cuda())
+    X, T = mlp.samples()
+    loss, *g = mlp.grad(X.shape[0])
+    oloss, *og = O.mlp_grads(X, *net, T.astype(np.float64), bf16_acts=True)
+    assert abs(loss - oloss) <= 1e-3 * abs(oloss)
+    for a, b in zip(g, og):
+        a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+        assert np.linalg.norm(a - b) <= 1e-2 * max(np.linalg.norm(b), 1e-30)
+    mlp.close()
+
+
 def test_trained_network_against_both_starts_on_held_out_grid(R):
     """The shipped network (weights/warmstart_h256.npz, trained on n = 20..25
     runs) on a held-out n = 22 grid (seed 99, never trained on), 12 iterations:
