@@ -6,8 +6,9 @@
 //   k_move_y     per tile: pending y move (Eq. 2.21; the F and half-Z forms)
 //                and the tile term cy*pi_y + cx*pi_x that rules 2 and 3
 //                (Eq. 2.22, 2.23) add to every z pool, plus an accepted Type 4
-//                amount (Section 2.3 rule 4)
-//   k_shift_psi  psi <- psi - tile term for the folded z move (kz = 1, equal phi)
+//                amount (Section 2.3 rule 4); for the folded z move (kz = 1,
+//                equal phi) also psi <- psi - tile term, and it zeroes the Z
+//                stage's LAP queue counter
 //   k_move_z     class-owned z move (Eq. 2.20 + 2.22 + 2.23, combined as in the
 //                proof of Theorem 1), in place on D^ (Section 3.3)
 //   k_lap(Z)     n^2 (n-1)^2 LAPs of size n-2 on the tiles of D^ (half of them
@@ -99,14 +100,14 @@ __global__ void k_setup_c(int nr, long long T, const double* Fr, const double* D
 // ------------------------------------------------------------------ moves ----
 static const int h_widx[5] = {0, 1, 3, 2, 4};
 
+// blockDim.x a multiple of 32 (the folded form's warps move 32 tiles together)
 __global__ void k_move_y(MoveYArgs a) {
+  // the Z stage's launch comes after this one on the stream
+  if (a.lap_head && blockIdx.x == 0 && threadIdx.x == 0) *a.lap_head = 0;
   if (!a.sc->have_snap || a.sc->done) return;
-  move_y_range(a, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
-}
-
-__global__ void k_shift_psi(MoveYArgs a) {
-  if (!a.sc->have_snap || a.sc->done) return;
-  shift_psi_range(a, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+  const long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  if (a.shift_psi) move_y_shift_range(a, start, stride);
+  else move_y_range(a, start, stride);
 }
 
 // at most 352 threads (move_z_threads) and 62 registers: three blocks per SM
@@ -275,7 +276,8 @@ struct rlt2_ctx {
   int *xperm = nullptr, *ubperm = nullptr, *trips = nullptr;
   int ntrip = 0;
   DevScalars* sc = nullptr;
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;       // one iteration
+  cudaGraphExec_t graph_many = nullptr;  // kGraphIters iterations (fewer launch gaps)
   bool timing = false;
   std::vector<cudaEvent_t> ev;  // timing mode: 2 events per kernel launch
   double kms[kKinds] = {};
@@ -335,6 +337,7 @@ static size_t ctx_pool_idle(cudaMemPool_t pool) {
 static void ctx_free(rlt2_ctx* c) {
   if (!c) return;
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->graph_many) cudaGraphExecDestroy(c->graph_many);
   for (auto e : c->ev) cudaEventDestroy(e);
   if (c->arena) cudaFreeAsync(c->arena, c->stream);
   if (c->sa_buf) cudaFree(c->sa_buf);
@@ -828,6 +831,7 @@ MoveYArgs rlt2::make_move_y(const IterView& v) {
   a.sa_count = v.sa_count;
   a.c4 = 1.0 / (((double)n * (double)(n - 1)) * (double)(n - 2));
   a.sc = v.sc;
+  a.lap_head = &v.sc->lap_head;
   return a;
 }
 
@@ -919,11 +923,7 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
     const MoveYArgs my = make_move_y(v);
     const long long blocks = (T + 255) / 256;
     k_move_y<<<(int)(blocks < 8192 ? blocks : 8192), 256, 0, s>>>(my);
-    count(0, my.shift_psi ? 2 : 1);
-    if (my.shift_psi) {
-      const long long b2 = (T * m + 255) / 256;
-      k_shift_psi<<<(int)(b2 < 16384 ? b2 : 16384), 256, 0, s>>>(my);
-    }
+    count(0, 1);
   }
   if ((e = cudaGetLastError()) != cudaSuccess || (e = rec(0, 1)) != cudaSuccess) return e;
   // 2) z move (inside the Z-stage launch when pipelined)
@@ -959,6 +959,7 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
   z.dual_mode = p.dual_mode;
   z.stats = v.sc->stats + 0;
   z.head = &v.sc->lap_head;
+  z.head_zeroed = 1;  // by k_move_y
   z.skip = done;
   if ((e = rec(2, 0)) != cudaSuccess) return e;
   if (pipelined) {
@@ -980,6 +981,7 @@ cudaError_t rlt2::enqueue_iteration(const IterView& v, cudaStream_t s, cudaEvent
     LapArgs z2 = z;
     z2.u0 = p.warm >= 1 ? v.xi : nullptr;  // from the first phase's row duals
     z2.warm_gate = nullptr;
+    z2.head_zeroed = 0;  // the first phase used the counter
     if ((e = launch_lap(z2, s)) != cudaSuccess) return e;
     count(7, 1);
   }
@@ -1063,25 +1065,49 @@ extern "C" rlt2_status rlt2_pipeline_check_wait_timeout(rlt2_ctx* c) {
   return RLT2_OK;
 }
 
-static rlt2_status build_graph(rlt2_ctx* c) {
-  if (c->graph) return RLT2_OK;
+// Iterations per replay of the longer graph: within one graph the kernels of
+// consecutive iterations follow each other with the short intra-graph gap
+// instead of a graph launch's.
+constexpr int kGraphIters = 8;
+
+// Captures `iters` iterations into *out.
+static rlt2_status capture_graph(rlt2_ctx* c, int iters, cudaGraphExec_t* out) {
   if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = enqueue_iteration_ctx(c, c->cap_stream, -1);
+  cudaError_t e = cudaSuccess;
+  for (int it = 0; it < iters && e == cudaSuccess; ++it) e = enqueue_iteration_ctx(c, c->cap_stream, -1);
   cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
   if (e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     return cuda_fail(e, "capture");
   }
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&c->graph, g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    c->graph = nullptr;
+    *out = nullptr;
     return cuda_fail(e, "cudaGraphInstantiate");
   }
   return RLT2_OK;
+}
+
+static rlt2_status build_graph(rlt2_ctx* c) {
+  if (c->graph) return RLT2_OK;
+  rlt2_status st = capture_graph(c, 1, &c->graph);
+  if (st != RLT2_OK) return st;
+  if ((st = capture_graph(c, kGraphIters, &c->graph_many)) != RLT2_OK) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return st;
+}
+
+// The graphs hold the arguments they were captured with.
+static void drop_graphs(rlt2_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->graph_many) cudaGraphExecDestroy(c->graph_many);
+  c->graph = c->graph_many = nullptr;
 }
 
 constexpr int kEvChunk = 64;  // iterations per batch of timing events
@@ -1127,7 +1153,9 @@ static rlt2_status enqueue_many(rlt2_ctx* c, int iters) {
   }
   rlt2_status st = build_graph(c);
   if (st != RLT2_OK) return st;
-  for (int it = 0; it < iters; ++it) CK(cudaGraphLaunch(c->graph, c->stream));
+  int left = iters;
+  for (; left >= kGraphIters; left -= kGraphIters) CK(cudaGraphLaunch(c->graph_many, c->stream));
+  for (; left > 0; --left) CK(cudaGraphLaunch(c->graph, c->stream));
   c->enqueued += iters;
   return RLT2_OK;
 }
@@ -1434,11 +1462,7 @@ extern "C" rlt2_status rlt2_set_sa(rlt2_ctx* c, int count, const double* kf, con
     CK(cudaMemcpy(c->sa_buf, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice));
     c->sa_count = count;
   }
-  // the graph holds the old arguments
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-  }
+  drop_graphs(c);  // the graphs hold the old arguments
   return RLT2_OK;
 }
 
@@ -1492,10 +1516,7 @@ extern "C" rlt2_status rlt2_set_mlp(rlt2_ctx* c, rlt2_mlp* m) {
   CK(cudaStreamSynchronize(c->stream));
   if (m && !c->u0buf) CK(cudaMalloc((void**)&c->u0buf, sizeof(double) * (size_t)c->T * c->m));
   c->mlp = m;
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-  }
+  drop_graphs(c);
   return RLT2_OK;
 }
 

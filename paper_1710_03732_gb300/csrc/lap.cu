@@ -137,8 +137,10 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap(LapArgs a) {
     const long long tb = t0 + grp;
     const bool have = tb < a.batch;
     const long long t = (have && a.map) ? (long long)a.map[tb] : tb;
-    const int L = stage_tile<G, FX>(tile, ld, m, gl, have ? a.A + t * mm : nullptr,
-                                    (have && a.Badd) ? a.Badd + t * mm : nullptr);
+    // with a reduced-cost output (the Y and X stages: few LAPs, one per warp)
+    // the tile's loads are batched
+    const int L = stage_tile<G, FX, false, PRE ? 1 : 4>(tile, ld, m, gl, have ? a.A + t * mm : nullptr,
+                                                        (have && a.Badd) ? a.Badd + t * mm : nullptr);
     T u0 = T(0);
     if (warm && have && gl < m) u0 = start_dual<FX>(a.u0[t * m + gl], L);
     __syncwarp();
@@ -164,6 +166,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap(LapArgs a) {
         double* dst = a.pi + t * mm;
         const T* ug = uv + grp * G;
         const T* vg = uv + 32 + grp * G;
+#pragma unroll 4
         for (int e = gl; e < mm; e += G) {
           const int r = e / m, c = e - r * m;
           dst[e] = out_value<FX>(A::sub(A::sub(tile[r * ld + c], ug[r]), vg[c]), L);
@@ -282,7 +285,8 @@ cudaError_t launch_lap(const LapArgs& a, cudaStream_t s) {
   const int grid = (int)(need < cap ? need : cap);
   const LapKernel kern = lap_kernel(G, a.pi == nullptr, a.dual_mode == 1);
   if (!b.prefetch) b.head = nullptr;
-  if (b.head && (e = cudaMemsetAsync(b.head, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+  if (b.head && !b.head_zeroed && (e = cudaMemsetAsync(b.head, 0, sizeof(unsigned long long), s)) != cudaSuccess)
+    return e;
   kern<<<grid, wpb * 32, smem, s>>>(b);
   return cudaGetLastError();
 }

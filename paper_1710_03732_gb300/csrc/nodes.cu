@@ -29,10 +29,13 @@
 namespace rlt2 {
 namespace {
 
+// blockDim.x a multiple of 32 (the folded form's warps move 32 tiles together)
 __global__ void k_move_y_nodes(const MoveYArgs* nodes) {
   const MoveYArgs a = nodes[blockIdx.y];
   if (!a.sc->have_snap || a.sc->done) return;
-  move_y_range(a, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+  const long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  if (a.shift_psi) move_y_shift_range(a, start, stride);
+  else move_y_range(a, start, stride);
 }
 
 __global__ void __launch_bounds__(352, 3) k_move_z_nodes(const MoveZArgs* nodes, const int* nblocks) {
@@ -40,12 +43,6 @@ __global__ void __launch_bounds__(352, 3) k_move_z_nodes(const MoveZArgs* nodes,
   const MoveZArgs a = nodes[blockIdx.y];
   if (!a.sc->have_snap || a.sc->done) return;
   move_z_block(a, blockIdx.x, threadIdx.x, blockDim.x);
-}
-
-__global__ void k_shift_psi_nodes(const MoveYArgs* nodes) {
-  const MoveYArgs a = nodes[blockIdx.y];
-  if (!a.shift_psi || !a.sc->have_snap || a.sc->done) return;
-  shift_psi_range(a, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
 __global__ void __launch_bounds__(512) k_phase2_nodes(const Phase2Args* nodes, const int* nblocks) {
@@ -244,9 +241,6 @@ cudaError_t enqueue_wave_iteration(const Wave& w, const WaveDev& d, int dual_mod
   {
     const int bx = std::max(1, std::min(1024, (w.max_T + 255) / 256));
     k_move_y_nodes<<<dim3(bx, w.nn), 256, 0, s>>>(d.my);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int bx2 = std::max(1, std::min(4096, (int)(((long long)w.max_T * (w.max_n - 2) + 255) / 256)));
-    k_shift_psi_nodes<<<dim3(bx2, w.nn), 256, 0, s>>>(d.my);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   k_move_z_nodes<<<dim3(w.max_blocks, w.nn), move_z_threads(w.max_n), 0, s>>>(d.mz, d.mz_blocks);

@@ -41,6 +41,7 @@ struct MoveYArgs {
   int sa_count;
   double c4;  // 1 / (n (n-1) (n-2))
   DevScalars* sc;
+  unsigned long long* lap_head;  // nullable: the Z stage's LAP queue counter, zeroed by the y-move launch
 };
 
 // Per tile (i,p,j,q): the pending y move on C^ (S: Eq. 2.21 on the full cost;
@@ -50,66 +51,111 @@ struct MoveYArgs {
 // kf_i g + kl_p g of an accepted draw (rule 4, Section 5: accepted when
 // kappa^lb * nu <= -ln(u) T).  Thread 0 records the draw's acceptance and, in
 // F, makes the last bound the base of the next one (Eq. 3.7).
-__device__ __forceinline__ void move_y_range(const MoveYArgs& a, long long start, long long stride) {
-  const int n = a.n, n1 = n - 1;
-  bool on = false;
-  double g = 0.0;
-  const double* kf = nullptr;
-  const double* kl = nullptr;
+struct MoveYDraw {
+  bool on;  // the Type 4 draw of this iteration was accepted
+  double g;
+  const double* kf;
+  const double* kl;
+};
+
+__device__ __forceinline__ MoveYDraw move_y_draw(const MoveYArgs& a) {
+  MoveYDraw r{false, 0.0, nullptr, nullptr};
   if (a.sa_count > 0) {
     const int d = a.sc->iter - 1;
     if (d >= 0 && d < a.sa_count) {
       const double nu = a.sc->lb;
       if (dmul_(a.sa_K[d], nu) <= a.sa_thr[d]) {
-        on = true;
-        g = dmul_(nu, a.c4);
-        kf = a.sa_kf + (long long)d * n;
-        kl = a.sa_kl + (long long)d * n;
+        r.on = true;
+        r.g = dmul_(nu, a.c4);
+        r.kf = a.sa_kf + (long long)d * a.n;
+        r.kl = a.sa_kl + (long long)d * a.n;
       }
     }
   }
-  for (long long t = start; t < a.T; t += stride) {
-    // T = n^2 (n-1)^2 < 2^20 for n <= 32: 32-bit divisions (a 64-bit one is a
-    // long subroutine)
-    const int ip = RLT2_IDX((int)((unsigned)t / (unsigned)(n1 * n1)), n * n);
-    const int rem = (int)(t - (long long)ip * n1 * n1);
-    const int jj = rem / n1, qq = rem - jj * n1;
-    const int i = ip / n, p = ip - i * n;
-    const int j = jj + (jj >= i), q = qq + (qq >= p);
-    const long long tp = RLT2_IDX(((long long)(j * n + q) * n1 + (i - (i > j))) * n1 + (p - (p > q)), a.T);
-    const double py = a.piy[t];
-    // half-Z scheme: the z pools of an upper tile take the y slack left after the y move
-    const double pyz = a.half ? dadd_(dsub_(py, dmul_(a.phi_y, py)), dmul_(a.phi_y, a.piy[tp])) : py;
-    double ty = dadd_(dmul_(a.cy, pyz), dmul_(a.cx, a.pix[ip]));
-    if (on) ty = dadd_(ty, dadd_(dmul_(kf[i], g), dmul_(kl[p], g)));
-    a.tterm[t] = ty;
-    if (a.half) {
-      // y move of Eq. 2.21, then Type 3 on the y level: a lower y (i > j) gives
-      // kx pi_x(ip) / (n-1) to its mirror (the lower z stay at zero)
-      const double c0 = dadd_(dsub_(a.Chat[t], dmul_(a.phi_y, py)), dmul_(a.phi_y, a.piy[tp]));
-      a.Chat[t] = (i > j) ? dsub_(c0, dmul_(a.cxy, a.pix[ip])) : dadd_(c0, dmul_(a.cxy, a.pix[j * n + q]));
-    } else if (a.fast)
-      a.Chat[t] = dadd_(dmul_(a.keep_y, py), dmul_(a.phi_y, a.piy[tp]));
-    else
-      a.Chat[t] = dadd_(dsub_(a.Chat[t], dmul_(a.phi_y, py)), dmul_(a.phi_y, a.piy[tp]));
-    if (t < (long long)n * n) {
-      const int xi_ = (int)t / n, xp = (int)t - xi_ * n;
-      if (a.fast) a.xcost[t] = dmul_(a.keep_x, a.pix[t]);
-      if (on) a.saterm[t] = dadd_(dmul_(kf[xi_], g), dmul_(kl[xp], g));
-    }
+  return r;
+}
+
+// The y move of tile t; returns the tile's term (also written to tterm).
+__device__ __forceinline__ double move_y_tile(const MoveYArgs& a, long long t, const MoveYDraw& dr) {
+  const int n = a.n, n1 = n - 1;
+  const bool on = dr.on;
+  const double g = dr.g;
+  const double* kf = dr.kf;
+  const double* kl = dr.kl;
+  // T = n^2 (n-1)^2 < 2^20 for n <= 32: 32-bit divisions (a 64-bit one is a
+  // long subroutine)
+  const int ip = RLT2_IDX((int)((unsigned)t / (unsigned)(n1 * n1)), n * n);
+  const int rem = (int)(t - (long long)ip * n1 * n1);
+  const int jj = rem / n1, qq = rem - jj * n1;
+  const int i = ip / n, p = ip - i * n;
+  const int j = jj + (jj >= i), q = qq + (qq >= p);
+  const long long tp = RLT2_IDX(((long long)(j * n + q) * n1 + (i - (i > j))) * n1 + (p - (p > q)), a.T);
+  const double py = a.piy[t];
+  // half-Z scheme: the z pools of an upper tile take the y slack left after the y move
+  const double pyz = a.half ? dadd_(dsub_(py, dmul_(a.phi_y, py)), dmul_(a.phi_y, a.piy[tp])) : py;
+  double ty = dadd_(dmul_(a.cy, pyz), dmul_(a.cx, a.pix[ip]));
+  if (on) ty = dadd_(ty, dadd_(dmul_(kf[i], g), dmul_(kl[p], g)));
+  a.tterm[t] = ty;
+  if (a.half) {
+    // y move of Eq. 2.21, then Type 3 on the y level: a lower y (i > j) gives
+    // kx pi_x(ip) / (n-1) to its mirror (the lower z stay at zero)
+    const double c0 = dadd_(dsub_(a.Chat[t], dmul_(a.phi_y, py)), dmul_(a.phi_y, a.piy[tp]));
+    a.Chat[t] = (i > j) ? dsub_(c0, dmul_(a.cxy, a.pix[ip])) : dadd_(c0, dmul_(a.cxy, a.pix[j * n + q]));
+  } else if (a.fast)
+    a.Chat[t] = dadd_(dmul_(a.keep_y, py), dmul_(a.phi_y, a.piy[tp]));
+  else
+    a.Chat[t] = dadd_(dsub_(a.Chat[t], dmul_(a.phi_y, py)), dmul_(a.phi_y, a.piy[tp]));
+  if (t < (long long)n * n) {
+    const int xi_ = (int)t / n, xp = (int)t - xi_ * n;
+    if (a.fast) a.xcost[t] = dmul_(a.keep_x, a.pix[t]);
+    if (on) a.saterm[t] = dadd_(dmul_(kf[xi_], g), dmul_(kl[xp], g));
   }
+  return ty;
+}
+
+__device__ __forceinline__ void move_y_range(const MoveYArgs& a, long long start, long long stride) {
+  const MoveYDraw dr = move_y_draw(a);
+  for (long long t = start; t < a.T; t += stride) (void)move_y_tile(a, t, dr);
   if (start == 0) {
-    a.sc->sa_on = on ? 1 : 0;
+    a.sc->sa_on = dr.on ? 1 : 0;
     if (a.fast) a.sc->lb_base = a.sc->lb;
   }
 }
 
-// Folded z move: psi <- psi - tile term, one element per thread (coalesced);
-// runs after move_y_range has written the tile terms.
-__device__ __forceinline__ void shift_psi_range(const MoveYArgs& a, long long start, long long stride) {
-  const int m = a.n - 2;
-  const long long Tm = a.T * m;  // < 2^25 for n <= 32: the tile by a 32-bit division
-  for (long long e = start; e < Tm; e += stride) a.psi[e] = dsub_(a.psi[e], a.tterm[(unsigned)e / (unsigned)m]);
+// The y move and, for the folded z move, psi <- psi - tile term in the same
+// pass: a warp moves 32 consecutive tiles (lane j tile tw + j) and then
+// shifts their 32 m column duals, which are contiguous, in coalesced turns
+// (each entry's term shuffled from the lane of its tile), six loads in flight
+// per lane.  start is the global thread index and stride a multiple of 32.
+__device__ __forceinline__ void move_y_shift_range(const MoveYArgs& a, long long start, long long stride) {
+  constexpr int kU = 6;
+  const int lane = (int)(start & 31), m = a.n - 2;
+  const MoveYDraw dr = move_y_draw(a);
+  for (long long tw = start - lane; tw < a.T; tw += stride) {
+    const long long t = tw + lane;
+    const double ty = t < a.T ? move_y_tile(a, t, dr) : 0.0;
+    const int cnt = (int)(a.T - tw < 32 ? a.T - tw : 32) * m;
+    double* p = a.psi + tw * m;
+    for (int e0 = 0; e0 < cnt; e0 += 32 * kU) {
+      double x[kU];
+#pragma unroll
+      for (int k = 0; k < kU; ++k) {
+        const int e = e0 + 32 * k + lane;
+        x[k] = e < cnt ? p[e] : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < kU; ++k) {
+        const int e = e0 + 32 * k + lane;
+        // every lane shuffles (full mask); the source lane is e's tile, < 32 since e < 32 m
+        const double tt = __shfl_sync(0xffffffffu, ty, (int)((unsigned)(e < cnt ? e : cnt - 1) / (unsigned)m));
+        if (e < cnt) p[e] = dsub_(x[k], tt);
+      }
+    }
+  }
+  if (start == 0) {
+    a.sc->sa_on = dr.on ? 1 : 0;
+    if (a.fast) a.sc->lb_base = a.sc->lb;
+  }
 }
 
 // The six members of a class {(i,p),(j,q),(k,r)} are the position orders of the

@@ -69,6 +69,7 @@ struct LapArgs {
                              // the next tile by cp.async while it solves the current one
   unsigned long long* head;  // nullable: device counter of the prefetching form's LAP queue
                              // (launch_lap zeroes it on the stream before the launch)
+  int head_zeroed;           // an earlier launch on the stream has zeroed *head: no memset
 };
 
 // The LAPs of one stage of one branch-and-bound node.

@@ -532,31 +532,46 @@ __host__ __device__ inline size_t warp_smem_bytes_async(int m, int G) {
 // returned (0 for FP64).  All 32 lanes call it; src == nullptr for a group
 // without a LAP.  CG: load through L2 only (the tile was written by other SMs
 // during the same launch, so a line in this SM's L1 may be stale).
-template <int G, bool FX, bool CG = false>
+// The lane's entries e = gl, gl + G, ... < mm of src (+ add, rounded), U
+// of them loaded before any is used (U > 1 for latency-bound launches of few
+// LAPs, where one warp's serial loads would be its time), each passed to f(e, x).
+template <int G, bool CG, int U, typename F>
+__device__ __forceinline__ void for_tile_entries(int mm, int gl, const double* src, const double* add, F&& f) {
+  for (int e0 = gl; e0 < mm; e0 += G * U) {
+    double x[U], y[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int e = e0 + k * G;
+      x[k] = e < mm ? (CG ? __ldcg(src + e) : __ldcs(src + e)) : 0.0;
+      y[k] = (add && e < mm) ? (CG ? __ldcg(add + e) : __ldcs(add + e)) : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int e = e0 + k * G;
+      if (e < mm) f(e, add ? __dadd_rn(x[k], y[k]) : x[k]);
+    }
+  }
+}
+
+template <int G, bool FX, bool CG = false, int U = 1>
 __device__ __forceinline__ int stage_tile(typename std::conditional<FX, long long, double>::type* tile, int ld,
                                           int m, int gl, const double* src, const double* add) {
   const int mm = m * m;
   if constexpr (!FX) {
-    if (src) {
-      for (int e = gl; e < mm; e += G) {
+    if (src)
+      for_tile_entries<G, CG, U>(mm, gl, src, add, [&](int e, double x) {
         const int r = e / m, c = e - r * m;
-        double x = CG ? __ldcg(src + e) : __ldcs(src + e);
-        if (add) x = __dadd_rn(x, CG ? __ldcg(add + e) : __ldcs(add + e));
         tile[r * ld + c] = x;
-      }
-    }
+      });
     return 0;
   } else {
     unsigned eb = 0;
-    if (src) {
-      for (int e = gl; e < mm; e += G) {
+    if (src)
+      for_tile_entries<G, CG, U>(mm, gl, src, add, [&](int e, double x) {
         const int r = e / m, c = e - r * m;
-        double x = CG ? __ldcg(src + e) : __ldcs(src + e);
-        if (add) x = __dadd_rn(x, CG ? __ldcg(add + e) : __ldcs(add + e));
         tile[r * ld + c] = __double_as_longlong(x);  // bits; converted below once the grid is known
         eb = max(eb, fx_expfield(x));
-      }
-    }
+      });
     if constexpr (G == 32) {
       eb = __reduce_max_sync(kFull, eb);
     } else {

@@ -573,12 +573,15 @@ def test_max_residual_size_n32_sampled(R):
         assert np.allclose(xi, o.u, atol=1e-9 * scale) and np.allclose(psi, o.v, atol=1e-9 * scale)
 
 
-def test_direct_launches_and_graph_replay_agree(R):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_direct_launches_and_graph_replay_agree(R, mode):
     """A context launches its first 64 iterations kernel by kernel and later ones
-    as CUDA-graph replays; splitting a run over many calls, or running it in one
-    call, gives the same trajectory bit for bit (raw duals)."""
+    as CUDA-graph replays (of eight iterations, then of one); splitting a run
+    over many calls, or running it in one call, gives the same trajectory bit
+    for bit (raw duals; canonical duals in fixed point, whose Z stage takes its
+    LAPs from a queue that the y-move launch resets every iteration)."""
     inst = I.random_instance(9, 81, with_b=True, asymmetric=True)
-    prm = R.params(dual_mode=0, feas_tol=0.0, warm=1)
+    prm = R.params(dual_mode=mode, feas_tol=0.0, warm=1)
     with R.Context(inst.F, inst.D, inst.B, prm=prm) as a:
         one, _ = a.iterate(90)
     parts = []
