@@ -191,8 +191,8 @@ rlt2_status rlt2_create_child(rlt2_ctx* parent, int facility, int location, cons
  * Stops early (returns OK) once the feasibility check, min_gap or the stall
  * rule fires: iterations are enqueued in chunks of 8, 16, 32, ... and the call
  * returns after the chunk in which the device stopped.  A context's first 64
- * iterations are launched kernel by kernel, later ones as replays of one
- * captured CUDA graph (same kernels, same results).
+ * iterations are launched kernel by kernel, later ones as replays of captured
+ * CUDA graphs of eight iterations and of one (same kernels, same results).
  * Synchronises the context's stream before returning. */
 rlt2_status rlt2_iterate(rlt2_ctx* ctx, int iters, double* lb_hist, int* done);
 

@@ -20,7 +20,8 @@
 //   k_finalize   bound, best bound, upper bound of the X primal, the feasibility
 //                check that follows Algorithm 1, stop flags, bound history
 // A context's first 64 iterations are launched kernel by kernel, later ones as
-// replays of one captured CUDA graph.  The ascent step of iteration m runs at
+// replays of captured CUDA graphs (eight iterations each, one for the rest of a
+// call).  The ascent step of iteration m runs at
 // the start of iteration m+1, so after every call the state, duals and reduced
 // costs describe the same multipliers.  Device-side flags (done / have_snap)
 // make every kernel a no-op after a stop, so whole batches of iterations can
@@ -1112,7 +1113,7 @@ static void drop_graphs(rlt2_ctx* c) {
 
 constexpr int kEvChunk = 64;  // iterations per batch of timing events
 // A context's first kDirectIters iterations are launched kernel by kernel:
-// capturing and instantiating the CUDA graph costs about as much as one
+// capturing and instantiating the CUDA graphs costs about as much as one
 // iteration of a mid-size node, which short-lived branch-and-bound contexts
 // never win back; the iterations are GPU-bound either way.
 constexpr long long kDirectIters = 64;
