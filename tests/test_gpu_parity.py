@@ -467,6 +467,26 @@ def test_stall_and_gap_stops(R):
         assert ctx.stats()[7] == 2 and done <= 61
 
 
+@pytest.mark.parametrize("K", [60, 101, 150])
+def test_gap_stop_inside_graph_replays(R, K):
+    """The min_gap stop lands on the same iteration whether it fires among the
+    first 64 iterations (launched kernel by kernel) or inside a replay of the
+    eight-iteration graph (the device flag makes the rest of that replay a no-op)."""
+    inst = I.config(2)
+    with R.Context(inst.F, inst.D, inst.B, prm=R.params(feas_tol=0.0)) as ctx:
+        full, _ = ctx.iterate(200)
+        _, _, ub, _, _, _ = ctx.bound()
+    best = np.maximum.accumulate(full)
+    gap_stop = (ub - best[K]) / ub * (1 + 1e-9)
+    first = int(np.argmax((ub - best) / ub < gap_stop))
+    assert (first >= 64) == (K >= 64)  # the two launch paths are both exercised
+    with R.Context(inst.F, inst.D, inst.B, prm=R.params(feas_tol=0.0, min_gap=gap_stop, ub=ub)) as ctx:
+        lbs, done = ctx.iterate(200)
+        assert ctx.stats()[7] == 2 and done == first + 1
+        assert np.array_equal(lbs[:done], full[:done])
+        assert ctx.bound()[5] == done  # no iteration counted after the stop
+
+
 def test_n30_full_size_sampled(R):
     """n = 30, Manhattan 5x6 grid (756,900 Z-LAPs of size 28, 4.75 GB z array): the
     first bound equals the Gilmore-Lawler closed form, the second matches the
