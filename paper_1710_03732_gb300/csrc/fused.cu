@@ -49,7 +49,7 @@ constexpr int kPipeCheckSpinLimit = 1 << 12;
 constexpr int kMoveWarps = 3;
 
 // 64 registers: four blocks of eight warps per SM (80 unbounded: three)
-template <int G, bool FX>
+template <int G, bool FX, bool RR = false>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 4) k_move_lap_z(MoveZArgs mz, LapArgs a, PipeArgs pa) {
   DevScalars* sc = pa.sc;
   if (sc->done) return;  // stopped: no work, counters untouched
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 4) k_move_lap_z(MoveZA
     if (warm && live && gl < m) u0 = start_dual<FX>(a.u0[t * m + gl], L);
     __syncwarp();
     const WarpLapResult<T> R =
-        group_lap<G, true, A>(tile, ld, live ? m : 0, lane, warm, u0, a.dual_mode, scr, uv + grp * G);
+        group_lap<G, true, A, RR && FX>(tile, ld, live ? m : 0, lane, warm, u0, a.dual_mode, scr, uv + grp * G);
     if (live && gl < m) {
       a.u[t * m + gl] = out_value<FX>(R.u, L);
       a.v[t * m + gl] = out_value<FX>(R.v, L);
@@ -164,12 +164,14 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 4) k_move_lap_z(MoveZA
 
 using PipeKernel = void (*)(MoveZArgs, LapArgs, PipeArgs);
 
+// rr: a cold fixed-point launch reduces the rows first (as k_lap does)
 template <int G>
-static PipeKernel pipe_kernel(bool fx) {
+static PipeKernel pipe_kernel(bool fx, bool rr) {
+  if (fx && rr) return k_move_lap_z<G, true, true>;
   return fx ? k_move_lap_z<G, true> : k_move_lap_z<G, false>;
 }
-static PipeKernel pipe_kernel(int G, bool fx) {
-  return G == 8 ? pipe_kernel<8>(fx) : (G == 16 ? pipe_kernel<16>(fx) : pipe_kernel<32>(fx));
+static PipeKernel pipe_kernel(int G, bool fx, bool rr) {
+  return G == 8 ? pipe_kernel<8>(fx, rr) : (G == 16 ? pipe_kernel<16>(fx, rr) : pipe_kernel<32>(fx, rr));
 }
 
 // Tiles of an n-facility problem sorted by the last move triple of their
@@ -221,8 +223,8 @@ const PipePlan* prepare_pipe(int n, cudaError_t* err) {
   const size_t smem = warp_smem_bytes(m, G) * kMaxWarpsPerBlock;
   const int cap = (int)(warp_smem_bytes(32, 32) * kMaxWarpsPerBlock);
   int occ = 1 << 20;
-  for (int fx = 0; fx < 2; ++fx) {
-    const PipeKernel kern = pipe_kernel(G, fx != 0);
+  for (int k = 0; k < 3; ++k) {  // every form the launch may pick: all co-resident
+    const PipeKernel kern = pipe_kernel(G, k >= 1, k == 2);
     if ((*err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess)
       return nullptr;
     int o = 0;
@@ -264,7 +266,7 @@ cudaError_t launch_move_lap_z(const MoveZArgs& mz, const LapArgs& a, const PipeP
   pa.sc = sc;
   pa.spin_limit = check ? kPipeCheckSpinLimit : kPipeSpinLimit;
   pa.extra = check ? 1ull : 0ull;
-  const PipeKernel kern = pipe_kernel(G, a.dual_mode == 1);
+  const PipeKernel kern = pipe_kernel(G, a.dual_mode == 1, a.dual_mode == 1 && a.u0 == nullptr);
   kern<<<plan.grid, kMaxWarpsPerBlock * 32, warp_smem_bytes(a.m, G) * kMaxWarpsPerBlock, s>>>(mz, a, pa);
   return cudaGetLastError();
 }

@@ -21,7 +21,7 @@ int default_group(int m) { return m <= 8 ? 8 : (m <= 16 ? 16 : 32); }
 // their next step of 32/G LAPs from that counter (zero at launch) when they
 // issue its copies, so that warps whose LAPs needed few searches take more of
 // them and all warps end together; otherwise they take a fixed grid stride.
-template <int G>
+template <int G, bool RR>
 __device__ __forceinline__ void k_lap_prefetching(const LapArgs& a, unsigned char* base, int lane, bool warm,
                                                   long long first, long long stride) {
   using A = ArithFx;
@@ -73,7 +73,7 @@ __device__ __forceinline__ void k_lap_prefetching(const LapArgs& a, unsigned cha
     T u0 = T(0);
     if (warm && have && gl < m) u0 = start_dual<true>(raw[mm + gl], L);
     long long next = a.batch;  // claimed in the hook, which group_lap calls once (raw is set)
-    const WarpLapResult<T> R = group_lap<G, true, A>(tile, ld, have ? m : 0, lane, warm, u0, a.dual_mode, scr,
+    const WarpLapResult<T> R = group_lap<G, true, A, RR>(tile, ld, have ? m : 0, lane, warm, u0, a.dual_mode, scr,
                                                      uv + grp * G, raw, L, [&]() {
                                                        next = claim(t0 + stride);
                                                        issue(next);
@@ -100,8 +100,9 @@ __device__ __forceinline__ void k_lap_prefetching(const LapArgs& a, unsigned cha
 }
 
 // Grid-stride over LAPs, 32/G LAPs per warp per step.  FX selects the exact
-// fixed-point arithmetic (canonical duals), else FP64.
-template <int G, bool PRE, bool FX>
+// fixed-point arithmetic (canonical duals), else FP64; RR (fixed point, cold
+// launches) reduces the rows of a cold start first.
+template <int G, bool PRE, bool FX, bool RR = false>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap(LapArgs a) {
   if (a.skip && *a.skip) return;
   using A = typename std::conditional<FX, ArithFx, ArithF64>::type;
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap(LapArgs a) {
       const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
       const bool warm = a.u0 != nullptr && (a.warm_gate == nullptr || *a.warm_gate != 0);
       const long long nwarps = (long long)gridDim.x * wpb;
-      k_lap_prefetching<G>(a, smem_raw + (size_t)wib * warp_smem_bytes_async(a.m, G), lane, warm,
+      k_lap_prefetching<G, RR>(a, smem_raw + (size_t)wib * warp_smem_bytes_async(a.m, G), lane, warm,
                            ((long long)blockIdx.x * wpb + wib) * (32 / G), nwarps * (32 / G));
       return;
     }
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap(LapArgs a) {
     __syncwarp();
     // without a reduced-cost output (PRE) the tile may be overwritten by the canonical pass
     const WarpLapResult<T> R =
-        group_lap<G, PRE, A>(tile, ld, have ? m : 0, lane, warm, u0, a.dual_mode, scr, uv + grp * G);
+        group_lap<G, PRE, A, RR && FX>(tile, ld, have ? m : 0, lane, warm, u0, a.dual_mode, scr, uv + grp * G);
     if (have && gl < m) {
       if (a.u) a.u[t * m + gl] = out_value<FX>(R.u, L);
       if (a.v) a.v[t * m + gl] = out_value<FX>(R.v, L);
@@ -213,17 +214,19 @@ static int gidx(int G) { return G == 8 ? 0 : (G == 16 ? 1 : 2); }
 
 using LapKernel = void (*)(LapArgs);
 
-// The kernel for (group, in-place canonical pass, fixed-point arithmetic).
+// The kernel for (group, in-place canonical pass, fixed-point arithmetic, row
+// reduction of cold starts; the last only with fixed point).
 template <int G>
-static LapKernel lap_kernel(bool pre, bool fx) {
+static LapKernel lap_kernel(bool pre, bool fx, bool rr) {
+  if (fx && rr) return pre ? k_lap<G, true, true, true> : k_lap<G, false, true, true>;
   if (pre) return fx ? k_lap<G, true, true> : k_lap<G, true, false>;
   return fx ? k_lap<G, false, true> : k_lap<G, false, false>;
 }
-static LapKernel lap_kernel(int G, bool pre, bool fx) {
-  return G == 8 ? lap_kernel<8>(pre, fx) : (G == 16 ? lap_kernel<16>(pre, fx) : lap_kernel<32>(pre, fx));
+static LapKernel lap_kernel(int G, bool pre, bool fx, bool rr) {
+  return G == 8 ? lap_kernel<8>(pre, fx, rr) : (G == 16 ? lap_kernel<16>(pre, fx, rr) : lap_kernel<32>(pre, fx, rr));
 }
 
-// Occupancy of the slowest of the four forms, so that one grid size serves all.
+// Occupancy of the slowest of the six forms, so that one grid size serves all.
 static cudaError_t prepare_one(LapDevCfg& cfg, int G, int m, int wpb) {
   int& slot = cfg.occ[m][gidx(G)][wpb == 4 ? 0 : 1];
   if (slot > 0) return cudaSuccess;
@@ -231,9 +234,9 @@ static cudaError_t prepare_one(LapDevCfg& cfg, int G, int m, int wpb) {
   cudaError_t e;
   const int cap = (int)(warp_smem_bytes_async(32, 32) * kMaxWarpsPerBlock);
   int occ = 1 << 20;
-  for (int k = 0; k < 4; ++k) {
-    const bool pre = (k & 1) != 0, fx = (k & 2) != 0;
-    const LapKernel kern = lap_kernel(G, pre, fx);
+  for (int k = 0; k < 6; ++k) {
+    const bool pre = (k & 1) != 0, fx = (k & 2) != 0 || k >= 4, rr = k >= 4;
+    const LapKernel kern = lap_kernel(G, pre, fx, rr);
     if (!attr_set[gidx(G)]) {
       if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cap)) != cudaSuccess)
         return e;
@@ -283,7 +286,8 @@ cudaError_t launch_lap(const LapArgs& a, cudaStream_t s) {
   const long long per_block = (long long)wpb * (32 / G);
   const long long need = (a.batch + per_block - 1) / per_block;
   const int grid = (int)(need < cap ? need : cap);
-  const LapKernel kern = lap_kernel(G, a.pi == nullptr, a.dual_mode == 1);
+  // a cold fixed-point launch reduces the rows first (the same canonical result)
+  const LapKernel kern = lap_kernel(G, a.pi == nullptr, a.dual_mode == 1, a.dual_mode == 1 && a.u0 == nullptr);
   if (!b.prefetch) b.head = nullptr;
   if (b.head && !b.head_zeroed && (e = cudaMemsetAsync(b.head, 0, sizeof(unsigned long long), s)) != cudaSuccess)
     return e;

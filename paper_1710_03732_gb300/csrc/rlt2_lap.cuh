@@ -248,7 +248,11 @@ struct NoHook {
 // entry onto the grid 2^L as it reads it (lanes = columns) and stores it into
 // cs, and calls hook() once raw is no longer needed.  Without raw, cs already
 // holds the converted tile.
-template <int G, bool PRE, typename A, typename Hook = NoHook>
+// RR (exact form only): a cold start reduces the rows first, u_r = the row's
+// minimum, as the classical Hungarian method does, before the column
+// reduction: fewer searches are left after the greedy matching, and the
+// canonical result does not depend on the start.
+template <int G, bool PRE, typename A, bool RR = false, typename Hook = NoHook>
 __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T* __restrict__ cs, int ld, int m,
                                                                   int lane, bool warm, typename A::T u0,
                                                                   int dual_mode, int* scr, typename A::T* uvs,
@@ -272,6 +276,25 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
   // exact form: the running minimum starts above every |x| < 2^58, so the first
   // row always takes it (the same result as testing arg < 0)
   T vmin = A::kExact ? T(0x7fffffffffffffffll) : T(0);
+  if constexpr (A::kExact && RR) {
+    if (!warm) {
+      if (raw) {  // the tile onto the grid first (lanes = columns)
+        for (int r = 0; r < M; ++r)
+          if (cv && r < m) cs[r * ld + gl] = fx_floor_entry(raw[r * m + gl], L);
+        __syncwarp();
+        hook();
+        raw = nullptr;
+      }
+      T mn = T(0x7fffffffffffffffll);  // above every entry (|x| < 2^58)
+      for (int c = 0; c < M; ++c)
+        if (cv && c < m) {
+          const T x = cs[gl * ld + c];  // lane = row (odd row stride: no bank conflicts)
+          mn = x < mn ? x : mn;
+        }
+      u = cv ? mn : T(0);
+      warm = true;  // the column reduction below subtracts these row duals
+    }
+  }
   if constexpr (A::kExact) {
     uvs[gl] = u;
     __syncwarp();
