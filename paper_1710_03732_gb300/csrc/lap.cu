@@ -305,7 +305,7 @@ cudaError_t launch_lap(const LapArgs& a, cudaStream_t s) {
 // group_lap's hook once the current raw tiles are converted).  The raw buffers
 // are sized for the largest LAP of the stage.  Results are those of the staged
 // form bit for bit (each LAP is independent of which warp solves it).
-template <int G>
+template <int G, bool RR>
 __device__ __forceinline__ void k_lap_nodes_prefetching(const NodeLapArgs& a, const long long* s_prefix,
                                                         unsigned char* base, int lane) {
   using A = ArithFx;
@@ -378,7 +378,7 @@ __device__ __forceinline__ void k_lap_nodes_prefetching(const NodeLapArgs& a, co
     }
     const int L = fx_grid(eb);
     const T u0 = (cur.warm && gl < m) ? start_dual<true>(raw[mm + gl], L) : T(0);
-    const WarpLapResult<T> R = group_lap<G, true, A>(tile, tile_ld(m), m, lane, cur.warm, u0, a.dual_mode, scr,
+    const WarpLapResult<T> R = group_lap<G, true, A, RR>(tile, tile_ld(m), m, lane, cur.warm, u0, a.dual_mode, scr,
                                                      uv + grp * G, raw, L, [&]() { issue(nxt); });
     if (cur.have) {
       const NodeLapItem& it = a.items[cur.k];
@@ -404,7 +404,7 @@ __device__ __forceinline__ void k_lap_nodes_prefetching(const NodeLapArgs& a, co
   }
 }
 
-template <int G, bool PRE, bool FX>
+template <int G, bool PRE, bool FX, bool RR = false>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap_nodes(NodeLapArgs a) {
   using A = typename std::conditional<FX, ArithFx, ArithF64>::type;
   using T = typename A::T;
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap_nodes(NodeLapArg
   if constexpr (PRE && FX) {
     if (a.prefetch) {
       const size_t pre = (((size_t)(a.nnodes + 1) * sizeof(long long)) + 255) & ~size_t(255);
-      k_lap_nodes_prefetching<G>(a, s_prefix,
+      k_lap_nodes_prefetching<G, RR>(a, s_prefix,
                                  smem_raw + pre + (size_t)(threadIdx.x >> 5) * warp_smem_bytes_async(a.max_m, G),
                                  threadIdx.x & 31);
       return;
@@ -462,7 +462,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap_nodes(NodeLapArg
     const bool warm = have && it.u0 != nullptr && (it.warm_gate == nullptr || *it.warm_gate != 0);
     const T u0 = (warm && gl < m) ? start_dual<FX>(it.u0[li * m + gl], L) : T(0);
     __syncwarp();
-    const WarpLapResult<T> R = group_lap<G, PRE, A>(tile, ld, m, lane, warm, u0, a.dual_mode, scr, uv + grp * G);
+    const WarpLapResult<T> R =
+        group_lap<G, PRE, A, RR && FX>(tile, ld, m, lane, warm, u0, a.dual_mode, scr, uv + grp * G);
     if (have && gl < m) {
       if (it.u) it.u[li * m + gl] = out_value<FX>(R.u, L);
       if (it.v) it.v[li * m + gl] = out_value<FX>(R.v, L);
@@ -496,12 +497,14 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_lap_nodes(NodeLapArg
 using NodeLapKernel = void (*)(NodeLapArgs);
 
 template <int G>
-static NodeLapKernel node_lap_kernel(bool pre, bool fx) {
+static NodeLapKernel node_lap_kernel(bool pre, bool fx, bool rr) {
+  if (fx && rr) return pre ? k_lap_nodes<G, true, true, true> : k_lap_nodes<G, false, true, true>;
   if (pre) return fx ? k_lap_nodes<G, true, true> : k_lap_nodes<G, true, false>;
   return fx ? k_lap_nodes<G, false, true> : k_lap_nodes<G, false, false>;
 }
-static NodeLapKernel node_lap_kernel(int G, bool pre, bool fx) {
-  return G == 8 ? node_lap_kernel<8>(pre, fx) : (G == 16 ? node_lap_kernel<16>(pre, fx) : node_lap_kernel<32>(pre, fx));
+static NodeLapKernel node_lap_kernel(int G, bool pre, bool fx, bool rr) {
+  return G == 8 ? node_lap_kernel<8>(pre, fx, rr)
+                : (G == 16 ? node_lap_kernel<16>(pre, fx, rr) : node_lap_kernel<32>(pre, fx, rr));
 }
 
 cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s) {
@@ -523,14 +526,14 @@ cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s) {
   const size_t cap_smem = (((size_t)(kMaxWaveNodes + 1) * sizeof(long long)) + 255) / 256 * 256 +
                           warp_smem_bytes_async(32, 32) * kMaxWarpsPerBlock;
   int& occ = cfg->occ_nodes[a.max_m][gidx(G)][wpb == 4 ? 0 : 1];
-  // occupancy of the slowest of the four forms, computed once per size (the
+  // occupancy of the slowest of the six forms, computed once per size (the
   // prefix table's share of shared memory varies with the node count; a grid
   // above the resident count only queues blocks, which never wait on others)
   if (!occ) {
     int lo = 1 << 20;
-    for (int k = 0; k < 4; ++k) {
-      const bool kpre = (k & 1) != 0, kfx = (k & 2) != 0;
-      const NodeLapKernel kern = node_lap_kernel(G, kpre, kfx);
+    for (int k = 0; k < 6; ++k) {
+      const bool kpre = (k & 1) != 0, kfx = (k & 2) != 0 || k >= 4;
+      const NodeLapKernel kern = node_lap_kernel(G, kpre, kfx, k >= 4);
       if (!attr_set[gidx(G)]) {
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap_smem)) !=
             cudaSuccess)
@@ -550,7 +553,7 @@ cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s) {
   const long long per_block = (long long)wpb * (32 / G);
   const long long need = (a.total + per_block - 1) / per_block;
   const int grid = (int)(need < cap ? need : cap);
-  const NodeLapKernel kern = node_lap_kernel(G, a.pre, a.dual_mode == 1);
+  const NodeLapKernel kern = node_lap_kernel(G, a.pre, a.dual_mode == 1, a.cold && a.dual_mode == 1);
   kern<<<grid, wpb * 32, smem, s>>>(b);
   return cudaGetLastError();
 }

@@ -166,6 +166,7 @@ struct Wave {
   std::vector<LearnedStart> learned;  // one per node when warm == 2
   int nn = 0;
   int two_phase = 0;
+  int cold = 0;  // warm == 0: no LAP of the wave has start duals
   long long total[kStages] = {0, 0, 0, 0};
   int max_m[kStages] = {0, 0, 0, 0};
   int max_blocks = 0;
@@ -259,6 +260,7 @@ cudaError_t enqueue_wave_iteration(const Wave& w, const WaveDev& d, int dual_mod
     }
     NodeLapArgs a{};
     a.dual_mode = dual_mode;
+    a.cold = w.cold;
     a.stats = d.stats + 2 * (stage == 3 ? 0 : stage);
     if (stage == 1 || stage == 2) {  // Y, X: one launch over all nodes, node order
       a.nnodes = w.nn;
@@ -523,6 +525,7 @@ cudaError_t iterate_views(const IterView* views, int nn, const rlt2_params& prm,
   Wave w;
   w.nn = nn;
   w.two_phase = prm.two_phase;
+  w.cold = prm.warm == 0;
   WaveHost h(nn);
   for (int j = 0; j < nn; ++j) add_node(w, h, j, views[j], prm);
   sort_z(w, h);
@@ -692,6 +695,7 @@ extern "C" rlt2_status rlt2_bound_nodes(int n, const double* F, const double* D,
     // carve the arenas and upload each node's index lists
     char* cur = pool;
     w.two_phase = prm.two_phase;
+    w.cold = prm.warm == 0;
     WaveHost hw(w.nn);
     std::vector<DevScalars> init(1);
     init[0] = DevScalars{};

@@ -106,6 +106,7 @@ struct NodeLapArgs {
              // such stages (the Z stages) have no Badd either
   int prefetch;  // set by launch_lap_nodes: fixed-point pre stages copy each warp's next
                  // queue item into shared memory by cp.async while the current one is solved
+  int cold;      // no item has start duals: fixed-point LAPs reduce their rows first
 };
 cudaError_t launch_lap_nodes(const NodeLapArgs& a, cudaStream_t s);
 
