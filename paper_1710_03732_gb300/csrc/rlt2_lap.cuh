@@ -277,7 +277,8 @@ __device__ __forceinline__ WarpLapResult<typename A::T> group_lap(typename A::T*
   // row always takes it (the same result as testing arg < 0)
   T vmin = A::kExact ? T(0x7fffffffffffffffll) : T(0);
   if constexpr (A::kExact && RR) {
-    if (!warm) {
+    // warp-uniform (the launches that take RR start every LAP cold)
+    if (!__any_sync(kFull, warm)) {
       if (raw) {  // the tile onto the grid first (lanes = columns)
         for (int r = 0; r < M; ++r)
           if (cv && r < m) cs[r * ld + gl] = fx_floor_entry(raw[r * m + gl], L);
