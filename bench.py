@@ -340,6 +340,19 @@ def run_profile_case(args):
                           "ms_per_call": e0.elapsed_time(e1) / max(1, args.steps)}))
         mlp.close()
         return 0
+    if args.profile in ("n22", "n30"):
+        # the root problem of the n=22 grid (config 4's QAP) or the n=30 grid, warm
+        # starts, launched kernel by kernel with CUDA events around every launch
+        inst = I.config(4 if args.profile == "n22" else 5)
+        with R.Context(inst.F, inst.D, inst.B, prm=R.params(dual_mode=1, warm=1, feas_tol=0.0)) as ctx:
+            ctx.iterate(args.warmup)
+            ctx.set_timing(True)
+            hist, got = ctx.iterate(args.steps)
+            kt = ctx.kernel_times()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": inst.name, "warm": 1, "iterations": args.warmup + got,
+                          "ms_per_iteration": {k: v[0] / max(1, v[1]) for k, v in kt.items() if v[1] > 0}}))
+        return 0
     inst = I.config(CFG)
     mlp = None
     warm = 1
@@ -626,9 +639,12 @@ def main():
     ap.add_argument("--bnb-hard", action="store_true",
                     help="only solve a Nugent-like n=20 QAP (4x5 grid, F 0..9 at density 0.5, seed 12) to proven "
                          "optimality with rlt2_bnb_solve and print its statistics (about two minutes)")
-    ap.add_argument("--profile", nargs="?", const="n20", choices=["n20", "nodes", "learned", "train", "gemm"],
+    ap.add_argument("--profile", nargs="?", const="n20",
+                    choices=["n20", "n22", "n30", "nodes", "learned", "train", "gemm"],
                     help="only run a small case for ncu captures: n20 = warmup+steps iterations of the n=20 "
-                         "workload (graph replay, warm start); nodes = 16 nodes of the n=22 grid QAP; "
+                         "workload (graph replay, warm start); n22 / n30 = warmup+steps iterations of the n=22 "
+                         "grid QAP's root or the n=30 grid QAP, warm, with per-kernel times; "
+                         "nodes = 16 nodes of the n=22 grid QAP; "
                          "learned = n=20 with the learned warm start; train = AdamW steps of the H=256 "
                          "network (16,384 rows); gemm = its gradients on 262,144 rows per call")
     args = ap.parse_args()
