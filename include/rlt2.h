@@ -328,7 +328,9 @@ long long rlt2_debug_bounds_violations(void);
  * small LAPs solved in one launch).
  *  batch, m : number of LAPs and their size, 1 <= m <= 32
  *  cost     : device, batch*m*m, LAP b at cost + b*m*m, row-major
- *  u0       : device, batch*m starting row duals, or NULL (cold start)
+ *  u0       : device, batch*m starting row duals, or NULL (cold start: a
+ *             column reduction, preceded in dual_mode 1 by a row reduction;
+ *             the canonical results do not depend on the start, n_aug does)
  *  value    : device, batch optimal values (sum of the assigned costs)
  *  u, v     : device, batch*m row / column duals (nullable)
  *  row_to_col: device, batch*m assignment (nullable)
