@@ -355,7 +355,7 @@ def run_profile_case(args):
         return 0
     inst = I.config(CFG)
     mlp = None
-    warm = 1
+    warm = 0 if args.profile == "cold" else 1
     if args.profile == "learned":
         mlp = R.Mlp(256)
         mlp.load(os.path.join(ROOT, "paper_1710_03732_gb300", "weights", "warmstart_h256.npz"))
@@ -640,9 +640,10 @@ def main():
                     help="only solve a Nugent-like n=20 QAP (4x5 grid, F 0..9 at density 0.5, seed 12) to proven "
                          "optimality with rlt2_bnb_solve and print its statistics (about two minutes)")
     ap.add_argument("--profile", nargs="?", const="n20",
-                    choices=["n20", "n22", "n30", "nodes", "learned", "train", "gemm"],
+                    choices=["n20", "cold", "n22", "n30", "nodes", "learned", "train", "gemm"],
                     help="only run a small case for ncu captures: n20 = warmup+steps iterations of the n=20 "
-                         "workload (graph replay, warm start); n22 / n30 = warmup+steps iterations of the n=22 "
+                         "workload (graph replay, warm start); cold = the same with cold LAPs; "
+                         "n22 / n30 = warmup+steps iterations of the n=22 "
                          "grid QAP's root or the n=30 grid QAP, warm, with per-kernel times; "
                          "nodes = 16 nodes of the n=22 grid QAP; "
                          "learned = n=20 with the learned warm start; train = AdamW steps of the H=256 "
